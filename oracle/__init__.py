@@ -1,0 +1,200 @@
+"""FP64 CPU oracle for IGA-FEM element-matrix integration (arxiv 2207.00280).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library (``paper_2207_00280_gb300``)
+and never serves as a fallback for it.
+
+The arithmetic lives in ``iga_oracle.c`` (plain C, ``-O2 -ffp-contract=off``);
+this module only compiles it, loads it with ctypes and marshals numpy arrays.
+Every routine cites the passage of the paper it follows in ``iga_oracle.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "iga_oracle.c")
+_HDR = os.path.join(_HERE, "iga_oracle.h")
+_SO = os.path.join(_HERE, "libiga_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/libiga_oracle.so`` (gcc, FP64, no FMA contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Patch(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
+                ("m", ctypes.c_int * 3), ("t", ctypes.c_void_p * 3)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            dp = ctypes.c_void_p
+            L.ora_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
+            L.ora_gauss_legendre.restype = ctypes.c_int
+            L.ora_bspline.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+            L.ora_bspline.restype = ctypes.c_double
+            L.ora_bspline_deriv.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+            L.ora_bspline_deriv.restype = ctypes.c_double
+            L.ora_spans.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+            L.ora_spans.restype = ctypes.c_int
+            L.ora_basis_1d.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+            L.ora_basis_1d.restype = None
+            pp = ctypes.POINTER(_Patch)
+            for name in ("ora_classical", "ora_sumfact"):
+                f = getattr(L, name)
+                f.argtypes = [pp, dp, ctypes.c_int64, dp, dp, dp, dp, dp]
+                f.restype = ctypes.c_int
+            L.ora_dofmap.argtypes = [pp, dp, ctypes.c_int64, dp]
+            L.ora_dofmap.restype = ctypes.c_int
+            L.ora_adjoint.argtypes = [pp, dp, ctypes.c_int64, dp, dp, dp, dp, dp, dp]
+            L.ora_adjoint.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def gauss_legendre(q: int):
+    """Gauss--Legendre nodes and weights on [-1, 1] (Golub--Welsch)."""
+    x = np.zeros(q)
+    w = np.zeros(q)
+    if lib().ora_gauss_legendre(q, _ptr(x), _ptr(w)) != 0:
+        raise ValueError(f"bad q={q}")
+    return x, w
+
+
+def bspline(t, i: int, p: int, xi: float) -> float:
+    t = _f64(t)
+    return lib().ora_bspline(_ptr(t), i, p, float(xi))
+
+
+def bspline_deriv(t, i: int, p: int, xi: float) -> float:
+    t = _f64(t)
+    return lib().ora_bspline_deriv(_ptr(t), i, p, float(xi))
+
+
+def spans(t, p: int) -> np.ndarray:
+    t = _f64(t)
+    out = np.zeros(len(t), dtype=np.int32)
+    c = lib().ora_spans(_ptr(t), len(t), p, _ptr(out))
+    return out[:c].copy()
+
+
+def basis_1d(t, p: int, s: int, q: int):
+    """(xi[q], w[q], val[q][p+1], der[q][p+1]) of span s."""
+    t = _f64(t)
+    xi = np.zeros(q); w = np.zeros(q)
+    val = np.zeros((q, p + 1)); der = np.zeros((q, p + 1))
+    lib().ora_basis_1d(_ptr(t), p, s, q, _ptr(xi), _ptr(w), _ptr(val), _ptr(der))
+    return xi, w, val, der
+
+
+class Patch:
+    """One tensor-product patch: dimension, degree, Gauss points, knot vectors."""
+
+    def __init__(self, knots, p: int, q: int):
+        self.knots = [_f64(t) for t in knots]
+        self.dim = len(self.knots)
+        if self.dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        self.p, self.q = int(p), int(q)
+        self.n = self.p + 1
+        self.N = self.n ** self.dim
+        self.Q = self.q ** self.dim
+        self.n_el = [len(spans(t, p)) for t in self.knots]
+        self.E = int(np.prod(self.n_el))
+        self.n_fun = [len(t) - self.p - 1 for t in self.knots]
+        self.n_dofs = int(np.prod(self.n_fun))
+        s = _Patch()
+        s.dim, s.p, s.q = self.dim, self.p, self.q
+        for k, t in enumerate(self.knots):
+            s.m[k] = len(t)
+            s.t[k] = t.ctypes.data
+        self._s = s
+
+    def _elems(self, elems):
+        if elems is None:
+            elems = np.arange(self.E, dtype=np.int64)
+        return np.ascontiguousarray(elems, dtype=np.int64)
+
+    def _check_qp(self, a, per_qp):
+        if a is None:
+            return None
+        a = _f64(a)
+        if a.size != self.E * self.Q * per_qp:
+            raise ValueError(f"expected {self.E * self.Q * per_qp} values, got {a.size}")
+        return a
+
+    def _mats(self, fn, elems, kappa, rho, G, stiffness, mass):
+        el = self._elems(elems)
+        kappa = self._check_qp(kappa, 1)
+        rho = self._check_qp(rho, 1)
+        G = self._check_qp(G, self.dim * self.dim)
+        if stiffness and kappa is None:
+            kappa = np.ones(self.E * self.Q)
+        K = np.zeros((len(el), self.N, self.N)) if stiffness else None
+        M = np.zeros((len(el), self.N, self.N)) if mass else None
+        rc = fn(ctypes.byref(self._s), _ptr(el), len(el), _ptr(kappa), _ptr(rho), _ptr(G),
+                _ptr(K), _ptr(M))
+        if rc != 0:
+            raise ValueError("oracle rejected its arguments")
+        return K, M
+
+    def classical(self, elems=None, kappa=None, rho=None, G=None, stiffness=True, mass=True):
+        """Element matrices by Algorithm 1 (the naive nested loop)."""
+        return self._mats(lib().ora_classical, elems, kappa, rho, G, stiffness, mass)
+
+    def sumfact(self, elems=None, kappa=None, rho=None, G=None, stiffness=True, mass=True):
+        """Element matrices by Algorithm 2 (sum factorization, literal)."""
+        return self._mats(lib().ora_sumfact, elems, kappa, rho, G, stiffness, mass)
+
+    def dofmap(self, elems=None) -> np.ndarray:
+        el = self._elems(elems)
+        out = np.zeros((len(el), self.N), dtype=np.int32)
+        if lib().ora_dofmap(ctypes.byref(self._s), _ptr(el), len(el), _ptr(out)) != 0:
+            raise ValueError("oracle rejected its arguments")
+        return out
+
+    def adjoint(self, u, v, kappa=None, G=None, elems=None):
+        """(g[n_sel][Q], J) with g = dJ/dkappa for J = u^T K(kappa) v."""
+        el = self._elems(elems)
+        u = _f64(u); v = _f64(v)
+        if u.size != self.n_dofs or v.size != self.n_dofs:
+            raise ValueError("u, v must have one value per global dof")
+        kappa = self._check_qp(kappa, 1)
+        G = self._check_qp(G, self.dim * self.dim)
+        g = np.zeros((len(el), self.Q))
+        J = np.zeros(1)
+        rc = lib().ora_adjoint(ctypes.byref(self._s), _ptr(el), len(el), _ptr(kappa), _ptr(G),
+                               _ptr(u), _ptr(v), _ptr(g), _ptr(J))
+        if rc != 0:
+            raise ValueError("oracle rejected its arguments")
+        return g, float(J[0])

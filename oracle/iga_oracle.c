@@ -1,0 +1,561 @@
+/*
+ * iga_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle for IGA-FEM
+ * element-matrix integration (arxiv 2207.00280).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline leg of the benchmark, never by the CUDA library.  Nothing here is
+ * shared with the GPU path.  Built with -O2 -ffp-contract=off so every product
+ * and sum is rounded exactly as written.
+ *
+ * Pins (what fixes each function independently of itself) live in
+ * tests/test_oracle_*.py: closed-form Gauss rules and polynomial exactness,
+ * scipy's B-spline evaluation, partition of unity, exact rational integrals of
+ * the piecewise polynomials, p = 1 Kronecker closed forms, K 1 = 0, mass sum =
+ * element volume, classical == sum factorization, Greville identities and
+ * finite differences for the adjoint, brute-force support sets for the dofs.
+ */
+#include "iga_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Gauss--Legendre by Golub--Welsch.                                         */
+/* The paper only asks for "a proper exact quadrature" (Sec. 3.1, eq. 10).   */
+/* Nodes are the eigenvalues of the Jacobi matrix of the Legendre three-term */
+/* recurrence (zero diagonal, off-diagonal k / sqrt(4k^2-1)); the weight of a */
+/* node is 2 v_0^2 from its normalised eigenvector.  The eigenproblem is     */
+/* solved by cyclic Jacobi rotations (Golub & Van Loan, "Matrix              */
+/* Computations", Sec. 8.5: each rotation zeroes one off-diagonal pair).     */
+/* ------------------------------------------------------------------------ */
+int ora_gauss_legendre(int q, double* x, double* w) {
+  if (q < 1 || q > 64 || !x || !w) return -1;
+  double* A = (double*)calloc((size_t)q * q, sizeof(double));
+  double* V = (double*)calloc((size_t)q * q, sizeof(double));
+  if (!A || !V) { free(A); free(V); return -1; }
+  for (int i = 0; i < q; ++i) V[i * q + i] = 1.0;
+  for (int k = 1; k < q; ++k) {
+    double beta = (double)k / sqrt(4.0 * k * k - 1.0);
+    A[k * q + (k - 1)] = beta;
+    A[(k - 1) * q + k] = beta;
+  }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j)
+        if (i != j) off += A[i * q + j] * A[i * q + j];
+    if (off < 1e-60) break;
+    for (int pp = 0; pp < q - 1; ++pp) {
+      for (int r = pp + 1; r < q; ++r) {
+        double apr = A[pp * q + r];
+        if (apr == 0.0) continue;
+        double tau = (A[r * q + r] - A[pp * q + pp]) / (2.0 * apr);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t);
+        double s = t * c;
+        for (int k = 0; k < q; ++k) { /* A <- A J */
+          double akp = A[k * q + pp], akr = A[k * q + r];
+          A[k * q + pp] = c * akp - s * akr;
+          A[k * q + r] = s * akp + c * akr;
+        }
+        for (int k = 0; k < q; ++k) { /* A <- J^T A */
+          double apk = A[pp * q + k], ark = A[r * q + k];
+          A[pp * q + k] = c * apk - s * ark;
+          A[r * q + k] = s * apk + c * ark;
+        }
+        for (int k = 0; k < q; ++k) { /* V <- V J */
+          double vkp = V[k * q + pp], vkr = V[k * q + r];
+          V[k * q + pp] = c * vkp - s * vkr;
+          V[k * q + r] = s * vkp + c * vkr;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < q; ++i) {
+    x[i] = A[i * q + i];
+    w[i] = 2.0 * V[0 * q + i] * V[0 * q + i];
+  }
+  /* insertion sort by node, ascending */
+  for (int i = 1; i < q; ++i) {
+    double xi = x[i], wi = w[i];
+    int j = i - 1;
+    while (j >= 0 && x[j] > xi) { x[j + 1] = x[j]; w[j + 1] = w[j]; --j; }
+    x[j + 1] = xi; w[j + 1] = wi;
+  }
+  free(A); free(V);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cox--de Boor, literally recursive (Sec. 2.3, eqs. cox1 and cox2).         */
+/* Degree 0 is the indicator of the half-open span [t_i, t_{i+1}); a term    */
+/* whose knot-difference denominator vanishes is 0 ("0/0 := 0").             */
+/* ------------------------------------------------------------------------ */
+double ora_bspline(const double* t, int i, int p, double xi) {
+  if (p == 0) return (t[i] <= xi && xi < t[i + 1]) ? 1.0 : 0.0;
+  double left = 0.0, right = 0.0;
+  double d1 = t[i + p] - t[i];
+  double d2 = t[i + p + 1] - t[i + 1];
+  if (d1 != 0.0) left = (xi - t[i]) / d1 * ora_bspline(t, i, p - 1, xi);
+  if (d2 != 0.0) right = (t[i + p + 1] - xi) / d2 * ora_bspline(t, i + 1, p - 1, xi);
+  return left + right;
+}
+
+/* Derivative (not in the paper; de Boor, "A Practical Guide to Splines",
+ * ch. X):  B'_{i;p} = p/(t_{i+p}-t_i) B_{i;p-1} - p/(t_{i+p+1}-t_{i+1}) B_{i+1;p-1},
+ * zero-denominator terms taken as 0. */
+double ora_bspline_deriv(const double* t, int i, int p, double xi) {
+  if (p == 0) return 0.0;
+  double a = 0.0, b = 0.0;
+  double d1 = t[i + p] - t[i];
+  double d2 = t[i + p + 1] - t[i + 1];
+  if (d1 != 0.0) a = (double)p / d1 * ora_bspline(t, i, p - 1, xi);
+  if (d2 != 0.0) b = (double)p / d2 * ora_bspline(t, i + 1, p - 1, xi);
+  return a - b;
+}
+
+/* Elements = non-empty spans of the knot vector (Sec. 2.3 knot vector with
+ * p+1 repeated end knots; Sec. 3.1 element decomposition). */
+int ora_spans(const double* t, int m, int p, int* spans) {
+  int c = 0;
+  for (int s = p; s <= m - p - 2; ++s)
+    if (t[s] < t[s + 1]) spans[c++] = s;
+  return c;
+}
+
+/* Quadrature nodes and weights mapped to the span, and the p+1 non-zero
+ * functions B_{s-p+r} and their derivatives at each node. */
+void ora_basis_1d(const double* t, int p, int s, int q, double* xi, double* w,
+                  double* val, double* der) {
+  double xr[64], wr[64];
+  ora_gauss_legendre(q, xr, wr);
+  double a = t[s], b = t[s + 1];
+  double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+  for (int j = 0; j < q; ++j) {
+    xi[j] = mid + half * xr[j];
+    w[j] = half * wr[j];
+    for (int r = 0; r <= p; ++r) {
+      val[j * (p + 1) + r] = ora_bspline(t, s - p + r, p, xi[j]);
+      der[j * (p + 1) + r] = ora_bspline_deriv(t, s - p + r, p, xi[j]);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shared bookkeeping for the element routines.                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int d, p, n, q, N, Q;
+  int K[3];           /* elements per direction */
+  int* spans[3];
+} layout;
+
+static int make_layout(const ora_patch* pt, layout* L) {
+  if (!pt || (pt->dim != 2 && pt->dim != 3) || pt->p < 1 || pt->p > 16 || pt->q < 1 || pt->q > 64)
+    return -1;
+  L->d = pt->dim; L->p = pt->p; L->n = pt->p + 1; L->q = pt->q;
+  L->N = 1; L->Q = 1;
+  for (int k = 0; k < 3; ++k) { L->spans[k] = NULL; L->K[k] = 1; }
+  for (int k = 0; k < L->d; ++k) {
+    if (!pt->t[k] || pt->m[k] < 2 * pt->p + 2) return -1;
+    L->spans[k] = (int*)malloc(sizeof(int) * (size_t)pt->m[k]);
+    L->K[k] = ora_spans(pt->t[k], pt->m[k], pt->p, L->spans[k]);
+    L->N *= L->n; L->Q *= L->q;
+  }
+  return 0;
+}
+
+static void free_layout(layout* L) {
+  for (int k = 0; k < 3; ++k) free(L->spans[k]);
+}
+
+static int64_t n_elements(const layout* L) {
+  return (int64_t)L->K[0] * L->K[1] * (L->d == 3 ? L->K[2] : 1);
+}
+
+/* element id -> per-direction element index */
+static void split_elem(const layout* L, int64_t e, int* ek) {
+  ek[0] = (int)(e % L->K[0]);
+  int64_t r = e / L->K[0];
+  ek[1] = (int)(r % L->K[1]);
+  ek[2] = (L->d == 3) ? (int)(r / L->K[1]) : 0;
+}
+
+/* |det G| and G^{-1} of a d x d row-major matrix by cofactors. */
+static double geom_inverse(int d, const double* G, double* Ginv) {
+  if (d == 2) {
+    double det = G[0] * G[3] - G[1] * G[2];
+    Ginv[0] = G[3] / det; Ginv[1] = -G[1] / det;
+    Ginv[2] = -G[2] / det; Ginv[3] = G[0] / det;
+    return fabs(det);
+  }
+  double c00 = G[4] * G[8] - G[5] * G[7];
+  double c01 = G[5] * G[6] - G[3] * G[8];
+  double c02 = G[3] * G[7] - G[4] * G[6];
+  double det = G[0] * c00 + G[1] * c01 + G[2] * c02;
+  /* inverse = adjugate / det, adjugate = cofactor matrix transposed */
+  Ginv[0] = c00 / det;
+  Ginv[1] = (G[2] * G[7] - G[1] * G[8]) / det;
+  Ginv[2] = (G[1] * G[5] - G[2] * G[4]) / det;
+  Ginv[3] = c01 / det;
+  Ginv[4] = (G[0] * G[8] - G[2] * G[6]) / det;
+  Ginv[5] = (G[2] * G[3] - G[0] * G[5]) / det;
+  Ginv[6] = c02 / det;
+  Ginv[7] = (G[1] * G[6] - G[0] * G[7]) / det;
+  Ginv[8] = (G[0] * G[4] - G[1] * G[3]) / det;
+  return fabs(det);
+}
+
+/* Per-element 1D data for every direction. */
+typedef struct {
+  double xi[3][64], w[3][64];
+  double val[3][64 * 17], der[3][64 * 17];
+} elem1d;
+
+static void element_1d(const ora_patch* pt, const layout* L, const int* ek, elem1d* B) {
+  for (int k = 0; k < L->d; ++k)
+    ora_basis_1d(pt->t[k], L->p, L->spans[k][ek[k]], L->q, B->xi[k], B->w[k],
+                 B->val[k], B->der[k]);
+}
+
+/* Quadrature point k -> per-direction indices. */
+static void split_qp(const layout* L, int k, int* kk) {
+  kk[0] = k % L->q;
+  kk[1] = (k / L->q) % L->q;
+  kk[2] = (L->d == 3) ? k / (L->q * L->q) : 0;
+}
+
+/* Local function a -> per-direction indices. */
+static void split_local(const layout* L, int a, int* aa) {
+  aa[0] = a % L->n;
+  aa[1] = (a / L->n) % L->n;
+  aa[2] = (L->d == 3) ? a / (L->n * L->n) : 0;
+}
+
+/* Weights, |det G| and G^{-T}-mapped reference gradients at every quadrature
+ * point of one element: the J(x^n) of eq. 10 is |det G| with G the derivative
+ * of the geometry map with respect to the knot coordinates; the factor from
+ * the reference interval to the span sits in the mapped weights. */
+static void element_geometry(const layout* L, int64_t e, const elem1d* B,
+                             const double* G, double* W, double* Ginv) {
+  int d = L->d;
+  for (int k = 0; k < L->Q; ++k) {
+    int kk[3];
+    split_qp(L, k, kk);
+    double wq = 1.0;
+    for (int j = 0; j < d; ++j) wq *= B->w[j][kk[j]];
+    double Gid[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    double G2[4] = {1, 0, 0, 1};
+    const double* Gq;
+    if (G) Gq = G + ((size_t)e * L->Q + k) * d * d;
+    else Gq = (d == 3) ? Gid : G2;
+    double det = geom_inverse(d, Gq, Ginv + (size_t)k * d * d);
+    W[k] = wq * det;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Classical integration: Algorithm 1 (Sec. 3.2) on the sum of eq. 10.       */
+/* ------------------------------------------------------------------------ */
+int ora_classical(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+                  const double* kappa, const double* rho, const double* G,
+                  double* K, double* M) {
+  layout L;
+  if (make_layout(pt, &L)) { free_layout(&L); return -1; }
+  if (K && !kappa) { free_layout(&L); return -1; }
+  int d = L.d, n = L.n, N = L.N, Q = L.Q;
+  int64_t E = n_elements(&L);
+  elem1d* B = (elem1d*)malloc(sizeof(elem1d));
+  double* W = (double*)malloc(sizeof(double) * Q);
+  double* Ginv = (double*)malloc(sizeof(double) * Q * 9);
+  double* phi = (double*)malloc(sizeof(double) * (size_t)N * Q);
+  double* grad = (double*)malloc(sizeof(double) * (size_t)N * Q * 3);
+  for (int64_t s = 0; s < n_sel; ++s) {
+    int64_t e = elems[s];
+    if (e < 0 || e >= E) { free(B); free(W); free(Ginv); free(phi); free(grad); free_layout(&L); return -1; }
+    int ek[3];
+    split_elem(&L, e, ek);
+    element_1d(pt, &L, ek, B);
+    element_geometry(&L, e, B, G, W, Ginv);
+    /* basis values and physical gradients of the tensor functions (eq.
+     * basis_construction) at every quadrature point */
+    for (int a = 0; a < N; ++a) {
+      int aa[3];
+      split_local(&L, a, aa);
+      for (int k = 0; k < Q; ++k) {
+        int kk[3];
+        split_qp(&L, k, kk);
+        double v = 1.0, gr[3];
+        for (int j = 0; j < d; ++j) v *= B->val[j][kk[j] * n + aa[j]];
+        for (int i = 0; i < d; ++i) {
+          double g = 1.0;
+          for (int j = 0; j < d; ++j)
+            g *= (i == j) ? B->der[j][kk[j] * n + aa[j]] : B->val[j][kk[j] * n + aa[j]];
+          gr[i] = g;
+        }
+        phi[(size_t)a * Q + k] = v;
+        const double* Gi = Ginv + (size_t)k * d * d;
+        for (int i = 0; i < d; ++i) { /* (G^{-T} gr)_i = sum_j Ginv[j][i] gr_j */
+          double s2 = 0.0;
+          for (int j = 0; j < d; ++j) s2 += Gi[j * d + i] * gr[j];
+          grad[((size_t)a * Q + k) * 3 + i] = s2;
+        }
+      }
+    }
+    double* Ke = K ? K + (size_t)s * N * N : NULL;
+    double* Me = M ? M + (size_t)s * N * N : NULL;
+    /* the six nested test/trial loops of Algorithm 1, then the quadrature loop */
+    int n2 = (d == 3) ? n : 1;
+    for (int i1 = 0; i1 < n; ++i1)
+      for (int j1 = 0; j1 < n; ++j1)
+        for (int i2 = 0; i2 < n; ++i2)
+          for (int j2 = 0; j2 < n; ++j2)
+            for (int i3 = 0; i3 < n2; ++i3)
+              for (int j3 = 0; j3 < n2; ++j3) {
+                int a = i1 + n * (i2 + n * i3);
+                int b = j1 + n * (j2 + n * j3);
+                double mab = 0.0, kab = 0.0;
+                for (int k = 0; k < Q; ++k) {
+                  if (Me) {
+                    double r = rho ? rho[(size_t)e * Q + k] : 1.0;
+                    mab += phi[(size_t)a * Q + k] * phi[(size_t)b * Q + k] * W[k] * r;
+                  }
+                  if (Ke) {
+                    double dot = 0.0;
+                    for (int i = 0; i < d; ++i)
+                      dot += grad[((size_t)a * Q + k) * 3 + i] * grad[((size_t)b * Q + k) * 3 + i];
+                    kab += dot * W[k] * kappa[(size_t)e * Q + k];
+                  }
+                }
+                if (Me) Me[(size_t)a * N + b] = mab;
+                if (Ke) Ke[(size_t)a * N + b] = kab;
+              }
+  }
+  free(B); free(W); free(Ginv); free(phi); free(grad);
+  free_layout(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sum factorization: Algorithm 2 (Sec. 3.2, eqs. finalsum and bufferC).     */
+/* Each term of the integrand is a product of one factor per direction       */
+/* (value or derivative of the test and of the trial function) and a        */
+/* coefficient J^t at the quadrature point.  The mass has one term; the      */
+/* stiffness has d*d terms (alpha, beta) = (direction differentiated in the  */
+/* test function, in the trial function) with coefficient                    */
+/* |det G| kappa (G^{-1} G^{-T})_{alpha beta}.  Buffers follow Algorithm 2:  */
+/* D(i3,j3,k1,k2) sums over k3 with w_z, C(i2,i3,j2,j3,k1) over k2 with w_y, */
+/* A(a,b) over k1 with w_x.  In 2D the last-direction stage is the y stage.  */
+/* ------------------------------------------------------------------------ */
+static void sf_term(const layout* L, const elem1d* B, const double* coef,
+                    int sa[3], int sb[3], double* Dbuf, double* Cbuf, double* A) {
+  int n = L->n, q = L->q, N = L->N;
+  /* factor table of direction j for test (s=sa) or trial (s=sb) */
+#define FAC(j, s, r, k) ((s) ? B->der[j][(k) * n + (r)] : B->val[j][(k) * n + (r)])
+  if (L->d == 3) {
+    /* D(i3,j3,k1,k2) = sum_k3 Bz_i3 Bz_j3 w_z J */
+    for (int i3 = 0; i3 < n; ++i3)
+      for (int j3 = 0; j3 < n; ++j3)
+        for (int k1 = 0; k1 < q; ++k1)
+          for (int k2 = 0; k2 < q; ++k2) {
+            double acc = 0.0;
+            for (int k3 = 0; k3 < q; ++k3)
+              acc += FAC(2, sa[2], i3, k3) * FAC(2, sb[2], j3, k3) * B->w[2][k3] *
+                     coef[k1 + q * (k2 + q * k3)];
+            Dbuf[((i3 * n + j3) * q + k1) * q + k2] = acc;
+          }
+    /* C(i2,i3,j2,j3,k1) = sum_k2 By_i2 By_j2 D(i3,j3,k1,k2) w_y */
+    for (int i2 = 0; i2 < n; ++i2)
+      for (int j2 = 0; j2 < n; ++j2)
+        for (int i3 = 0; i3 < n; ++i3)
+          for (int j3 = 0; j3 < n; ++j3)
+            for (int k1 = 0; k1 < q; ++k1) {
+              double acc = 0.0;
+              for (int k2 = 0; k2 < q; ++k2)
+                acc += FAC(1, sa[1], i2, k2) * FAC(1, sb[1], j2, k2) *
+                       Dbuf[((i3 * n + j3) * q + k1) * q + k2] * B->w[1][k2];
+              Cbuf[(((i2 * n + i3) * n + j2) * n + j3) * q + k1] = acc;
+            }
+    /* A((i1,i2,i3),(j1,j2,j3)) += sum_k1 Bx_i1 Bx_j1 C(i2,i3,j2,j3,k1) w_x */
+    for (int i1 = 0; i1 < n; ++i1)
+      for (int j1 = 0; j1 < n; ++j1)
+        for (int i2 = 0; i2 < n; ++i2)
+          for (int j2 = 0; j2 < n; ++j2)
+            for (int i3 = 0; i3 < n; ++i3)
+              for (int j3 = 0; j3 < n; ++j3) {
+                double acc = 0.0;
+                for (int k1 = 0; k1 < q; ++k1)
+                  acc += FAC(0, sa[0], i1, k1) * FAC(0, sb[0], j1, k1) *
+                         Cbuf[(((i2 * n + i3) * n + j2) * n + j3) * q + k1] * B->w[0][k1];
+                int a = i1 + n * (i2 + n * i3);
+                int b = j1 + n * (j2 + n * j3);
+                A[(size_t)a * N + b] += acc;
+              }
+  } else {
+    /* D(i2,j2,k1) = sum_k2 By_i2 By_j2 w_y J */
+    for (int i2 = 0; i2 < n; ++i2)
+      for (int j2 = 0; j2 < n; ++j2)
+        for (int k1 = 0; k1 < q; ++k1) {
+          double acc = 0.0;
+          for (int k2 = 0; k2 < q; ++k2)
+            acc += FAC(1, sa[1], i2, k2) * FAC(1, sb[1], j2, k2) * B->w[1][k2] *
+                   coef[k1 + q * k2];
+          Dbuf[(i2 * n + j2) * q + k1] = acc;
+        }
+    /* A((i1,i2),(j1,j2)) += sum_k1 Bx_i1 Bx_j1 D(i2,j2,k1) w_x */
+    for (int i1 = 0; i1 < n; ++i1)
+      for (int j1 = 0; j1 < n; ++j1)
+        for (int i2 = 0; i2 < n; ++i2)
+          for (int j2 = 0; j2 < n; ++j2) {
+            double acc = 0.0;
+            for (int k1 = 0; k1 < q; ++k1)
+              acc += FAC(0, sa[0], i1, k1) * FAC(0, sb[0], j1, k1) *
+                     Dbuf[(i2 * n + j2) * q + k1] * B->w[0][k1];
+            A[(size_t)(i1 + n * i2) * N + (j1 + n * j2)] += acc;
+          }
+  }
+#undef FAC
+}
+
+int ora_sumfact(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+                const double* kappa, const double* rho, const double* G,
+                double* K, double* M) {
+  layout L;
+  if (make_layout(pt, &L)) { free_layout(&L); return -1; }
+  if (K && !kappa) { free_layout(&L); return -1; }
+  int d = L.d, n = L.n, q = L.q, N = L.N, Q = L.Q;
+  int64_t E = n_elements(&L);
+  elem1d* B = (elem1d*)malloc(sizeof(elem1d));
+  double* coef = (double*)malloc(sizeof(double) * Q);
+  double* Dbuf = (double*)malloc(sizeof(double) * (size_t)n * n * q * q);
+  double* Cbuf = (double*)malloc(sizeof(double) * (size_t)n * n * n * n * q);
+  for (int64_t s = 0; s < n_sel; ++s) {
+    int64_t e = elems[s];
+    if (e < 0 || e >= E) { free(B); free(coef); free(Dbuf); free(Cbuf); free_layout(&L); return -1; }
+    int ek[3];
+    split_elem(&L, e, ek);
+    element_1d(pt, &L, ek, B);
+    /* J(x^n) of eq. 10 without the weights, which Algorithm 2 applies one
+     * direction per stage. */
+    double* Ke = K ? K + (size_t)s * N * N : NULL;
+    double* Me = M ? M + (size_t)s * N * N : NULL;
+    if (Me) {
+      memset(Me, 0, sizeof(double) * (size_t)N * N);
+      for (int k = 0; k < Q; ++k) {
+        double Gid[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, G2[4] = {1, 0, 0, 1}, tmp[9];
+        const double* Gq = G ? G + ((size_t)e * Q + k) * d * d : (d == 3 ? Gid : G2);
+        double det = geom_inverse(d, Gq, tmp);
+        coef[k] = det * (rho ? rho[(size_t)e * Q + k] : 1.0);
+      }
+      int sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
+      sf_term(&L, B, coef, sa, sb, Dbuf, Cbuf, Me);
+    }
+    if (Ke) {
+      memset(Ke, 0, sizeof(double) * (size_t)N * N);
+      for (int al = 0; al < d; ++al)
+        for (int be = 0; be < d; ++be) {
+          for (int k = 0; k < Q; ++k) {
+            double Gid[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, G2[4] = {1, 0, 0, 1}, Gi[9];
+            const double* Gq = G ? G + ((size_t)e * Q + k) * d * d : (d == 3 ? Gid : G2);
+            double det = geom_inverse(d, Gq, Gi);
+            double gg = 0.0; /* (G^{-1} G^{-T})_{al be} = sum_l Ginv[al][l] Ginv[be][l] */
+            for (int l = 0; l < d; ++l) gg += Gi[al * d + l] * Gi[be * d + l];
+            coef[k] = det * kappa[(size_t)e * Q + k] * gg;
+          }
+          int sa[3] = {al == 0, al == 1, al == 2};
+          int sb[3] = {be == 0, be == 1, be == 2};
+          sf_term(&L, B, coef, sa, sb, Dbuf, Cbuf, Ke);
+        }
+    }
+  }
+  free(B); free(coef); free(Dbuf); free(Cbuf);
+  free_layout(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dof map (Remark on K^Delta_alpha, Sec. 3.1; ordering x fastest).          */
+/* ------------------------------------------------------------------------ */
+int ora_dofmap(const ora_patch* pt, const int64_t* elems, int64_t n_sel, int32_t* dof) {
+  layout L;
+  if (make_layout(pt, &L)) { free_layout(&L); return -1; }
+  int64_t E = n_elements(&L);
+  int64_t nf[3] = {1, 1, 1};
+  for (int k = 0; k < L.d; ++k) nf[k] = pt->m[k] - pt->p - 1;
+  for (int64_t s = 0; s < n_sel; ++s) {
+    int64_t e = elems[s];
+    if (e < 0 || e >= E) { free_layout(&L); return -1; }
+    int ek[3];
+    split_elem(&L, e, ek);
+    for (int a = 0; a < L.N; ++a) {
+      int aa[3];
+      split_local(&L, a, aa);
+      int64_t g = 0, stride = 1;
+      for (int k = 0; k < L.d; ++k) {
+        g += (int64_t)(L.spans[k][ek[k]] - L.p + aa[k]) * stride;
+        stride *= nf[k];
+      }
+      dof[(size_t)s * L.N + a] = (int32_t)g;
+    }
+  }
+  free_layout(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of J(kappa) = u^T K(kappa) v (not in the paper): J is linear in    */
+/* kappa, J = sum_q kappa_q g_q, so dJ/dkappa_q = g_q.                        */
+/* ------------------------------------------------------------------------ */
+int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+                const double* kappa, const double* G, const double* u,
+                const double* v, double* g, double* J) {
+  layout L;
+  if (make_layout(pt, &L)) { free_layout(&L); return -1; }
+  int d = L.d, n = L.n, N = L.N, Q = L.Q;
+  int64_t E = n_elements(&L);
+  elem1d* B = (elem1d*)malloc(sizeof(elem1d));
+  double* W = (double*)malloc(sizeof(double) * Q);
+  double* Ginv = (double*)malloc(sizeof(double) * Q * 9);
+  int32_t* dof = (int32_t*)malloc(sizeof(int32_t) * N);
+  double Jsum = 0.0;
+  for (int64_t s = 0; s < n_sel; ++s) {
+    int64_t e = elems[s];
+    if (e < 0 || e >= E) { free(B); free(W); free(Ginv); free(dof); free_layout(&L); return -1; }
+    int ek[3];
+    split_elem(&L, e, ek);
+    element_1d(pt, &L, ek, B);
+    element_geometry(&L, e, B, G, W, Ginv);
+    ora_dofmap(pt, &e, 1, dof);
+    for (int k = 0; k < Q; ++k) {
+      int kk[3];
+      split_qp(&L, k, kk);
+      double gu[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+      for (int a = 0; a < N; ++a) {
+        int aa[3];
+        split_local(&L, a, aa);
+        for (int i = 0; i < d; ++i) {
+          double f = 1.0;
+          for (int j = 0; j < d; ++j)
+            f *= (i == j) ? B->der[j][kk[j] * n + aa[j]] : B->val[j][kk[j] * n + aa[j]];
+          gu[i] += u[dof[a]] * f;
+          gv[i] += v[dof[a]] * f;
+        }
+      }
+      const double* Gi = Ginv + (size_t)k * d * d;
+      double dot = 0.0;
+      for (int i = 0; i < d; ++i) {
+        double pu = 0.0, pv = 0.0;
+        for (int j = 0; j < d; ++j) { pu += Gi[j * d + i] * gu[j]; pv += Gi[j * d + i] * gv[j]; }
+        dot += pu * pv;
+      }
+      double gq = W[k] * dot;
+      g[(size_t)s * Q + k] = gq;
+      if (kappa) Jsum += kappa[(size_t)e * Q + k] * gq;
+    }
+  }
+  if (J) *J = Jsum;
+  free(B); free(W); free(Ginv); free(dof);
+  free_layout(&L);
+  return 0;
+}

@@ -1,0 +1,100 @@
+/*
+ * iga_oracle.h -- plain, slow, FP64 CPU oracle for IGA-FEM element-matrix
+ * integration over tensor-product B-spline bases (arxiv 2207.00280).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library and must never be used as a
+ * fallback for it.
+ *
+ * Conventions (0-based everywhere, x fastest in every multi-index):
+ *   knots t[0..m-1] per direction, degree p, number of functions m-p-1;
+ *   elements per direction = non-empty knot spans [t_s, t_{s+1});
+ *   element e = e1 + K1*(e2 + K2*e3);
+ *   local function a = a1 + n*(a2 + n*a3), n = p+1, global 1D index s-p+a_k;
+ *   quadrature point k = k1 + q*(k2 + q*k3);
+ *   kappa[E][Q], rho[E][Q], G[E][Q][d][d] with G[i][j] = dx_i/dxi_j (row-major);
+ *   element matrices [n_sel][N][N] row-major, N = n^d.
+ *
+ * Every function cites the passage of the paper it follows.  Items with no
+ * counterpart in the paper (derivatives, stiffness, the adjoint) are written
+ * from their textbook definitions and say so.
+ */
+#ifndef IGA_ORACLE_H
+#define IGA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Gauss--Legendre rule on [-1,1] by Golub--Welsch: eigen-decomposition of the
+ * symmetric tridiagonal Jacobi matrix of the Legendre recurrence, done with
+ * cyclic Jacobi rotations.  Nodes ascending.  Returns 0 on success. */
+int ora_gauss_legendre(int q, double* x, double* w);
+
+/* B_{i;p}(xi), literally recursive Cox--de Boor (Sec. 2.3, eqs. cox1/cox2;
+ * 0/0 := 0). */
+double ora_bspline(const double* t, int i, int p, double xi);
+
+/* dB_{i;p}/dxi by the de Boor derivative identity (not in the paper). */
+double ora_bspline_deriv(const double* t, int i, int p, double xi);
+
+/* Non-empty knot spans s (t_s < t_{s+1}, s = p..m-p-2) -> spans[], returns
+ * their count (Sec. 2.3 knot vector; Sec. 3.1 element decomposition). */
+int ora_spans(const double* t, int m, int p, int* spans);
+
+/* One direction of one element: mapped Gauss nodes xi[q], mapped weights w[q]
+ * (reference weight times half the span length), values val[q][n] and
+ * derivatives der[q][n] of B_{s-p+r}, r = 0..p, by the recursive functions. */
+void ora_basis_1d(const double* t, int p, int s, int q, double* xi, double* w,
+                  double* val, double* der);
+
+/* Description of one patch for the element-matrix routines. */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int p;                   /* degree, all directions */
+  int q;                   /* Gauss points per direction */
+  int m[3];                /* knots per direction */
+  const double* t[3];      /* knot vectors */
+} ora_patch;
+
+/* Classical integration (Sec. 3.2, Algorithm 1; element integral eq. 10),
+ * extended with the variable-coefficient stiffness:
+ *   M_ab = sum_q w_q |det G_q| rho_q phi_a phi_b,
+ *   K_ab = sum_q w_q |det G_q| kappa_q (G_q^{-T} grad phi_a).(G_q^{-T} grad phi_b).
+ * elems[n_sel] are global element ids; kappa/rho/G are indexed by global id.
+ * rho or G may be NULL (1 / identity); K or M may be NULL (skip).
+ * Returns 0, or -1 on bad arguments. */
+int ora_classical(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+                  const double* kappa, const double* rho, const double* G,
+                  double* K, double* M);
+
+/* Sum factorization (Sec. 3.2, Algorithm 2; eqs. finalsum/bufferC): per
+ * element and per derivative term, contract the last direction first, then
+ * the middle, then x, with per-direction weights applied in their own stage.
+ * Same arguments and result as ora_classical (up to rounding order). */
+int ora_sumfact(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+                const double* kappa, const double* rho, const double* G,
+                double* K, double* M);
+
+/* Global dof of each local function of each selected element (Remark on the
+ * support set K^Delta_alpha, Sec. 3.1): dof = sum_k (s_k - p + a_k) * stride_k,
+ * stride = 1, n_1, n_1 n_2 with n_k = m_k - p - 1. */
+int ora_dofmap(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+               int32_t* dof);
+
+/* Adjoint of J(kappa) = u^T K(kappa) v (not in the paper): for each selected
+ * element and quadrature point
+ *   g_q = w_q |det G_q| (G_q^{-T} grad u)(x_q) . (G_q^{-T} grad v)(x_q),
+ * with grad u = sum_a u[dof(e,a)] grad phi_a.  Writes g[n_sel][Q] and
+ * *J = sum over the selected elements of sum_q kappa_q g_q (if J != NULL). */
+int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
+                const double* kappa, const double* G, const double* u,
+                const double* v, double* g, double* J);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
