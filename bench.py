@@ -1,0 +1,485 @@
+#!/usr/bin/env python
+"""Benchmark: batched IGA-FEM element-matrix integration on GB300.
+
+Default workload: 3D, p=3, 32^3 elements, 4^3 Gauss points, lognormal(0,0.5)
+kappa (seed 2207), identity geometry, FP64 sum factorization producing the
+stiffness and mass element matrices (64x64 each) and the dof map.  A step is
+one iga_integrate call (Cox--de Boor tables, dof map, element matrices) with
+inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--method sumfact|classical] [--precision fp64|fp32|bf16]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D p=3 element matrices/s, sumfact vs classical, FP64 vs FP32/BF16 at stated err"
+UNIT = "element matrices/s (one K_e and one M_e per element)"
+L2_BYTES = 129 * 1024 * 1024
+
+# FP64 issue rate of the GB300 CUDA cores used for the FP64 roofline: DFMA per
+# SM per clock (2 flops each).  See the design doc (roofline section) for the
+# measurement and the derivation of the peak.
+DFMA_PER_SM_CLK = 2.0
+N_SM = 152
+
+
+def flops_per_element(dim, p, q, stiffness, mass, general_geometry):
+    """Algorithmic flops of sum factorization per element (multiply-add = 2),
+    last stage over the symmetric half S = N(N+1)/2.  General geometry: all d^2
+    stiffness terms; identity geometry: the d diagonal terms only (the
+    off-diagonal coefficients vanish identically)."""
+    n, N = p + 1, (p + 1) ** dim
+    S = N * (N + 1) // 2
+    terms = dim * dim if general_geometry else dim
+    f = 0
+    if dim == 3:
+        if stiffness:
+            f += 2 * terms * (n * n * q ** 3 + n ** 4 * q * q) + (8 if general_geometry else 4) * q * S
+        if mass:
+            f += 2 * n * n * q ** 3 + 2 * n ** 4 * q * q + 2 * q * S
+    else:
+        if stiffness:
+            f += 2 * terms * n * n * q * q + (8 if general_geometry else 4) * q * S
+        if mass:
+            f += 2 * n * n * q * q + 2 * q * S
+    return f
+
+
+def classical_flops_per_element(dim, p, q, stiffness, mass):
+    N, Q = (p + 1) ** dim, q ** dim
+    S = N * (N + 1) // 2
+    return 2 * S * Q * ((dim if stiffness else 0) + (1 if mass else 0))
+
+
+def bytes_per_element(dim, p, q, esize, stiffness, mass, general_geometry, dof=True):
+    N, Q = (p + 1) ** dim, q ** dim
+    b = N * N * esize * (int(stiffness) + int(mass)) + 8 * Q
+    if general_geometry:
+        b += 8 * Q * dim * dim
+    if dof:
+        b += 4 * N
+    return b
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in a thread."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for_smi(local):
+    """nvidia-smi -i accepts a UUID; fall back to the local index."""
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(local).uuid
+        u = str(u)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline_oracle(workload, budget_s=12.0, method="sumfact", max_elems=None):
+    """Time the FP64 oracle (as it stands, one core) on a bounded sample of the
+    workload's elements; returns elements/s and a description."""
+    import numpy as np
+    import oracle
+    from paper_2207_00280_gb300 import workloads as wl
+    W = wl.WORKLOADS[workload]
+    sp = W.spec
+    P = oracle.Patch(sp.knots, sp.p, sp.q)
+    kappa = W.kappa()
+    G = W.jacobian()
+    fn = P.sumfact if method == "sumfact" else P.classical
+    rng = np.random.default_rng(2207)
+    order = rng.permutation(sp.E)
+    done, t0, chunk = 0, time.perf_counter(), 64
+    limit = max_elems or sp.E
+    while done < limit and time.perf_counter() - t0 < budget_s:
+        el = order[done:done + chunk]
+        fn(el, kappa=kappa, G=G, stiffness=True, mass=True)
+        done += len(el)
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2207_00280_gb300 import workloads as wl
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W = wl.WORKLOADS[args.workload]
+    sp = W.spec
+    G = W.jacobian()
+    general = G is not None
+    mass = not general   # the curved workload integrates the stiffness only
+    plan = IgaPlan(Patch(sp.knots, sp.p, sp.q), method=args.method, precision=args.precision,
+                   mass=mass, stiffness=True, blocking=False, profile=True)
+    kappa_h = torch.from_numpy(W.kappa())
+    kappa = kappa_h.to(dev)
+    jac = torch.from_numpy(np.ascontiguousarray(G)).reshape(-1).to(dev) if general else None
+    K, M, D = plan.empty_outputs(device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.integrate(kappa=kappa, jac=jac, K=K, M=M, dof=D, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    plan.profile_read()  # reset the kernel counters
+
+    sampler = ClockSampler(gpu_id_for_smi(local))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))          # L2 flush, outside the step's events
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms, launches = plan.profile_read()
+    total_ms = max_over_ranks(sum(step_ms), ws)
+    E = sp.E
+    value = ws * E * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the element-matrix kernel)
+    esize = 8 if args.precision == "fp64" else 4
+    peaks, peak_src = measured_peaks()
+    launch_ms = kern_ms / max(1, launches)
+    if args.method == "sumfact":
+        f_el = flops_per_element(3 if len(sp.knots) == 3 else 2, sp.p, sp.q, True, mass, general)
+    else:
+        f_el = classical_flops_per_element(len(sp.knots), sp.p, sp.q, True, mass)
+    b_el = bytes_per_element(len(sp.knots), sp.p, sp.q, esize, True, mass, general, dof=False)
+    if args.precision == "fp64":
+        peak_tf = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = f_el * E / (launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
+                "traffic": None,
+                "flop_per_element": f_el, "elements_per_launch": E,
+                "launch_ms": round(launch_ms, 4),
+                "peak_source": f"FP64 CUDA cores: {N_SM} SMs x {DFMA_PER_SM_CLK:g} DFMA/clk x 2 x "
+                               f"{peaks.get('sm_max_mhz', 2070.0):g} MHz",
+                "hbm_frac": round(b_el * E / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src}
+    else:
+        ach = b_el * E / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None,
+                "bytes_per_element": b_el, "elements_per_launch": E,
+                "launch_ms": round(launch_ms, 4), "peak_source": peak_src}
+    tr = traffic_from_profiles(args, esize)
+    if tr is not None:
+        roof["traffic"] = tr
+
+    # classical FP64 on the same GPU, for the speedup of the chosen form
+    forms = {}
+    if args.compare and args.method == "sumfact" and rank == 0:
+        cplan = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="classical", precision="fp64",
+                        mass=mass, stiffness=True, blocking=False)
+        Kc, Mc, _ = cplan.empty_outputs(device=dev, dof=False)
+        for _ in range(2):
+            cplan.integrate(kappa=kappa, jac=jac, K=Kc, M=Mc, stream=stream)
+        ts = []
+        for _ in range(3):
+            flush.fill_(2.0)
+            a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            cplan.integrate(kappa=kappa, jac=jac, K=Kc, M=Mc, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        cms = statistics.median(ts)
+        forms["classical_fp64"] = {"ms_per_step": round(cms, 4), "value": round(E / (cms * 1e-3), 1)}
+        forms[f"{args.method}_{args.precision}"] = {"ms_per_step": round(total_ms / args.steps, 4),
+                                                   "value": round(E / (total_ms / args.steps * 1e-3), 1)}
+        forms["speedup_vs_classical_fp64"] = round(cms / (total_ms / args.steps), 3)
+        del Kc, Mc
+        cplan.close()
+
+    # end to end through the public API with host buffers: H2D of kappa (and the
+    # Jacobian), the integration, D2H of the element matrices and the dof map.
+    e2e = None
+    if args.e2e:
+        kap_pin = kappa_h.pin_memory()
+        jac_pin = torch.from_numpy(np.ascontiguousarray(G)).reshape(-1).pin_memory() if general else None
+        outs_h = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() if t is not None else None
+                  for t in (K, M, D)]
+        h2d = kap_pin.numel() * 8 + (jac_pin.numel() * 8 if general else 0)
+        d2h = sum(t.numel() * t.element_size() for t in (K, M, D) if t is not None)
+        n_e2e = max(2, min(args.steps, 5))
+
+        def e2e_step():
+            kappa.copy_(kap_pin, non_blocking=True)
+            if general:
+                jac.copy_(jac_pin, non_blocking=True)
+            step()
+            for th, td in zip(outs_h, (K, M, D)):
+                if td is not None:
+                    th.copy_(td, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        b.record(stream)
+        b.synchronize()
+        barrier(ws)
+        e_ms = max_over_ranks(a.elapsed_time(b), ws)
+        e2e = {"value": round(ws * E * n_e2e / (e_ms * 1e-3), 1), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": n_e2e,
+               "ms_per_step": round(e_ms / n_e2e, 4)}
+
+    cpu = None
+    if args.cpu_baseline and rank == 0 and ws == 1:
+        rate, done, dt = cpu_baseline_oracle(args.workload, budget_s=args.cpu_seconds,
+                                             method=args.method if args.method == "classical" else "sumfact")
+        cpu = {"value": round(rate, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} of {E} elements (seeded permutation), oracle "
+                         f"{'Algorithm 2 sum factorization' if args.method == 'sumfact' else 'Algorithm 1 classical'}"
+                         f", FP64, one thread, {dt:.1f} s"}
+
+    n_kernels_per_step = 3  # basis tables, dof map, element matrices
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic (seeded lognormal kappa, open uniform knots)",
+        "config": {"workload": args.workload, "dim": len(sp.knots), "degree": sp.p,
+                   "elements": E, "gauss_per_dir": sp.q, "method": args.method,
+                   "precision": args.precision, "matrices": "stiffness+mass" if mass else "stiffness",
+                   "geometry": "curved" if general else "identity",
+                   "l2": "flushed before every step (256 MiB write outside the step's events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": n_kernels_per_step * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "forms": forms or None,
+        "wall_s_timed_region": round(t_wall, 4),
+        "kernel_ms_per_launch": round(launch_ms, 4),
+    }
+    plan.close()
+    return line
+
+
+def traffic_from_profiles(args, esize):
+    """DRAM bytes per launch of the element kernel from a committed ncu summary,
+    if its recorded source hash matches the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    key = f"{args.workload}:{args.method}:{args.precision}"
+    ent = tab.get(key)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2207_00280_gb300", "csrc", ent["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    if h != ent.get("sha"):
+        return None
+    return ent["dram_bytes_per_launch"]
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle timed on the host cores, each step a
+    bounded sample of the workload's elements."""
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    from paper_2207_00280_gb300 import workloads as wl
+    W = wl.WORKLOADS[args.workload]
+    sp = W.spec
+    P = oracle.Patch(sp.knots, sp.p, sp.q)
+    kappa = W.kappa()
+    G = W.jacobian()
+    mass = G is None
+    fn = P.sumfact if args.method == "sumfact" else P.classical
+    per_step = args.ref_elements
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        fn(rng.choice(sp.E, size=min(8, sp.E), replace=False), kappa=kappa, G=G, mass=mass)
+    times = []
+    for _ in range(args.steps):
+        el = rng.choice(sp.E, size=min(per_step, sp.E), replace=False)
+        t0 = time.perf_counter()
+        fn(el, kappa=kappa, G=G, mass=mass)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    rate = per_step * args.steps / tot
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(rate, 2), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded lognormal kappa, open uniform knots)",
+        "config": {"workload": args.workload, "method": args.method, "precision": "fp64",
+                   "sample_elements_per_step": per_step, "elements": sp.E},
+        "cpu_baseline": {"value": round(rate, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} random elements per step of {sp.E}, FP64 oracle "
+                                   f"({'Algorithm 2' if args.method == 'sumfact' else 'Algorithm 1'}), one thread"},
+        "e2e": {"value": round(rate, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d_p3_32")
+    ap.add_argument("--method", default="sumfact", choices=["sumfact", "classical"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-elements", type=int, default=512)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+
+    ws, rank, local = dist_setup()
+    line = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * iga.h -- C ABI of the GB300 (sm_103a) library for batched integration of
+ * IGA-FEM element matrices over tensor-product B-spline bases
+ * (arxiv 2207.00280, "A study of efficient concurrent integration methods of
+ * B-Spline basis functions in IGA-FEM").
+ *
+ * What is computed (per element E of a patch, N = (p+1)^d local functions):
+ *   mass       M_ab = sum_q w_q |det G_q| rho_q   phi_a(x_q) phi_b(x_q)
+ *   stiffness  K_ab = sum_q w_q |det G_q| kappa_q (G_q^{-T} grad phi_a).(G_q^{-T} grad phi_b)
+ * The mass is the element Gram matrix of Sec. 3.1 (eqs. 88 and 10); the
+ * stiffness is the diffusion term of the weak form of Sec. 2.2 (eq. Euler)
+ * with a coefficient per quadrature point (not integrated in the paper).
+ * phi_a are tensor products of 1D B-splines (Sec. 2.3, eqs. cox1, cox2,
+ * basis_construction) on open knot vectors (eq. knot_vector).  The quadrature
+ * is Gauss--Legendre with q points per direction ("a proper exact
+ * quadrature", Sec. 3.1).  Two methods give the same sums up to rounding:
+ * the classical loop (Sec. 3.2, Algorithm 1) and sum factorization
+ * (Sec. 3.2, Algorithm 2, eqs. finalsum and bufferC).
+ *
+ * Conventions (all indices 0-based, x fastest in every multi-index):
+ *   element   e = e1 + K1*(e2 + K2*e3), elements = non-empty knot spans;
+ *   local fn  a = a1 + n*(a2 + n*a3), n = p+1 (the support set of the Remark
+ *             in Sec. 3.1, global 1D index s_k - p + a_k for span s_k);
+ *   global dof = i1 + n1*(i2 + n2*i3), n_k = functions in direction k,
+ *             patches concatenated in batch order;
+ *   quad pt   k = k1 + q*(k2 + q*k3);
+ *   kappa, rho: [n_qp] doubles, element-major: index = qp_offset(patch) +
+ *             e*Q + k, Q = q^d;
+ *   jac:      [n_qp][d][d] doubles, jac[..][i][j] = d x_i / d xi_j with xi
+ *             the knot (parametric) coordinate; |det| is the J(x^n) of eq. 10;
+ *   K_out, M_out: per patch [E][N][N] row-major, patches concatenated
+ *             (offsets in iga_plan_info.mat_offset), double for IGA_FP64,
+ *             float for IGA_FP32 and IGA_BF16;
+ *   dof_out:  per patch [E][N] int32, concatenated (iga_plan_info.dofmap_offset).
+ *
+ * Ownership: every pointer passed to iga_integrate/iga_integrate_backward is
+ * owned by the caller and must be device memory of the device that was
+ * current at iga_plan (no copies are made).  The plan owns its device tables
+ * and the arrays that iga_plan_info points to; iga_destroy frees them.
+ *
+ * Errors: argument and knot errors are returned synchronously and nothing is
+ * launched.  Device-side errors set a plan-owned error word; with
+ * opts.blocking = 1 the call synchronizes the stream and returns it, otherwise
+ * it is sticky and reported by the next call or by iga_destroy.  No device
+ * code traps or asserts; device waits are bounded and end in IGA_ERR_TIMEOUT.
+ */
+#ifndef IGA_H
+#define IGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iga_plan_s* iga_plan_t;
+
+typedef enum {
+  IGA_OK = 0,
+  IGA_ERR_ARG = 1,          /* null/negative/out-of-range argument */
+  IGA_ERR_KNOTS = 2,        /* knot vector not open, decreasing, or multiplicity > p */
+  IGA_ERR_UNSUPPORTED = 3,  /* valid but not built (degree, Gauss order, mixed dims) */
+  IGA_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  IGA_ERR_OOM = 5,          /* device allocation failed */
+  IGA_ERR_TIMEOUT = 6,      /* a bounded device wait expired */
+  IGA_ERR_DEVICE = 7        /* the device reported an inconsistency (bad work item) */
+} iga_status;
+
+enum { IGA_CLASSICAL = 0, IGA_SUMFACT = 1 };
+enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_BF16 = 2 };
+enum { IGA_MASS = 1, IGA_STIFF = 2 };
+
+/* One tensor-product patch.  Knot vectors are host arrays, copied by
+ * iga_plan.  Each must be non-decreasing and open (first and last p+1 knots
+ * equal) with interior multiplicity <= p (Sec. 2.3, eq. knot_vector).
+ * 1 <= degree <= 5 in 3D and <= 8 in 2D; n_gauss in {degree+1, degree+2}. */
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int degree;               /* p, the same in every direction */
+  int n_gauss;              /* q, Gauss points per direction */
+  int n_knots[3];           /* knots per direction (dim entries used) */
+  const double* knots[3];   /* host pointers */
+} iga_patch_desc;
+
+typedef struct {
+  int method;     /* IGA_CLASSICAL or IGA_SUMFACT */
+  int precision;  /* IGA_FP64, IGA_FP32 or IGA_BF16 (sum factorization only) */
+  int matrices;   /* bitmask of IGA_MASS | IGA_STIFF */
+  int schedule;   /* 0 = automatic (autotuned), else a schedule id (iga_schedule_*) */
+  int blocking;   /* 1 = synchronize the stream and return the device status */
+  int profile;    /* 1 = record CUDA events around the element-matrix kernels */
+} iga_plan_opts;
+
+typedef struct {
+  int64_t n_elements;       /* all patches */
+  int64_t n_qp;             /* length of kappa / rho, and of jac in d*d units */
+  int64_t n_dofs;           /* length of u, v */
+  int64_t n_mat_entries;    /* length of K_out / M_out */
+  int64_t n_dofmap_entries; /* length of dof_out */
+  int64_t n_table_entries;  /* length of the output of iga_basis_tables */
+  int dim;
+  int n_patches;
+  int local_n;              /* N of the first patch (all patches if uniform) */
+  /* per-patch arrays of n_patches+1 prefix offsets, owned by the plan */
+  const int64_t* elem_offset;
+  const int64_t* qp_offset;
+  const int64_t* dof_offset;
+  const int64_t* mat_offset;
+  const int64_t* dofmap_offset;
+} iga_plan_info;
+
+/* Validate the patches, build the element spans, Gauss rules and dof strides
+ * on the host, allocate the plan's device tables on the current device.
+ * A batch (n_patches > 1) may mix degrees and sizes but not dimensions.
+ * info_out may be NULL.  Returns IGA_OK and *out, or an error and *out = NULL. */
+int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_patches,
+             const iga_plan_opts* opts, iga_plan_info* info_out);
+
+/* Integrate every element of every patch on `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream): the Cox--de Boor basis/derivative tables,
+ * the dof map, then mass and/or stiffness by the plan's method.
+ *   kappa  [n_qp] or NULL (= 1); required values > 0 are not checked.
+ *   rho    [n_qp] or NULL (= 1); used by the mass only.
+ *   jac    [n_qp][d][d] or NULL (= identity).
+ *   K_out, M_out: NULL skips that matrix; must be non-NULL if the plan's
+ *          `matrices` includes it and the other is NULL.
+ *   dof_out: [n_dofmap_entries] or NULL (skip). */
+int iga_integrate(iga_plan_t plan, const double* kappa, const double* rho,
+                  const double* jac, void* K_out, void* M_out, int32_t* dof_out,
+                  void* cuda_stream);
+
+/* Matrix-free adjoint of J(kappa) = u^T K(kappa) v (not in the paper):
+ *   grad_kappa[k] = dJ/dkappa_k = w_k |det G_k| (G_k^{-T} grad u).(G_k^{-T} grad v)
+ * at every quadrature point, computed by sum-factorized interpolation of u and
+ * v from the basis tables (no element matrix is formed), and
+ *   J_out = sum_k kappa_k grad_kappa[k]   (deterministic fixed-order reduction).
+ * u, v: [n_dofs] global vectors; double for IGA_FP64 plans, float otherwise.
+ * grad_kappa: [n_qp], same dtype as u.  J_out: one double, may be NULL.
+ * kappa may be NULL only if J_out is NULL.  jac as for iga_integrate. */
+int iga_integrate_backward(iga_plan_t plan, const double* kappa, const double* jac,
+                           const void* u, const void* v, void* grad_kappa,
+                           double* J_out, void* cuda_stream);
+
+/* Evaluate the 1D basis tables (Sec. 2.3, eqs. cox1/cox2; derivatives by the
+ * de Boor identity) into `out` (device, n_table_entries doubles) on
+ * `cuda_stream`.  Order: patches, then directions, then elements of that
+ * direction; one record per element: val[q][p+1], der[q][p+1] of the p+1
+ * functions non-zero on the element at its Gauss points, then w[q], the Gauss
+ * weights times half the element length.  iga_integrate computes the same
+ * tables internally; this entry exposes them for inspection. */
+int iga_basis_tables(iga_plan_t plan, double* out, void* cuda_stream);
+
+/* With opts.profile = 1: synchronize on the last recorded event and return
+ * the summed device time (ms) of the element-matrix kernel launches since the
+ * previous call, timed by CUDA events recorded on the caller's stream
+ * immediately before and after them, and the number of such launches; then
+ * reset the counters.  Returns IGA_ERR_ARG if profiling is off. */
+int iga_profile_read(iga_plan_t plan, double* kernel_ms, int64_t* launches);
+
+/* Free the plan and its device memory; NULL-safe.  Returns the sticky device
+ * status of the plan (IGA_OK if none). */
+int iga_destroy(iga_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* iga_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA_H */

@@ -1,0 +1,408 @@
+// iga_capi.cu -- host side of the C ABI declared in include/iga.h: argument
+// and knot validation, element spans, Gauss--Legendre rules, plan layout,
+// device tables and kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "iga_internal.h"
+
+using namespace iga;
+
+struct iga_plan_s {
+  int device = 0;
+  iga_plan_opts opts{};
+  int dim = 0;
+  int n_patches = 0;
+  std::vector<PatchDev> ph;          // host copy of the patch descriptions
+  std::vector<std::vector<int>> spans_h;  // [patch*3 + k]
+  PatchDev* d_patches = nullptr;
+  double* d_knots = nullptr;
+  int* d_spans = nullptr;
+  double* d_gauss = nullptr;
+  double* d_tables = nullptr;
+  TableJob* d_jobs = nullptr;
+  int n_jobs = 0;
+  int* d_err = nullptr;
+  int sticky = IGA_OK;
+  // profiling: event pairs around the element-matrix kernels
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  size_t prof_used = 0;
+  int64_t prof_launches = 0;
+  std::vector<int64_t> elem_off, qp_off, dof_off, mat_off, dofmap_off;
+  iga_plan_info info{};
+};
+
+namespace {
+
+bool g_log = false;
+
+void log_msg(const char* msg) {
+  if (g_log) fprintf(stderr, "[iga] %s\n", msg);
+}
+
+// Gauss--Legendre on [-1,1] by Newton's method on the Legendre polynomial
+// P_q (three-term recurrence (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1});
+// weight 2 / ((1 - x^2) P_q'(x)^2).  Symmetric nodes are mirrored exactly.
+void gauss_legendre_newton(int q, double* x, double* w) {
+  for (int i = 0; i < (q + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < q; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) { p1 = z; p0 = 1.0; }
+      dp = q * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    // final derivative at the converged node
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < q; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) { p1 = z; p0 = 1.0; }
+      dp = q * (z * p1 - p0) / (z * z - 1.0);
+    }
+    double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[q - 1 - i] = z;   // z > 0 for the first half: largest nodes first
+    x[i] = -z;
+    w[i] = w[q - 1 - i] = wi;
+  }
+  if (q % 2 == 1) x[q / 2] = 0.0;
+}
+
+int validate_knots(const double* t, int m, int p) {
+  if (!t || m < 2 * p + 2) return IGA_ERR_KNOTS;
+  for (int i = 0; i < m; ++i)
+    if (!std::isfinite(t[i])) return IGA_ERR_KNOTS;
+  for (int i = 1; i < m; ++i)
+    if (t[i] < t[i - 1]) return IGA_ERR_KNOTS;
+  for (int i = 1; i <= p; ++i)
+    if (t[i] != t[0] || t[m - 1 - i] != t[m - 1]) return IGA_ERR_KNOTS;
+  if (!(t[m - 1] > t[0])) return IGA_ERR_KNOTS;
+  // open: exactly p+1 repeated end knots; interior multiplicity <= p
+  if (t[p + 1] == t[0] || t[m - p - 2] == t[m - 1]) return IGA_ERR_KNOTS;
+  int run = 1;
+  for (int i = p + 2; i < m - p - 1; ++i) {
+    run = (t[i] == t[i - 1]) ? run + 1 : 1;
+    if (run > p) return IGA_ERR_KNOTS;
+  }
+  return IGA_OK;
+}
+
+std::vector<int> knot_spans(const double* t, int m, int p) {
+  std::vector<int> s;
+  for (int i = p; i <= m - p - 2; ++i)
+    if (t[i] < t[i + 1]) s.push_back(i);
+  return s;
+}
+
+bool method_supported(const iga_plan_opts& o, int dim, int p, int q) {
+  if (o.precision == IGA_FP64) {
+    if (o.method == IGA_SUMFACT) return sumfact_f64_supported(dim, p, q);
+    return classical_f64_supported(dim, p, q);
+  }
+  return false;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const T* src, size_t n) {
+  *dst = nullptr;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_plan_memory(iga_plan_s* P) {
+  for (auto& pr : P->prof_events) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  P->prof_events.clear();
+  cudaFree(P->d_patches);
+  cudaFree(P->d_knots);
+  cudaFree(P->d_spans);
+  cudaFree(P->d_gauss);
+  cudaFree(P->d_tables);
+  cudaFree(P->d_jobs);
+  cudaFree(P->d_err);
+}
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return IGA_OK;
+  if (e == cudaErrorMemoryAllocation) return IGA_ERR_OOM;
+  return IGA_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" const char* iga_status_str(int s) {
+  switch (s) {
+    case IGA_OK: return "IGA_OK";
+    case IGA_ERR_ARG: return "IGA_ERR_ARG: invalid argument";
+    case IGA_ERR_KNOTS: return "IGA_ERR_KNOTS: knot vector not open/non-decreasing or multiplicity > p";
+    case IGA_ERR_UNSUPPORTED: return "IGA_ERR_UNSUPPORTED: configuration not built";
+    case IGA_ERR_CUDA: return "IGA_ERR_CUDA: CUDA runtime error";
+    case IGA_ERR_OOM: return "IGA_ERR_OOM: device allocation failed";
+    case IGA_ERR_TIMEOUT: return "IGA_ERR_TIMEOUT: bounded device wait expired";
+    case IGA_ERR_DEVICE: return "IGA_ERR_DEVICE: device-side consistency check failed";
+    default: return "unknown iga status";
+  }
+}
+
+extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_patches,
+                        const iga_plan_opts* opts, iga_plan_info* info_out) {
+  if (out) *out = nullptr;
+  const char* lg = getenv("IGA_LOG");
+  g_log = lg && lg[0] == '1';
+  if (!out || !patches || n_patches < 1 || !opts) return IGA_ERR_ARG;
+  const iga_plan_opts o = *opts;
+  if (o.method != IGA_CLASSICAL && o.method != IGA_SUMFACT) return IGA_ERR_ARG;
+  if (o.precision < IGA_FP64 || o.precision > IGA_BF16) return IGA_ERR_ARG;
+  if (o.matrices < 1 || o.matrices > 3) return IGA_ERR_ARG;
+  if (o.method == IGA_CLASSICAL && o.precision != IGA_FP64) return IGA_ERR_UNSUPPORTED;
+  const int dim = patches[0].dim;
+  if (dim != 2 && dim != 3) return IGA_ERR_ARG;
+
+  iga_plan_s* P = new (std::nothrow) iga_plan_s();
+  if (!P) return IGA_ERR_OOM;
+  P->opts = o;
+  P->dim = dim;
+  P->n_patches = n_patches;
+
+  std::vector<double> knots_all, gauss_all;
+  std::vector<int> spans_all;
+  std::vector<TableJob> jobs;
+  int64_t e_off = 0, qp_off = 0, dof_off = 0, mat_off = 0, dm_off = 0, tab_off = 0;
+  for (int ip = 0; ip < n_patches; ++ip) {
+    const iga_patch_desc& d = patches[ip];
+    if (d.dim != dim) { delete P; return IGA_ERR_UNSUPPORTED; }
+    const int p = d.degree, q = d.n_gauss;
+    if (p < 1 || q < 1 || q > kMaxGauss) { delete P; return IGA_ERR_ARG; }
+    if ((dim == 3 && p > kMaxDegree3D) || (dim == 2 && p > kMaxDegree2D)) {
+      delete P;
+      return IGA_ERR_UNSUPPORTED;
+    }
+    for (int k = 0; k < dim; ++k) {
+      int rc = validate_knots(d.knots[k], d.n_knots[k], p);
+      if (rc != IGA_OK) { delete P; return rc; }
+    }
+    if (!method_supported(o, dim, p, q)) { delete P; return IGA_ERR_UNSUPPORTED; }
+    PatchDev pd{};
+    pd.dim = dim; pd.p = p; pd.q = q; pd.n = p + 1;
+    pd.N = 1; pd.Q = 1;
+    int64_t E = 1, nd = 1;
+    pd.gauss_offset = (int)gauss_all.size();
+    std::vector<double> xr(q), wr(q);
+    gauss_legendre_newton(q, xr.data(), wr.data());
+    gauss_all.insert(gauss_all.end(), xr.begin(), xr.end());
+    gauss_all.insert(gauss_all.end(), wr.begin(), wr.end());
+    for (int k = 0; k < 3; ++k) {
+      if (k >= dim) { pd.K[k] = 1; pd.nf[k] = 1; continue; }
+      const double* t = d.knots[k];
+      const int m = d.n_knots[k];
+      std::vector<int> s = knot_spans(t, m, p);
+      pd.K[k] = (int)s.size();
+      pd.nf[k] = m - p - 1;
+      pd.knot_offset[k] = (int)knots_all.size();
+      pd.span_offset[k] = (int)spans_all.size();
+      pd.tab_offset[k] = tab_off;
+      for (int ek = 0; ek < pd.K[k]; ++ek) {
+        TableJob j;
+        j.knot_off = pd.knot_offset[k];
+        j.span = s[ek];
+        j.p = p; j.q = q;
+        j.gauss_off = pd.gauss_offset;
+        j.out_off = tab_off;
+        jobs.push_back(j);
+        tab_off += record_size(p + 1, q);
+      }
+      knots_all.insert(knots_all.end(), t, t + m);
+      spans_all.insert(spans_all.end(), s.begin(), s.end());
+      P->spans_h.push_back(s);
+      E *= pd.K[k];
+      nd *= pd.nf[k];
+      pd.N *= pd.n;
+      pd.Q *= q;
+    }
+    pd.elem_offset = e_off; pd.qp_offset = qp_off; pd.dof_offset = dof_off;
+    pd.mat_offset = mat_off; pd.dofmap_offset = dm_off;
+    P->elem_off.push_back(e_off); P->qp_off.push_back(qp_off); P->dof_off.push_back(dof_off);
+    P->mat_off.push_back(mat_off); P->dofmap_off.push_back(dm_off);
+    e_off += E;
+    qp_off += E * pd.Q;
+    dof_off += nd;
+    mat_off += E * (int64_t)pd.N * pd.N;
+    dm_off += E * (int64_t)pd.N;
+    if (dm_off > INT32_MAX || dof_off > INT32_MAX) { delete P; return IGA_ERR_UNSUPPORTED; }
+    P->ph.push_back(pd);
+  }
+  P->elem_off.push_back(e_off); P->qp_off.push_back(qp_off); P->dof_off.push_back(dof_off);
+  P->mat_off.push_back(mat_off); P->dofmap_off.push_back(dm_off);
+  P->n_jobs = (int)jobs.size();
+
+  cudaError_t ce = cudaGetDevice(&P->device);
+  if (ce == cudaSuccess) ce = upload(&P->d_patches, P->ph.data(), P->ph.size());
+  if (ce == cudaSuccess) ce = upload(&P->d_knots, knots_all.data(), knots_all.size());
+  if (ce == cudaSuccess) ce = upload(&P->d_spans, spans_all.data(), spans_all.size());
+  if (ce == cudaSuccess) ce = upload(&P->d_gauss, gauss_all.data(), gauss_all.size());
+  if (ce == cudaSuccess) ce = upload(&P->d_jobs, jobs.data(), jobs.size());
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_tables, sizeof(double) * (size_t)tab_off);
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_err, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemset(P->d_err, 0, sizeof(int));
+  if (ce != cudaSuccess) {
+    free_plan_memory(P);
+    delete P;
+    cudaGetLastError();
+    return map_cuda(ce);
+  }
+  iga_plan_info& I = P->info;
+  I.n_elements = e_off; I.n_qp = qp_off; I.n_dofs = dof_off;
+  I.n_mat_entries = mat_off; I.n_dofmap_entries = dm_off; I.n_table_entries = tab_off;
+  I.dim = dim; I.n_patches = n_patches; I.local_n = P->ph[0].N;
+  I.elem_offset = P->elem_off.data(); I.qp_offset = P->qp_off.data();
+  I.dof_offset = P->dof_off.data(); I.mat_offset = P->mat_off.data();
+  I.dofmap_offset = P->dofmap_off.data();
+  if (info_out) *info_out = I;
+  log_msg("plan built");
+  *out = P;
+  return IGA_OK;
+}
+
+static int finish(iga_plan_s* P, cudaStream_t st, cudaError_t launch_err) {
+  if (launch_err != cudaSuccess) {
+    P->sticky = map_cuda(launch_err);
+    return P->sticky;
+  }
+  if (!P->opts.blocking) return IGA_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { P->sticky = map_cuda(e); return P->sticky; }
+  int h = 0;
+  e = cudaMemcpy(&h, P->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { P->sticky = map_cuda(e); return P->sticky; }
+  if (h != 0) P->sticky = h;
+  return h;
+}
+
+extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rho,
+                             const double* jac, void* K_out, void* M_out, int32_t* dof_out,
+                             void* cuda_stream) {
+  if (!P) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  const bool want_K = (P->opts.matrices & IGA_STIFF) && K_out;
+  const bool want_M = (P->opts.matrices & IGA_MASS) && M_out;
+  if (!want_K && !want_M && !dof_out) return IGA_ERR_ARG;
+  if ((K_out && !(P->opts.matrices & IGA_STIFF)) || (M_out && !(P->opts.matrices & IGA_MASS)))
+    return IGA_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+
+  cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
+                                      P->d_tables, st);
+  if (e == cudaSuccess && dof_out) {
+    for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip)
+      e = launch_dofmap(P->d_patches + ip, P->ph[ip], P->d_spans,
+                        dof_out + P->ph[ip].dofmap_offset, st);
+  }
+  const size_t esz = (P->opts.precision == IGA_FP64) ? sizeof(double) : sizeof(float);
+  std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+  if (e == cudaSuccess && P->opts.profile && (want_K || want_M)) {
+    if (P->prof_used == P->prof_events.size()) {
+      cudaEvent_t a, b;
+      e = cudaEventCreate(&a);
+      if (e == cudaSuccess) e = cudaEventCreate(&b);
+      if (e == cudaSuccess) P->prof_events.push_back({a, b});
+    }
+    if (e == cudaSuccess) {
+      ev = &P->prof_events[P->prof_used++];
+      e = cudaEventRecord(ev->first, st);
+    }
+  }
+  int64_t n_launch = 0;
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess && (want_K || want_M); ++ip) {
+    const PatchDev& pd = P->ph[ip];
+    ElemArgs a{};
+    a.pd = P->d_patches + ip;
+    a.n_elem = (int64_t)pd.K[0] * pd.K[1] * pd.K[2];
+    a.K1 = pd.K[0]; a.K2 = pd.K[1]; a.K3 = pd.K[2];
+    for (int k = 0; k < 3; ++k) a.tab[k] = P->d_tables + pd.tab_offset[k];
+    a.kappa = kappa ? kappa + pd.qp_offset : nullptr;
+    a.rho = rho ? rho + pd.qp_offset : nullptr;
+    a.jac = jac ? jac + pd.qp_offset * pd.dim * pd.dim : nullptr;
+    a.K_out = want_K ? (char*)K_out + esz * pd.mat_offset : nullptr;
+    a.M_out = want_M ? (char*)M_out + esz * pd.mat_offset : nullptr;
+    a.err = P->d_err;
+    if (P->opts.method == IGA_SUMFACT)
+      e = launch_sumfact_f64(a, pd.dim, pd.p, pd.q, st);
+    else
+      e = launch_classical_f64(a, pd.dim, pd.p, pd.q, st);
+    ++n_launch;
+  }
+  if (ev && e == cudaSuccess) {
+    e = cudaEventRecord(ev->second, st);
+    P->prof_launches += n_launch;
+  }
+  return finish(P, st, e);
+}
+
+extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const double* jac,
+                                      const void* u, const void* v, void* grad_kappa,
+                                      double* J_out, void* cuda_stream) {
+  (void)kappa; (void)jac; (void)u; (void)v; (void)grad_kappa; (void)J_out; (void)cuda_stream;
+  if (!P) return IGA_ERR_ARG;
+  return IGA_ERR_UNSUPPORTED;
+}
+
+extern "C" int iga_basis_tables(iga_plan_t P, double* out, void* cuda_stream) {
+  if (!P || !out) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss, out, st);
+  return finish(P, st, e);
+}
+
+extern "C" int iga_profile_read(iga_plan_t P, double* kernel_ms, int64_t* launches) {
+  if (!P || !P->opts.profile) return IGA_ERR_ARG;
+  double total = 0.0;
+  for (size_t i = 0; i < P->prof_used; ++i) {
+    cudaError_t e = cudaEventSynchronize(P->prof_events[i].second);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, P->prof_events[i].first, P->prof_events[i].second);
+    if (e != cudaSuccess) return map_cuda(e);
+    total += ms;
+  }
+  if (kernel_ms) *kernel_ms = total;
+  if (launches) *launches = P->prof_launches;
+  P->prof_used = 0;
+  P->prof_launches = 0;
+  return IGA_OK;
+}
+
+extern "C" int iga_destroy(iga_plan_t P) {
+  if (!P) return IGA_OK;
+  int rc = P->sticky;
+  int h = 0;
+  if (P->d_err && cudaMemcpy(&h, P->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+      h != 0 && rc == IGA_OK)
+    rc = h;
+  free_plan_memory(P);
+  delete P;
+  return rc;
+}

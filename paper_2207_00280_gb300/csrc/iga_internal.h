@@ -1,0 +1,76 @@
+// iga_internal.h -- plan layout and kernel launchers shared by the CUDA
+// translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "iga.h"
+
+namespace iga {
+
+constexpr int kMaxDegree3D = 5;
+constexpr int kMaxDegree2D = 8;
+constexpr int kMaxGauss = 16;
+
+// Per-patch description, uploaded to the device.  Offsets index the plan's
+// concatenated arrays.
+struct PatchDev {
+  int dim, p, q, n, N, Q;
+  int K[3];              // elements per direction
+  int nf[3];             // functions per direction (global 1D dofs)
+  int64_t elem_offset;   // first global element
+  int64_t qp_offset;     // first global quadrature point
+  int64_t dof_offset;    // first global dof
+  int64_t mat_offset;    // first entry of K_out / M_out
+  int64_t dofmap_offset; // first entry of dof_out
+  int64_t tab_offset[3]; // first double of direction k's basis records
+  int span_offset[3];    // first entry of direction k's spans
+  int knot_offset[3];    // first knot of direction k
+  int gauss_offset;      // first reference node / weight of this patch
+};
+
+// Basis record of one element of one direction: val[q][n], der[q][n], w[q]
+// (w = reference weight times half the span length).
+__host__ __device__ constexpr int record_size(int n, int q) { return 2 * q * n + q; }
+
+// One table job = one (patch, direction, element) record.
+struct TableJob {
+  int knot_off;   // first knot of the direction
+  int span;       // knot span index s of the element
+  int p, q;
+  int gauss_off;  // reference nodes at gauss[gauss_off], weights at gauss[gauss_off + q]
+  int64_t out_off;
+};
+
+// Device error word values are iga_status codes; 0 = OK.
+
+// ---- launchers (each returns a cudaError_t of the launch) ----------------
+cudaError_t launch_basis_tables(const TableJob* jobs, int n_jobs, const double* knots,
+                                const double* gauss, double* tables, cudaStream_t st);
+
+cudaError_t launch_dofmap(const PatchDev* patches_dev, const PatchDev& ph, const int* spans,
+                          int32_t* dof_out, cudaStream_t st);
+
+struct ElemArgs {
+  const PatchDev* pd;     // device copy of the patch
+  int64_t n_elem;         // elements of this patch
+  int K1, K2, K3;
+  const double* tab[3];   // first record of each direction
+  const double* kappa;    // patch-local (already offset), [E][Q] or null
+  const double* rho;
+  const double* jac;
+  void* K_out;            // patch-local, or null
+  void* M_out;
+  int* err;
+};
+
+// FP64 sum factorization (Algorithm 2 generalised to the stiffness terms).
+cudaError_t launch_sumfact_f64(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
+// FP64 classical integration (Algorithm 1).
+cudaError_t launch_classical_f64(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
+
+bool sumfact_f64_supported(int dim, int p, int q);
+bool classical_f64_supported(int dim, int p, int q);
+
+}  // namespace iga

@@ -1,0 +1,103 @@
+// k_tables.cu -- Cox--de Boor basis/derivative tables and the global dof map.
+#include "iga_internal.h"
+
+namespace iga {
+
+// One thread per (patch, direction, element) record.  For every Gauss point
+// of the element the p+1 non-zero B-splines B_{s-p+r;p}(xi), r = 0..p, are
+// built by the triangular form of the Cox--de Boor recursion (Sec. 2.3,
+// eq. cox2: each degree combines two neighbours of the previous degree, the
+// degree-0 start being the indicator of span s, eq. cox1).  Only the
+// non-vanishing functions are carried, so no 0/0 term ever arises.  The
+// derivative uses the degree p-1 row:
+//   B'_{i;p} = p B_{i;p-1}/(t_{i+p}-t_i) - p B_{i+1;p-1}/(t_{i+p+1}-t_{i+1}).
+// The record also stores the Gauss weight scaled by half the span length.
+__global__ void k_basis_tables(const TableJob* __restrict__ jobs, int n_jobs,
+                               const double* __restrict__ knots,
+                               const double* __restrict__ gauss, double* __restrict__ tables) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_jobs) return;
+  const TableJob J = jobs[r];
+  const double* t = knots + J.knot_off;
+  const int p = J.p, q = J.q, n = p + 1, s = J.span;
+  const double a = t[s], b = t[s + 1];
+  const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+  double* out = tables + J.out_off;
+  for (int j = 0; j < q; ++j) {
+    const double xi = mid + half * gauss[J.gauss_off + j];
+    double N[kMaxDegree2D + 1], Nm1[kMaxDegree2D + 1];
+    double left[kMaxDegree2D + 1], right[kMaxDegree2D + 1];
+    N[0] = 1.0;
+    Nm1[0] = 1.0;
+    for (int d = 1; d <= p; ++d) {
+      if (d == p) {
+        for (int k = 0; k < d; ++k) Nm1[k] = N[k];
+      }
+      left[d] = xi - t[s + 1 - d];
+      right[d] = t[s + d] - xi;
+      double saved = 0.0;
+      for (int k = 0; k < d; ++k) {
+        const double tmp = N[k] / (right[k + 1] + left[d - k]);
+        N[k] = saved + right[k + 1] * tmp;
+        saved = left[d - k] * tmp;
+      }
+      N[d] = saved;
+    }
+    for (int rr = 0; rr < n; ++rr) {
+      double dv = 0.0;
+      // B_{s-p+rr; p-1} is Nm1[rr-1] (rr >= 1), B_{s-p+rr+1; p-1} is Nm1[rr] (rr <= p-1)
+      if (rr >= 1) dv += Nm1[rr - 1] / (t[s + rr] - t[s - p + rr]);
+      if (rr <= p - 1) dv -= Nm1[rr] / (t[s + rr + 1] - t[s - p + rr + 1]);
+      out[j * n + rr] = N[rr];
+      out[q * n + j * n + rr] = p * dv;
+    }
+    out[2 * q * n + j] = half * gauss[J.gauss_off + q + j];
+  }
+}
+
+cudaError_t launch_basis_tables(const TableJob* jobs, int n_jobs, const double* knots,
+                                const double* gauss, double* tables, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  const int bs = 128;
+  k_basis_tables<<<(n_jobs + bs - 1) / bs, bs, 0, st>>>(jobs, n_jobs, knots, gauss, tables);
+  return cudaGetLastError();
+}
+
+// Global dof of every local function of every element (support set of the
+// Remark in Sec. 3.1): dof = dof_offset + sum_k (s_k - p + a_k) stride_k.
+// One thread per (element, local function); consecutive threads write
+// consecutive entries.
+__global__ void k_dofmap(const PatchDev* __restrict__ pdp, const int* __restrict__ spans,
+                         int32_t* __restrict__ dof, int64_t total) {
+  const PatchDev pd = *pdp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / pd.N;
+    const int a = (int)(i - e * pd.N);
+    const int e1 = (int)(e % pd.K[0]);
+    const int64_t r = e / pd.K[0];
+    const int e2 = (int)(r % pd.K[1]);
+    const int e3 = (int)(r / pd.K[1]);
+    const int a1 = a % pd.n;
+    const int a2 = (a / pd.n) % pd.n;
+    const int a3 = a / (pd.n * pd.n);
+    int64_t g = spans[pd.span_offset[0] + e1] - pd.p + a1;
+    g += (int64_t)(spans[pd.span_offset[1] + e2] - pd.p + a2) * pd.nf[0];
+    if (pd.dim == 3)
+      g += (int64_t)(spans[pd.span_offset[2] + e3] - pd.p + a3) * pd.nf[0] * pd.nf[1];
+    dof[i] = (int32_t)(pd.dof_offset + g);
+  }
+}
+
+cudaError_t launch_dofmap(const PatchDev* pdp, const PatchDev& ph, const int* spans,
+                          int32_t* dof_out, cudaStream_t st) {
+  const int64_t total = (int64_t)ph.K[0] * ph.K[1] * ph.K[2] * ph.N;
+  if (total == 0) return cudaSuccess;
+  const int bs = 256;
+  int64_t blocks = (total + bs - 1) / bs;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_dofmap<<<(unsigned)blocks, bs, 0, st>>>(pdp, spans, dof_out, total);
+  return cudaGetLastError();
+}
+
+}  // namespace iga

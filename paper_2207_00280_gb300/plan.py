@@ -1,0 +1,151 @@
+"""Torch-facing wrapper of the C ABI: owns a plan, allocates outputs as torch
+tensors and passes raw device pointers and the current stream to the library.
+Torch supplies device memory and streams only; all computation is in libiga.so.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import capi
+
+_METHODS = {"classical": capi.IGA_CLASSICAL, "sumfact": capi.IGA_SUMFACT}
+_PRECISIONS = {"fp64": capi.IGA_FP64, "fp32": capi.IGA_FP32, "bf16": capi.IGA_BF16}
+
+
+@dataclass
+class Patch:
+    knots: list          # one 1D array per direction
+    degree: int
+    n_gauss: int
+
+    @property
+    def dim(self) -> int:
+        return len(self.knots)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class IgaPlan:
+    """Plan for one patch or a batch of patches (same dimension)."""
+
+    def __init__(self, patches, method: str = "sumfact", precision: str = "fp64",
+                 mass: bool = True, stiffness: bool = True, schedule: int = 0,
+                 blocking: bool = True, profile: bool = False):
+        if isinstance(patches, Patch):
+            patches = [patches]
+        self.patches = list(patches)
+        self.precision = precision
+        self.method = method
+        self._knots = []
+        descs = []
+        for pt in self.patches:
+            d = capi.PatchDesc()
+            d.dim, d.degree, d.n_gauss = pt.dim, int(pt.degree), int(pt.n_gauss)
+            for k, t in enumerate(pt.knots):
+                arr = np.ascontiguousarray(t, dtype=np.float64)
+                self._knots.append(arr)
+                d.n_knots[k] = len(arr)
+                d.knots[k] = arr.ctypes.data
+            descs.append(d)
+        opts = capi.PlanOpts()
+        opts.method = _METHODS[method]
+        opts.precision = _PRECISIONS[precision]
+        opts.matrices = (capi.IGA_MASS if mass else 0) | (capi.IGA_STIFF if stiffness else 0)
+        opts.schedule = int(schedule)
+        opts.blocking = 1 if blocking else 0
+        opts.profile = 1 if profile else 0
+        self.mass, self.stiffness = mass, stiffness
+        self.handle, info = capi.iga_plan(descs, opts)
+        self.info = info
+        npt = info.n_patches
+        self.elem_offset = [info.elem_offset[i] for i in range(npt + 1)]
+        self.qp_offset = [info.qp_offset[i] for i in range(npt + 1)]
+        self.dof_offset = [info.dof_offset[i] for i in range(npt + 1)]
+        self.mat_offset = [info.mat_offset[i] for i in range(npt + 1)]
+        self.dofmap_offset = [info.dofmap_offset[i] for i in range(npt + 1)]
+        self.out_dtype = torch.float64 if precision == "fp64" else torch.float32
+
+    # -- sizes ---------------------------------------------------------------
+    @property
+    def n_elements(self) -> int:
+        return self.info.n_elements
+
+    @property
+    def n_qp(self) -> int:
+        return self.info.n_qp
+
+    @property
+    def n_dofs(self) -> int:
+        return self.info.n_dofs
+
+    def empty_outputs(self, device="cuda", dof: bool = True):
+        n = self.info.n_mat_entries
+        K = torch.empty(n, dtype=self.out_dtype, device=device) if self.stiffness else None
+        M = torch.empty(n, dtype=self.out_dtype, device=device) if self.mass else None
+        D = torch.empty(self.info.n_dofmap_entries, dtype=torch.int32, device=device) if dof else None
+        return K, M, D
+
+    # -- calls -----------------------------------------------------------------
+    def integrate(self, kappa=None, rho=None, jac=None, K=None, M=None, dof=None, stream=None):
+        rc = capi.iga_integrate(self.handle, _ptr(kappa), _ptr(rho), _ptr(jac), _ptr(K), _ptr(M),
+                                _ptr(dof), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_integrate")
+        return K, M, dof
+
+    def backward(self, kappa, u, v, grad=None, J=None, jac=None, stream=None):
+        rc = capi.iga_integrate_backward(self.handle, _ptr(kappa), _ptr(jac), _ptr(u), _ptr(v),
+                                         _ptr(grad), _ptr(J), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_integrate_backward")
+        return grad, J
+
+    def profile_read(self):
+        """(ms, launches) of the element-matrix kernels since the last read."""
+        return capi.iga_profile_read(self.handle)
+
+    def basis_tables(self, stream=None):
+        out = torch.empty(self.info.n_table_entries, dtype=torch.float64, device="cuda")
+        rc = capi.iga_basis_tables(self.handle, _ptr(out), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_basis_tables")
+        return out
+
+    def patch_view(self, flat, i: int):
+        """Reshape patch i's block of a flat K/M output to [E][N][N]."""
+        pt = self.patches[i]
+        N = (pt.degree + 1) ** pt.dim
+        a, b = self.mat_offset[i], self.mat_offset[i + 1]
+        return flat[a:b].view(-1, N, N)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            rc = capi.iga_destroy(self.handle)
+            self.handle = None
+            if rc != capi.IGA_OK:
+                raise capi.IgaError(rc, "iga_destroy")
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None and self.handle.value:
+                capi.iga_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
