@@ -195,7 +195,7 @@ def cpu_baseline_oracle(workload, budget_s=12.0, method="sumfact", max_elems=Non
     limit = max_elems or sp.E
     while done < limit and time.perf_counter() - t0 < budget_s:
         el = order[done:done + chunk]
-        fn(el, kappa=kappa, G=G, stiffness=True, mass=True)
+        fn(el, kappa=kappa, G=G, stiffness=True, mass=G is None)
         done += len(el)
     dt = time.perf_counter() - t0
     return done / dt, done, dt

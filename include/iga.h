@@ -70,6 +70,20 @@ enum { IGA_CLASSICAL = 0, IGA_SUMFACT = 1 };
 enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_BF16 = 2 };
 enum { IGA_MASS = 1, IGA_STIFF = 2 };
 
+/* Schedules (iga_plan_opts.schedule).  AUTO picks PERSISTENT_GRAPH for FP32 or
+ * BF16 sum factorization of a batch of several patches, PER_PATCH otherwise,
+ * and lets the autotuner choose the work-item size of every degree class.
+ *   PER_PATCH:        one grid launch (one CTA per element) per patch;
+ *   PERSISTENT:       one persistent kernel per (degree, Gauss order) class,
+ *                     CTAs pop work items (consecutive elements of one patch)
+ *                     from a device queue;
+ *   PERSISTENT_GRAPH: the same kernels plus the table and dof-map kernels
+ *                     captured once into a CUDA graph (classes on parallel
+ *                     branches) and replayed while the pointers are unchanged.
+ * The persistent schedules exist for FP32/BF16 sum factorization only. */
+enum { IGA_SCHED_AUTO = 0, IGA_SCHED_PER_PATCH = 1, IGA_SCHED_PERSISTENT = 2,
+       IGA_SCHED_PERSISTENT_GRAPH = 3 };
+
 /* One tensor-product patch.  Knot vectors are host arrays, copied by
  * iga_plan.  Each must be non-decreasing and open (first and last p+1 knots
  * equal) with interior multiplicity <= p (Sec. 2.3, eq. knot_vector).
@@ -86,7 +100,7 @@ typedef struct {
   int method;     /* IGA_CLASSICAL or IGA_SUMFACT */
   int precision;  /* IGA_FP64, IGA_FP32 or IGA_BF16 (sum factorization only) */
   int matrices;   /* bitmask of IGA_MASS | IGA_STIFF */
-  int schedule;   /* 0 = automatic (autotuned), else a schedule id (iga_schedule_*) */
+  int schedule;   /* IGA_SCHED_*; 0 = automatic (autotuned) */
   int blocking;   /* 1 = synchronize the stream and return the device status */
   int profile;    /* 1 = record CUDA events around the element-matrix kernels */
 } iga_plan_opts;

@@ -31,6 +31,10 @@ IGA_FP32 = 1
 IGA_BF16 = 2
 IGA_MASS = 1
 IGA_STIFF = 2
+IGA_SCHED_AUTO = 0
+IGA_SCHED_PER_PATCH = 1
+IGA_SCHED_PERSISTENT = 2
+IGA_SCHED_PERSISTENT_GRAPH = 3
 
 # Every exported symbol of include/iga.h (checked by tests/test_capi_symbols.py).
 EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_basis_tables",

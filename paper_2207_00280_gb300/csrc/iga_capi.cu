@@ -9,6 +9,7 @@
 #include <utility>
 #include <vector>
 
+#include "iga_batch.h"
 #include "iga_internal.h"
 
 using namespace iga;
@@ -28,7 +29,12 @@ struct iga_plan_s {
   TableJob* d_jobs = nullptr;
   int n_jobs = 0;
   int* d_err = nullptr;
+  double* d_partial = nullptr;   // adjoint scratch: one double per element
   int sticky = IGA_OK;
+  // batched schedules (FP32/BF16 sum factorization)
+  bool use_batch = false;
+  bool use_graph = false;
+  BatchState batch;
   // profiling: event pairs around the element-matrix kernels
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   size_t prof_used = 0;
@@ -115,6 +121,8 @@ bool method_supported(const iga_plan_opts& o, int dim, int p, int q) {
     if (o.method == IGA_SUMFACT) return sumfact_f64_supported(dim, p, q);
     return classical_f64_supported(dim, p, q);
   }
+  if (o.precision == IGA_FP32 || o.precision == IGA_BF16)
+    return o.method == IGA_SUMFACT && sumfact_f32_supported(dim, p, q);
   return false;
 }
 
@@ -128,6 +136,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 }
 
 void free_plan_memory(iga_plan_s* P) {
+  batch_free(&P->batch);
   for (auto& pr : P->prof_events) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -140,6 +149,7 @@ void free_plan_memory(iga_plan_s* P) {
   cudaFree(P->d_tables);
   cudaFree(P->d_jobs);
   cudaFree(P->d_err);
+  cudaFree(P->d_partial);
 }
 
 int map_cuda(cudaError_t e) {
@@ -175,6 +185,9 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   if (o.precision < IGA_FP64 || o.precision > IGA_BF16) return IGA_ERR_ARG;
   if (o.matrices < 1 || o.matrices > 3) return IGA_ERR_ARG;
   if (o.method == IGA_CLASSICAL && o.precision != IGA_FP64) return IGA_ERR_UNSUPPORTED;
+  if (o.schedule < IGA_SCHED_AUTO || o.schedule > IGA_SCHED_PERSISTENT_GRAPH) return IGA_ERR_ARG;
+  const bool lowprec_sf = o.method == IGA_SUMFACT && o.precision != IGA_FP64;
+  if (!lowprec_sf && o.schedule > IGA_SCHED_PER_PATCH) return IGA_ERR_UNSUPPORTED;
   const int dim = patches[0].dim;
   if (dim != 2 && dim != 3) return IGA_ERR_ARG;
 
@@ -264,11 +277,29 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_tables, sizeof(double) * (size_t)tab_off);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_err, sizeof(int));
   if (ce == cudaSuccess) ce = cudaMemset(P->d_err, 0, sizeof(int));
+  if (ce == cudaSuccess && e_off > 0)
+    ce = cudaMalloc((void**)&P->d_partial, sizeof(double) * (size_t)e_off);
   if (ce != cudaSuccess) {
     free_plan_memory(P);
     delete P;
     cudaGetLastError();
     return map_cuda(ce);
+  }
+  if (lowprec_sf) {
+    const int sched = o.schedule == IGA_SCHED_AUTO
+                          ? (n_patches > 1 ? IGA_SCHED_PERSISTENT_GRAPH : IGA_SCHED_PER_PATCH)
+                          : o.schedule;
+    if (sched != IGA_SCHED_PER_PATCH) {
+      P->use_batch = true;
+      P->use_graph = sched == IGA_SCHED_PERSISTENT_GRAPH;
+      const int rc = batch_plan(&P->batch, P->ph, o.precision, o.schedule);
+      if (rc != IGA_OK) {
+        free_plan_memory(P);
+        delete P;
+        cudaGetLastError();
+        return rc;
+      }
+    }
   }
   iga_plan_info& I = P->info;
   I.n_elements = e_off; I.n_qp = qp_off; I.n_dofs = dof_off;
@@ -282,6 +313,27 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   *out = P;
   return IGA_OK;
 }
+
+namespace {
+struct ProCtx {
+  iga_plan_s* P;
+  int32_t* dof_out;
+};
+
+// Basis tables of every patch, then the dof maps (when requested).
+cudaError_t run_prologue(void* c, cudaStream_t st) {
+  ProCtx* x = (ProCtx*)c;
+  iga_plan_s* P = x->P;
+  cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
+                                      P->d_tables, st);
+  if (e == cudaSuccess && x->dof_out) {
+    for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip)
+      e = launch_dofmap(P->d_patches + ip, P->ph[ip], P->d_spans,
+                        x->dof_out + P->ph[ip].dofmap_offset, st);
+  }
+  return e;
+}
+}  // namespace
 
 static int finish(iga_plan_s* P, cudaStream_t st, cudaError_t launch_err) {
   if (launch_err != cudaSuccess) {
@@ -312,13 +364,40 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
-  cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
-                                      P->d_tables, st);
-  if (e == cudaSuccess && dof_out) {
-    for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip)
-      e = launch_dofmap(P->d_patches + ip, P->ph[ip], P->d_spans,
-                        dof_out + P->ph[ip].dofmap_offset, st);
+  ProCtx pctx{P, dof_out};
+  cudaError_t e = cudaSuccess;
+  if (P->use_batch && (want_K || want_M)) {
+    QueueArgs b{};
+    b.patches = P->d_patches;
+    b.n_patches = P->n_patches;
+    b.tables = P->d_tables;
+    b.kappa = kappa; b.rho = rho; b.jac = jac;
+    b.K_out = want_K ? K_out : nullptr;
+    b.M_out = want_M ? M_out : nullptr;
+    b.err = P->d_err;
+    const int mode = (want_K && want_M) ? 0 : (want_K ? 1 : 2);
+    BatchPrologue pro{run_prologue, &pctx, dof_out};
+    std::pair<cudaEvent_t, cudaEvent_t>* evb = nullptr;
+    if (P->opts.profile) {
+      if (P->prof_used == P->prof_events.size()) {
+        cudaEvent_t a0, b0;
+        e = cudaEventCreate(&a0);
+        if (e == cudaSuccess) e = cudaEventCreate(&b0);
+        if (e == cudaSuccess) P->prof_events.push_back({a0, b0});
+      }
+      if (e == cudaSuccess) {
+        evb = &P->prof_events[P->prof_used++];
+        e = cudaEventRecord(evb->first, st);
+      }
+    }
+    if (e == cudaSuccess) e = batch_integrate(&P->batch, b, mode, st, pro, P->use_graph);
+    if (e == cudaSuccess && evb) {
+      e = cudaEventRecord(evb->second, st);
+      P->prof_launches += 1;
+    }
+    return finish(P, st, e);
   }
+  e = run_prologue(&pctx, st);
   const size_t esz = (P->opts.precision == IGA_FP64) ? sizeof(double) : sizeof(float);
   std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
   if (e == cudaSuccess && P->opts.profile && (want_K || want_M)) {
@@ -347,7 +426,9 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
     a.K_out = want_K ? (char*)K_out + esz * pd.mat_offset : nullptr;
     a.M_out = want_M ? (char*)M_out + esz * pd.mat_offset : nullptr;
     a.err = P->d_err;
-    if (P->opts.method == IGA_SUMFACT)
+    if (P->opts.method == IGA_SUMFACT && P->opts.precision != IGA_FP64)
+      e = launch_sumfact_f32(a, pd.dim, pd.p, pd.q, P->opts.precision == IGA_BF16, st);
+    else if (P->opts.method == IGA_SUMFACT)
       e = launch_sumfact_f64(a, pd.dim, pd.p, pd.q, st);
     else
       e = launch_classical_f64(a, pd.dim, pd.p, pd.q, st);
@@ -363,9 +444,39 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
 extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const double* jac,
                                       const void* u, const void* v, void* grad_kappa,
                                       double* J_out, void* cuda_stream) {
-  (void)kappa; (void)jac; (void)u; (void)v; (void)grad_kappa; (void)J_out; (void)cuda_stream;
   if (!P) return IGA_ERR_ARG;
-  return IGA_ERR_UNSUPPORTED;
+  if (P->sticky != IGA_OK) return P->sticky;
+  if (!u || !v || (!grad_kappa && !J_out) || (J_out && !kappa)) return IGA_ERR_ARG;
+  for (const PatchDev& pd : P->ph)
+    if (!adjoint_supported(pd.dim, pd.p, pd.q)) return IGA_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool fp64 = P->opts.precision == IGA_FP64;
+  const size_t gsz = fp64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
+                                      P->d_tables, st);
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip) {
+    const PatchDev& pd = P->ph[ip];
+    AdjArgs a{};
+    a.n_elem = (int64_t)pd.K[0] * pd.K[1] * pd.K[2];
+    a.K1 = pd.K[0]; a.K2 = pd.K[1]; a.K3 = pd.K[2];
+    for (int k = 0; k < 3; ++k) {
+      a.tab[k] = P->d_tables + pd.tab_offset[k];
+      a.span[k] = P->d_spans + pd.span_offset[k];
+    }
+    a.nf0 = pd.nf[0]; a.nf1 = pd.nf[1];
+    a.dof_offset = pd.dof_offset;
+    a.kappa = kappa ? kappa + pd.qp_offset : nullptr;
+    a.jac = jac ? jac + pd.qp_offset * 9 : nullptr;
+    a.u = u; a.v = v;
+    a.grad = grad_kappa ? (char*)grad_kappa + gsz * pd.qp_offset : nullptr;
+    a.partial = J_out ? P->d_partial : nullptr;
+    a.partial_offset = pd.elem_offset;
+    e = launch_adjoint(a, pd.p, pd.q, fp64, st);
+  }
+  if (e == cudaSuccess && J_out) e = launch_reduce_fixed(P->d_partial, P->info.n_elements, J_out, st);
+  return finish(P, st, e);
 }
 
 extern "C" int iga_basis_tables(iga_plan_t P, double* out, void* cuda_stream) {

@@ -70,7 +70,61 @@ cudaError_t launch_sumfact_f64(const ElemArgs& a, int dim, int p, int q, cudaStr
 // FP64 classical integration (Algorithm 1).
 cudaError_t launch_classical_f64(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
 
+// Persistent batched form: one work item = `count` consecutive elements of one
+// patch; CTAs pop items from a device counter.
+struct WorkItem {
+  int patch;
+  int count;
+  int64_t e0;
+};
+struct QueueArgs {
+  const PatchDev* patches;
+  int n_patches;
+  const double* tables;
+  const double* kappa;   // global [n_qp] or null
+  const double* rho;
+  const double* jac;     // global [n_qp][9] or null
+  void* K_out;           // global, float
+  void* M_out;
+  const WorkItem* items;
+  int n_items;
+  int* counter;          // zeroed before the launch
+  int* err;
+  unsigned long long budget_ns;  // 0 = no time budget
+};
+cudaError_t launch_sumfact_f32_queue(const QueueArgs& b, int p, int q, bool bf16, int mode,
+                                     int grid, cudaStream_t st, int* max_grid);
+bool queue_both_fit(int p, int q, bool bf16);
+
+// FP32 sum factorization (3D): FP64 cofactors/determinant, FP32 contractions;
+// with bf16 = true the last contraction runs on the tensor cores in BF16.
+cudaError_t launch_sumfact_f32(const ElemArgs& a, int dim, int p, int q, bool bf16,
+                               cudaStream_t st);
+
+// Matrix-free adjoint (3D): grad[e*Q + k] = dJ/dkappa, partial[partial_offset + e]
+// = per-element sum of kappa * grad.  All array pointers are patch-local except
+// u, v (global dof vectors) and partial.
+struct AdjArgs {
+  int64_t n_elem;
+  int K1, K2, K3;
+  const double* tab[3];
+  const int* span[3];
+  int nf0, nf1;
+  int64_t dof_offset;
+  const double* kappa;   // patch-local [E][Q] or null (= 1)
+  const double* jac;     // patch-local [E][Q][9] or null
+  const void* u;         // global [n_dofs], double or float
+  const void* v;
+  void* grad;            // patch-local [E][Q] or null
+  double* partial;       // [n_elements] or null
+  int64_t partial_offset;
+};
+cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, cudaStream_t st);
+cudaError_t launch_reduce_fixed(const double* partial, int64_t n, double* out, cudaStream_t st);
+bool adjoint_supported(int dim, int p, int q);
+
 bool sumfact_f64_supported(int dim, int p, int q);
+bool sumfact_f32_supported(int dim, int p, int q);
 bool classical_f64_supported(int dim, int p, int q);
 
 }  // namespace iga

@@ -171,4 +171,7 @@ WORKLOADS = {
     "3d_p3_32": Workload("3d_p3_32", PatchSpec(3, 3, 32, 4), SEED_KAPPA_P3),
     "3d_p4_48_curved": Workload("3d_p4_48_curved", PatchSpec(3, 4, 48, 5), SEED_KAPPA_P4, curved=True),
     "3d_p3_40_adjoint": Workload("3d_p3_40_adjoint", PatchSpec(3, 3, 40, 4), SEED_ADJ_KAPPA),
+    # reduced sizes of the same workloads, for profiler captures (inputs + outputs > L2)
+    "3d_p3_16": Workload("3d_p3_16", PatchSpec(3, 3, 16, 4), SEED_KAPPA_P3),
+    "3d_p4_24_curved": Workload("3d_p4_24_curved", PatchSpec(3, 4, 24, 5), SEED_KAPPA_P4, curved=True),
 }
