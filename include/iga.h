@@ -63,7 +63,8 @@ typedef enum {
   IGA_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   IGA_ERR_OOM = 5,          /* device allocation failed */
   IGA_ERR_TIMEOUT = 6,      /* a bounded device wait expired */
-  IGA_ERR_DEVICE = 7        /* the device reported an inconsistency (bad work item) */
+  IGA_ERR_DEVICE = 7,       /* the device reported an inconsistency (bad work item) */
+  IGA_ERR_TOO_LARGE = 8     /* beyond the fixed scratch of iga_adjoint_noalloc */
 } iga_status;
 
 enum { IGA_CLASSICAL = 0, IGA_SUMFACT = 1 };
@@ -170,6 +171,30 @@ int iga_basis_tables(iga_plan_t plan, double* out, void* cuda_stream);
  * immediately before and after them, and the number of such launches; then
  * reset the counters.  Returns IGA_ERR_ARG if profiling is off. */
 int iga_profile_read(iga_plan_t plan, double* kernel_ms, int64_t* launches);
+
+/* iga_integrate_backward without any device allocation.  The paper has no
+ * counterpart: this entry exists for callers that cannot call cudaMalloc --
+ * code that runs inside a memory pool or arena it does not own, an embedding
+ * host whose allocator forbids foreign allocations, or a latency-critical loop
+ * that must never enter the allocator -- and so cannot create a plan, which
+ * allocates its tables.
+ * It computes dJ/dkappa and J = u^T K(kappa) v (FP64) for one 3D patch whose
+ * knot vectors are host arrays, with kappa, jac, u, v, grad_kappa and J_out
+ * in device memory as for a FP64 plan's iga_integrate_backward (jac may be
+ * NULL; kappa may be NULL only if J_out is NULL).  Its working memory is one
+ * file-scope device array of 3.7 MiB that every GPU which loads the library
+ * holds until the process exits: at most 1024 knots per direction, 262144
+ * elements and 196608 doubles of basis tables; larger patches return
+ * IGA_ERR_TOO_LARGE before anything is launched.  The first call on a device
+ * looks up the array's device address (with that device current), so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads on one device) race and must be serialized by the caller.  Nothing
+ * in the array needs clearing: each call overwrites what it reads.  Launch
+ * errors are returned; the call does not synchronize. */
+int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* kappa, const double* jac,
+                        const double* u, const double* v, double* grad_kappa, double* J_out,
+                        void* cuda_stream);
 
 /* Free the plan and its device memory; NULL-safe.  Returns the sticky device
  * status of the plan (IGA_OK if none). */

@@ -24,6 +24,7 @@ IGA_ERR_CUDA = 4
 IGA_ERR_OOM = 5
 IGA_ERR_TIMEOUT = 6
 IGA_ERR_DEVICE = 7
+IGA_ERR_TOO_LARGE = 8
 IGA_CLASSICAL = 0
 IGA_SUMFACT = 1
 IGA_FP64 = 0
@@ -38,7 +39,7 @@ IGA_SCHED_PERSISTENT_GRAPH = 3
 
 # Every exported symbol of include/iga.h (checked by tests/test_capi_symbols.py).
 EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_basis_tables",
-            "iga_profile_read", "iga_destroy", "iga_status_str")
+            "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str")
 
 
 class IgaError(RuntimeError):
@@ -98,6 +99,8 @@ def lib() -> ctypes.CDLL:
             L.iga_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
             L.iga_profile_read.restype = i32
+            L.iga_adjoint_noalloc.argtypes = [ctypes.POINTER(PatchDesc), vp, vp, vp, vp, vp, vp, vp]
+            L.iga_adjoint_noalloc.restype = i32
             L.iga_destroy.argtypes = [vp]
             L.iga_destroy.restype = i32
             L.iga_status_str.argtypes = [i32]

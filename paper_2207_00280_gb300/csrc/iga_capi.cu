@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -170,6 +171,9 @@ extern "C" const char* iga_status_str(int s) {
     case IGA_ERR_OOM: return "IGA_ERR_OOM: device allocation failed";
     case IGA_ERR_TIMEOUT: return "IGA_ERR_TIMEOUT: bounded device wait expired";
     case IGA_ERR_DEVICE: return "IGA_ERR_DEVICE: device-side consistency check failed";
+    case IGA_ERR_TOO_LARGE:
+      return "IGA_ERR_TOO_LARGE: the patch exceeds the fixed scratch of the allocation-free entry "
+             "point (at most 1024 knots per direction, 262144 elements, 196608 table doubles)";
     default: return "unknown iga status";
   }
 }
@@ -516,4 +520,155 @@ extern "C" int iga_destroy(iga_plan_t P) {
   free_plan_memory(P);
   delete P;
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint for callers that cannot allocate device memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNaMaxKnots = 1024;            // knots per direction
+constexpr int64_t kNaMaxElements = 262144;   // elements of the patch
+constexpr int64_t kNaTableDoubles = 196608;  // basis-table records
+// scratch layout, in doubles
+constexpr int64_t kNaKnots = 0;                                   // [3][kNaMaxKnots]
+constexpr int64_t kNaGauss = kNaKnots + 3 * kNaMaxKnots;          // [2][kMaxGauss]
+constexpr int64_t kNaSpans = kNaGauss + 2 * kMaxGauss;            // int [3][kNaMaxKnots]
+constexpr int64_t kNaJobs = kNaSpans + 3 * kNaMaxKnots / 2;       // TableJob [3][kNaMaxKnots]
+constexpr int64_t kNaTables = kNaJobs + 3 * kNaMaxKnots * (int64_t)sizeof(TableJob) / 8;
+constexpr int64_t kNaPartials = kNaTables + kNaTableDoubles;      // [kNaMaxElements]
+constexpr int64_t kNaDoubles = kNaPartials + kNaMaxElements;      // 3.7 MiB in total
+
+// The scratch of iga_adjoint_noalloc: one fixed array per GPU that loads the
+// library, kept until the process exits and shared by every call.
+static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
+
+// Per-device address of g_noalloc_scratch, looked up once per device.
+std::mutex g_na_mu;
+double* g_na_ptr[64] = {nullptr};
+
+struct NaParams {
+  double knots[3][kNaMaxKnots];
+  int m[3];
+  int p, q;
+  double gx[kMaxGauss], gw[kMaxGauss];
+};
+
+// Writes the knots, the Gauss rule, the element spans and the table jobs of
+// one 3D patch into the scratch (one thread per (direction, element)).
+__global__ void k_noalloc_setup(const NaParams P, double* scratch, int K0, int K1, int K2) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double* knots = scratch + kNaKnots;
+  double* gauss = scratch + kNaGauss;
+  int* spans = (int*)(scratch + kNaSpans);
+  TableJob* jobs = (TableJob*)(scratch + kNaJobs);
+  for (int i = tid; i < 3 * kNaMaxKnots; i += gridDim.x * blockDim.x) {
+    const int d = i / kNaMaxKnots, j = i % kNaMaxKnots;
+    knots[i] = j < P.m[d] ? P.knots[d][j] : 0.0;
+  }
+  for (int i = tid; i < P.q; i += gridDim.x * blockDim.x) {
+    gauss[i] = P.gx[i];
+    gauss[P.q + i] = P.gw[i];
+  }
+  const int Ks[3] = {K0, K1, K2};
+  const int rec = 2 * P.q * (P.p + 1) + P.q;
+  for (int i = tid; i < K0 + K1 + K2; i += gridDim.x * blockDim.x) {
+    int d = 0, ek = i;
+    while (ek >= Ks[d]) { ek -= Ks[d]; ++d; }
+    // the ek-th non-empty span of direction d
+    int s = P.p, c = -1;
+    for (; s <= P.m[d] - P.p - 2; ++s) {
+      if (P.knots[d][s] < P.knots[d][s + 1]) ++c;
+      if (c == ek) break;
+    }
+    spans[d * kNaMaxKnots + ek] = s;
+    TableJob j;
+    j.knot_off = d * kNaMaxKnots;
+    j.span = s;
+    j.p = P.p;
+    j.q = P.q;
+    j.gauss_off = 0;
+    int64_t before = 0;
+    for (int dd = 0; dd < d; ++dd) before += Ks[dd];
+    j.out_off = (before + ek) * rec;
+    jobs[i] = j;
+  }
+}
+
+}  // namespace
+
+extern "C" int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* kappa,
+                                   const double* jac, const double* u, const double* v,
+                                   double* grad_kappa, double* J_out, void* cuda_stream) {
+  if (!patch || !u || !v || (!grad_kappa && !J_out) || (J_out && !kappa)) return IGA_ERR_ARG;
+  const iga_patch_desc& d = *patch;
+  if (d.dim != 3) return IGA_ERR_UNSUPPORTED;
+  const int p = d.degree, q = d.n_gauss;
+  if (p < 1 || q < 1 || q > kMaxGauss) return IGA_ERR_ARG;
+  if (!adjoint_supported(3, p, q)) return IGA_ERR_UNSUPPORTED;
+  int K[3], nf[3];
+  int64_t E = 1, tab = 0;
+  for (int k = 0; k < 3; ++k) {
+    const int rc = validate_knots(d.knots[k], d.n_knots[k], p);
+    if (rc != IGA_OK) return rc;
+    if (d.n_knots[k] > kNaMaxKnots) return IGA_ERR_TOO_LARGE;
+    K[k] = (int)knot_spans(d.knots[k], d.n_knots[k], p).size();
+    nf[k] = d.n_knots[k] - p - 1;
+    E *= K[k];
+    tab += (int64_t)K[k] * record_size(p + 1, q);
+  }
+  if (E > kNaMaxElements || tab > kNaTableDoubles) return IGA_ERR_TOO_LARGE;
+
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return IGA_ERR_CUDA;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) return IGA_ERR_CUDA;
+      g_na_ptr[dev] = (double*)ptr;
+    }
+    scratch = g_na_ptr[dev];
+  }
+  NaParams P;
+  for (int k = 0; k < 3; ++k) {
+    P.m[k] = d.n_knots[k];
+    for (int j = 0; j < kNaMaxKnots; ++j) P.knots[k][j] = j < d.n_knots[k] ? d.knots[k][j] : 0.0;
+  }
+  P.p = p;
+  P.q = q;
+  gauss_legendre_newton(q, P.gx, P.gw);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  k_noalloc_setup<<<8, 256, 0, st>>>(P, scratch, K[0], K[1], K[2]);
+  cudaError_t e = cudaGetLastError();
+  const int n_jobs = K[0] + K[1] + K[2];
+  double* tables = scratch + kNaTables;
+  if (e == cudaSuccess)
+    e = launch_basis_tables((const TableJob*)(scratch + kNaJobs), n_jobs, scratch + kNaKnots,
+                            scratch + kNaGauss, tables, st);
+  if (e == cudaSuccess) {
+    AdjArgs a{};
+    a.n_elem = E;
+    a.K1 = K[0]; a.K2 = K[1]; a.K3 = K[2];
+    const int rec = record_size(p + 1, q);
+    a.tab[0] = tables;
+    a.tab[1] = tables + (int64_t)K[0] * rec;
+    a.tab[2] = tables + (int64_t)(K[0] + K[1]) * rec;
+    const int* spans = (const int*)(scratch + kNaSpans);
+    for (int k = 0; k < 3; ++k) a.span[k] = spans + k * kNaMaxKnots;
+    a.nf0 = nf[0]; a.nf1 = nf[1];
+    a.dof_offset = 0;
+    a.kappa = kappa;
+    a.jac = jac;
+    a.u = u; a.v = v;
+    a.grad = grad_kappa;
+    a.partial = J_out ? scratch + kNaPartials : nullptr;
+    a.partial_offset = 0;
+    e = launch_adjoint(a, p, q, true, st);
+  }
+  if (e == cudaSuccess && J_out) e = launch_reduce_fixed(scratch + kNaPartials, E, J_out, st);
+  if (e != cudaSuccess) return map_cuda(e);
+  return IGA_OK;
 }

@@ -42,7 +42,7 @@ def test_exports_every_declared_symbol(capi):
 
 
 def test_status_strings(capi):
-    for code in range(8):
+    for code in range(9):
         s = capi.iga_status_str(code)
         assert s.startswith("IGA_")
     assert "unknown" in capi.iga_status_str(99)
