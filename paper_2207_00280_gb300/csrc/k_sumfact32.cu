@@ -4,20 +4,21 @@
 // Algorithm 2 generalised to the stiffness; see k_sumfact64.cu): stage 1
 // contracts the last direction (k3), stage 2 the middle one (k2), stage 3 the
 // first (k1).  Precision: the Jacobian cofactors and determinant are formed in
-// FP64; D = w kappa / |det| c^T c, the 1D factor patterns and the three
-// contractions run in FP32.  In the BF16 form the stage-3 contraction is a
-// dense GEMM per element on the tensor cores (bf16 operands, FP32
-// accumulation): rows (a',b'), columns (a1,b1), depth (x pattern, k1); the
-// x-pattern operand is split into bf16 hi + lo parts.
+// FP64; D = w kappa / |det| c^T c, the 1D factor patterns and stages 1-2 run
+// in FP32 FFMA (register-blocked: the reused operand in registers, the 1D
+// factor patterns streamed from shared memory as float4 records).
 //
-// The FP32 stages are register-blocked: each thread keeps the operand that is
-// reused (quadrature-point coefficients in stage 1, stage-1 buffers in stage
-// 2, stage-2 buffers in stage 3) in registers and streams the 1D factor
-// patterns from shared memory, laid out [a][b][pattern][k] so that stage 3
-// reads them as broadcast float4 loads (one load feeds four FMAs).  Each
-// element matrix is assembled in shared memory (upper triangle computed,
-// mirrored there) and written with coalesced stores when it fits, else stored
-// directly.  MODE: 0 = stiffness and mass, 1 = stiffness only, 2 = mass only.
+// Stage 3 is a dense GEMM per element on the tensor cores:
+//   K[(a1 + n a')][(b1 + n b')] = sum_{X,k1} C^X[(a',b')][k1] P^X_x[(a1,b1)][k1]
+// with rows (a',b') over the symmetric pairs a' <= b' only, columns (a1,b1)
+// and depth (x pattern X, k1); every result is written to (a,b) and, off the
+// diagonal blocks, mirrored to (b,a).  FP32 form: 3xTF32 (operands split into
+// TF32 hi + lo; hi*hi + hi*lo + lo*hi, FP32 accumulation) with
+// mma.sync.m16n8k8.tf32.  BF16 form: bf16 stage-2 operand, x patterns split
+// into bf16 hi + lo, mma.sync.m16n8k16.bf16, FP32 accumulation.  Each element
+// matrix is assembled in shared memory and written with coalesced 16-byte
+// stores when it fits, else scattered to HBM directly.
+// MODE: 0 = stiffness and mass, 1 = stiffness only, 2 = mass only.
 #include <cuda_bf16.h>
 
 #include "iga_internal.h"
@@ -41,6 +42,7 @@ struct SF3F {
   static constexpr int NT = 256;
   static constexpr int REC = 2 * q * n + q;
   static constexpr size_t al4(size_t x) { return (x + 3) / 4 * 4; }
+  static constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
   // pattern records, floats: x [a1][b1][4][q] (11, 00, 10, 01); y [a2][b2][4][q]
   // (00, 11, 10, 01); z [a3][b3][3][q] (00, 11, 01)
   static constexpr int RW = 4 * q;
@@ -49,26 +51,25 @@ struct SF3F {
   static constexpr size_t f_coef = al4((size_t)7 * Q);
   // stage-1 buffers T[7][a3][b3][k1][k2] (same indices as the coefficients)
   static constexpr size_t f_T1 = al4((size_t)7 * n2 * q * q);
-  // stage-2 buffers: FP32 form Cs [3: C11, C00, CM][NSp][q] and C10 [Np][Np][q]
-  static constexpr size_t f_Cs32 = al4((size_t)3 * NSp * q);
-  static constexpr size_t f_C10 = (GEN && !BF) ? al4((size_t)Np * Np * q) : 0;
-  // BF16 form: GEMM operands A_K [MP][LDK], A_M [MP][LDM], B_K and B_M hi/lo
-  static constexpr int al16i(int x) { return (x + 15) / 16 * 16; }
+  // stage-3 GEMM: A rows = symmetric pairs (padded to 16), depth padded to the k-step
   static constexpr int NXK = GEN ? 4 : 2;
-  static constexpr int KK = al16i(NXK * q), KM = al16i(q);
-  static constexpr int LDK = KK + 8, LDM = KM + 8;
-  static constexpr int MP = al16i(Np * Np);
-  static constexpr int NPAD = (n2 + 7) / 8 * 8;
-  static constexpr size_t h_A = (size_t)MP * ((DK ? LDK : 0) + (DM ? LDM : 0));
-  static constexpr size_t h_B = (size_t)2 * NPAD * ((DK ? LDK : 0) + (DM ? LDM : 0));
-  static constexpr size_t f_Cs = BF ? al4((h_A + h_B + 1) / 2) : f_Cs32;
+  static constexpr int KSTEP = BF ? 16 : 8;
+  static constexpr int KA = rup(NXK * q, KSTEP), KAM = rup(q, KSTEP);
+  static constexpr int LDA = KA + 4, LDAM = KAM + 4;          // FP32 A row strides (words)
+  static constexpr int MPs = rup(NSp, 16);
+  static constexpr int NPAD = rup(n2, 8);
+  static constexpr int LDB = BF ? (KA + 8) / 2 : KA + 4;        // B row strides (words)
+  static constexpr int LDBM = BF ? (KAM + 8) / 2 : KAM + 4;
+  static constexpr size_t f_A = (size_t)MPs * ((DK ? LDA : 0) + (DM ? LDAM : 0));
+  static constexpr size_t f_B = (size_t)2 * NPAD * ((DK ? LDB : 0) + (DM ? LDBM : 0));
   static constexpr size_t f_out = al4((size_t)N * N);
   static constexpr size_t d_geo = 3 * REC + 2 * (size_t)Q + (GEN ? 9 * (size_t)Q : 0);
   static constexpr size_t f_recf = al4(3 * REC);
   // aliased region: {T1, coef, geometry staging, FP32 records} until stage 2
   // ends, then the output stage
   static constexpr size_t f_alias = f_T1 + f_coef + 2 * d_geo + f_recf;
-  static constexpr size_t f_fixed = f_px + f_py + f_pz + f_Cs + f_C10;
+  static constexpr size_t f_A4 = al4(f_A), f_B4 = al4(f_B);
+  static constexpr size_t f_fixed = f_px + f_py + f_pz + f_A4 + f_B4;
   static constexpr size_t f_pairs = al4((size_t)NSp);
   static constexpr bool STAGE =
       4 * (f_fixed + (f_alias > f_out ? f_alias : f_out) + f_pairs) <= 200 * 1024;
@@ -84,15 +85,41 @@ __device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, cons
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Stage 3 of the BF16 form on the tensor cores: for one element,
-//   OUT[(a',b')][(a1,b1)] = sum_k A[(a',b')][k] * (Bhi + Blo)[(a1,b1)][k],
-// k = (x pattern, k1), FP32 accumulation, scattered to K[a1 + n a'][b1 + n b'].
-// Warp w takes the 16-row tiles w, w+8, ...; the fragments follow the
-// m16n8k16 register layout (row g = lane/4, column pair 2*(lane%4)).
-template <class C, int LD, int KS>
-__device__ __forceinline__ void gemm_scatter(const __nv_bfloat16* Am, const __nv_bfloat16* Bm,
-                                             float* dst_stage, float* dst_global) {
-  constexpr int n = C::n, N = C::N, Np = C::Np, NTN = C::NPAD / 8, MT = C::MP / 16;
+__device__ __forceinline__ void mma_tf32_1688(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *(const uint32_t*)&v;
+}
+
+// packed index of (a', b'), a' <= b', in the upper triangle of an Np x Np matrix
+template <int Np>
+__device__ __forceinline__ int upper_index(int ap, int bp) {
+  return ap * Np - (ap * (ap - 1)) / 2 + (bp - ap);
+}
+
+// Stage 3 on the tensor cores for one matrix.  A: [MPs][LDA_] FP32 (rows =
+// symmetric pairs), B: hi and lo [2][NPAD][LDB_] (tf32 bit patterns or bf16x2
+// words).  Warp w takes the 16-row tiles w, w+8, ...; fragments follow the
+// m16n8k8 (TF32) / m16n8k16 (BF16) register layouts: row g = lane/4, column
+// pair 2*(lane%4).
+template <class C, int LDA_, int LDB_, int KS>
+__device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, const int* pairs,
+                                         float* dst_stage, float* dst_global) {
+  constexpr int n = C::n, N = C::N, NSp = C::NSp, NTN = C::NPAD / 8, MT = C::MPs / 16;
+  constexpr bool BF = C::KSTEP == 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   uint32_t bh[NTN][KS][2], bl[NTN][KS][2];
@@ -100,51 +127,110 @@ __device__ __forceinline__ void gemm_scatter(const __nv_bfloat16* Am, const __nv
   for (int nt = 0; nt < NTN; ++nt)
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
-      const __nv_bfloat16* r0 = Bm + (nt * 8 + g) * LD + ks * 16 + t * 2;
-      const __nv_bfloat16* r1 = Bm + (C::NPAD + nt * 8 + g) * LD + ks * 16 + t * 2;
-      bh[nt][ks][0] = *(const uint32_t*)r0;
-      bh[nt][ks][1] = *(const uint32_t*)(r0 + 8);
-      bl[nt][ks][0] = *(const uint32_t*)r1;
-      bl[nt][ks][1] = *(const uint32_t*)(r1 + 8);
+      const uint32_t* r0 = Bm + (nt * 8 + g) * LDB_;
+      const uint32_t* r1 = Bm + (C::NPAD + nt * 8 + g) * LDB_;
+      if (BF) {  // k pairs: word index = k / 2
+        bh[nt][ks][0] = r0[ks * 8 + t];
+        bh[nt][ks][1] = r0[ks * 8 + t + 4];
+        bl[nt][ks][0] = r1[ks * 8 + t];
+        bl[nt][ks][1] = r1[ks * 8 + t + 4];
+      } else {
+        bh[nt][ks][0] = r0[ks * 8 + t];
+        bh[nt][ks][1] = r0[ks * 8 + t + 4];
+        bl[nt][ks][0] = r1[ks * 8 + t];
+        bl[nt][ks][1] = r1[ks * 8 + t + 4];
+      }
     }
+  // column offsets of this lane's two columns in every N tile: direct (a1 N + b1)
+  // and mirrored (b1 N + a1); -1 marks padding columns
+  int cd[NTN][2], cm[NTN][2];
+#pragma unroll
+  for (int nt = 0; nt < NTN; ++nt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int nn = nt * 8 + 2 * t + h;
+      const int a1 = nn / n, b1 = nn % n;
+      cd[nt][h] = nn < n * n ? a1 * N + b1 : -1;
+      cm[nt][h] = b1 * N + a1;
+    }
+  float* dst = C::STAGE ? dst_stage : dst_global;
   for (int mt = warp; mt < MT; mt += C::NT / 32) {
-    uint32_t a[KS][4];
+    uint32_t ah[KS][4], al[KS][4];
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
-      const __nv_bfloat16* r0 = Am + (mt * 16 + g) * LD + ks * 16 + t * 2;
-      const __nv_bfloat16* r1 = r0 + 8 * LD;
-      a[ks][0] = *(const uint32_t*)r0;
-      a[ks][1] = *(const uint32_t*)r1;
-      a[ks][2] = *(const uint32_t*)(r0 + 8);
-      a[ks][3] = *(const uint32_t*)(r1 + 8);
+      const float* r0 = Am + (mt * 16 + g) * LDA_;
+      const float* r1 = r0 + 8 * LDA_;
+      if (BF) {
+        const float2 x0 = *(const float2*)(r0 + ks * 16 + 2 * t);
+        const float2 x1 = *(const float2*)(r1 + ks * 16 + 2 * t);
+        const float2 x2 = *(const float2*)(r0 + ks * 16 + 2 * t + 8);
+        const float2 x3 = *(const float2*)(r1 + ks * 16 + 2 * t + 8);
+        ah[ks][0] = pack_bf16x2(x0.x, x0.y);
+        ah[ks][1] = pack_bf16x2(x1.x, x1.y);
+        ah[ks][2] = pack_bf16x2(x2.x, x2.y);
+        ah[ks][3] = pack_bf16x2(x3.x, x3.y);
+      } else {
+        const float x[4] = {r0[ks * 8 + t], r1[ks * 8 + t], r0[ks * 8 + t + 4], r1[ks * 8 + t + 4]};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ah[ks][i] = to_tf32(x[i]);
+          al[ks][i] = to_tf32(x[i] - __uint_as_float(ah[ks][i]));
+        }
+      }
+    }
+    // row bases of this lane's two rows: direct n (a' N + b'), mirrored n (b' N + a')
+    int rd[2], rm[2];
+    bool rv[2], off[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = mt * 16 + g + 8 * h;
+      rv[h] = m < NSp;
+      const int pr = rv[h] ? pairs[m] : 0;
+      const int ap = pr >> 16, bp = pr & 0xffff;
+      rd[h] = n * (ap * N + bp);
+      rm[h] = n * (bp * N + ap);
+      off[h] = ap != bp;
     }
 #pragma unroll
     for (int nt = 0; nt < NTN; ++nt) {
       float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
-        mma_bf16_16816(c, a[ks], bh[nt][ks]);
-        mma_bf16_16816(c, a[ks], bl[nt][ks]);
+        if (BF) {
+          mma_bf16_16816(c, ah[ks], bh[nt][ks]);
+          mma_bf16_16816(c, ah[ks], bl[nt][ks]);
+        } else {
+          mma_tf32_1688(c, ah[ks], bh[nt][ks]);
+          mma_tf32_1688(c, ah[ks], bl[nt][ks]);
+          mma_tf32_1688(c, al[ks], bh[nt][ks]);
+        }
       }
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        const int m = mt * 16 + g + (h >> 1) * 8;
-        const int nn = nt * 8 + t * 2 + (h & 1);
-        if (m < Np * Np && nn < n * n) {
-          const int ap = m / Np, bp = m % Np, a1 = nn / n, b1 = nn % n;
-          const int idx = (a1 + n * ap) * N + b1 + n * bp;
-          if (C::STAGE) dst_stage[idx] = c[h];
-          else dst_global[idx] = c[h];
+        const int r = h >> 1, cc = h & 1;
+        if (rv[r] && cd[nt][cc] >= 0) {
+          dst[rd[r] + cd[nt][cc]] = c[h];
+          if (off[r]) dst[rm[r] + cm[nt][cc]] = c[h];
         }
       }
     }
   }
 }
 
-// packed index of (a', b'), a' <= b', in the upper triangle of an Np x Np matrix
-template <int Np>
-__device__ __forceinline__ int upper_index(int ap, int bp) {
-  return ap * Np - (ap * (ap - 1)) / 2 + (bp - ap);
+// Copy one staged element matrix (N*N floats) to HBM: scalar head up to a
+// 16-byte boundary of the destination, 16-byte stores, scalar tail.
+template <int NN, int NT>
+__device__ __forceinline__ void copy_out(const float* __restrict__ s, float* __restrict__ g) {
+  const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
+  const int h = head < NN ? head : NN;
+  for (int i = threadIdx.x; i < h; i += NT) g[i] = s[i];
+  const int nv = (NN - h) / 4;
+  float4* g4 = (float4*)(g + h);
+  for (int i = threadIdx.x; i < nv; i += NT) {
+    const int j = h + 4 * i;
+    g4[i] = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
+  }
+  for (int i = h + 4 * nv + threadIdx.x; i < NN; i += NT) g[i] = s[i];
 }
 
 // One element, all stages.  Called by the per-patch kernel (e = blockIdx.x)
@@ -158,9 +244,11 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   float* px = smf;                                   // [n2][4][q]
   float* py = px + C::f_px;                          // [n2][4][q]
   float* pz = py + C::f_py;                          // [n2][3][q]
-  float* Cs = pz + C::f_pz;                          // [3][NSp][q]  (or the BF16 operands)
-  float* C10 = Cs + C::f_Cs;                         // [Np][Np][q]
-  float* region = C10 + C::f_C10;
+  float* AK = pz + C::f_pz;                          // [MPs][LDA]   stiffness GEMM operand
+  float* AM = AK + (DK ? (size_t)C::MPs * C::LDA : 0);  // [MPs][LDAM]  mass GEMM operand
+  uint32_t* BK = (uint32_t*)(AK + C::f_A4);   // [2][NPAD][LDB]
+  uint32_t* BM = BK + (DK ? (size_t)2 * C::NPAD * C::LDB : 0);  // [2][NPAD][LDBM]
+  float* region = (float*)BK + C::f_B4;
   float* T1 = region;                                // [7][n2][q][q]
   float* coef = T1 + C::f_T1;                        // [7][Q]
   double* geo = (double*)(coef + C::f_coef);
@@ -171,10 +259,6 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   float* recf = (float*)(geo + C::d_geo);            // [3][REC]
   float* outs = region;                              // [N][N] after stage 2
   int* pairs = (int*)(region + C::f_region);         // [NSp] packed (a' << 16 | b')
-  __nv_bfloat16* AK = (__nv_bfloat16*)Cs;
-  __nv_bfloat16* AM = AK + (DK ? (size_t)C::MP * C::LDK : 0);
-  __nv_bfloat16* BK = AM + (DM ? (size_t)C::MP * C::LDM : 0);
-  __nv_bfloat16* BM = BK + (DK ? (size_t)2 * C::NPAD * C::LDK : 0);
 
   const int tid = threadIdx.x;
   const int e1 = (int)(e % A.K1);
@@ -182,7 +266,7 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
   __syncthreads();  // shared memory of the previous element is no longer read
 
-  // ---- coalesced staging of this element's inputs --------------------------
+  // ---- coalesced staging of this element's inputs; zero the GEMM operands -------
   for (int i = tid; i < 3 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
@@ -202,6 +286,7 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
     while (r >= Np - a) { r -= Np - a; ++a; }
     pairs[i] = (a << 16) | (a + r);
   }
+  for (int i = tid; i < (int)C::f_A; i += NT) AK[i] = 0.f;
   __syncthreads();
   for (int i = tid; i < 3 * REC; i += NT) recf[i] = (float)rec[i];
   __syncthreads();
@@ -259,35 +344,45 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
       coef[3 * Q + k] = W * rh;
     }
   }
-  if constexpr (BF) {
-    // zero every GEMM operand (padding rows and columns must be zero)
-    uint32_t* z = (uint32_t*)Cs;
-    for (size_t i = tid; i < (C::h_A + C::h_B) / 2; i += NT) z[i] = 0u;
-  }
   __syncthreads();
 
-  if constexpr (BF) {
-    // B operand: x patterns split into bf16 hi + lo, B[(a1,b1)][X q + k1]
-    if (DK) {
-      for (int i = tid; i < n2 * C::NXK * q; i += NT) {
-        const int nn = i / (C::NXK * q), kx = i % (C::NXK * q);
-        const float v = px[nn * RW + kx];  // record order 11, 00, 10, 01 matches X
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        BK[nn * C::LDK + kx] = hi;
-        BK[(C::NPAD + nn) * C::LDK + kx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+  // ---- B operands: x patterns split into hi + lo (TF32 bits or bf16 pairs) ------
+  // B[(a1,b1)][X q + k1] = P^X_x[a1][b1][k1] in the record order 11, 00, 10, 01
+  // (the same X order as the A columns); mass: B[(a1,b1)][k1] = P^00_x
+#pragma unroll 1
+  for (int mat = 0; mat < 2; ++mat) {
+    if ((mat == 0 && !DK) || (mat == 1 && !DM)) continue;
+    uint32_t* Bm = mat == 0 ? BK : BM;
+    const int ld = mat == 0 ? C::LDB : C::LDBM;
+    const int kdepth = mat == 0 ? C::KA : C::KAM;
+    const int kvalid = mat == 0 ? C::NXK * q : q;
+    const int kofs = mat == 0 ? 0 : q;
+    if (BF) {
+      for (int i = tid; i < C::NPAD * (kdepth / 2); i += NT) {
+        const int nn = i / (kdepth / 2), kw = i % (kdepth / 2);
+        float v[2], hv[2];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+          const int k = 2 * kw + s2;
+          v[s2] = (nn < n2 && k < kvalid) ? px[nn * RW + kofs + k] : 0.f;
+          hv[s2] = __bfloat162float(__float2bfloat16_rn(v[s2]));
+        }
+        Bm[nn * ld + kw] = pack_bf16x2(hv[0], hv[1]);
+        Bm[(C::NPAD + nn) * ld + kw] = pack_bf16x2(v[0] - hv[0], v[1] - hv[1]);
       }
-    }
-    if (DM) {
-      for (int i = tid; i < n2 * q; i += NT) {
-        const int nn = i / q, k1 = i % q;
-        const float v = px[nn * RW + q + k1];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        BM[nn * C::LDM + k1] = hi;
-        BM[(C::NPAD + nn) * C::LDM + k1] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    } else {
+      for (int i = tid; i < C::NPAD * kdepth; i += NT) {
+        const int nn = i / kdepth, k = i % kdepth;
+        const float v = (nn < n2 && k < kvalid) ? px[nn * RW + kofs + k] : 0.f;
+        const uint32_t hi = to_tf32(v);
+        Bm[nn * ld + k] = hi;
+        Bm[(C::NPAD + nn) * ld + k] = to_tf32(v - __uint_as_float(hi));
       }
     }
   }
 
+  const float* Pz = pz;
+  const float* Py = py;
   // ---- stage 1: T_t[a3][b3][k1][k2] = sum_k3 Z_t[a3][b3][k3] D_t[k1,k2,k3] -------
   // item = (k1, k2, a3), coefficients of the item in registers, loop over b3
   for (int it = tid; it < q * q * n; it += NT) {
@@ -305,7 +400,7 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
     }
 #pragma unroll 1
     for (int b3 = 0; b3 < n; ++b3) {
-      const float* z = pz + (a3 * n + b3) * 3 * q;
+      const float* z = Pz + (a3 * n + b3) * 3 * q;
       float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f, t6 = 0.f;
 #pragma unroll
       for (int k3 = 0; k3 < q; ++k3) {
@@ -333,17 +428,17 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   }
   __syncthreads();
 
-  // ---- stage 2 ----------------------------------------------------------------
+  // ---- stage 2: the GEMM operand rows (a',b'), a' <= b' --------------------------
   {
     constexpr int S = n2 * q * q;
     constexpr int T11 = GEN ? 1 : 0;
-    // (a) symmetric buffers C11, C00, CM for a' <= b': item = (a3 <= b3, k1, a2)
+    // (a) C11, C00, CM: item = (a3 <= b3, k1, a2)
     for (int it = tid; it < NS1 * q * n; it += NT) {
       const int a2 = it % n, r = it / n, k1 = r % q, ps = r / q;
       int a3 = 0, rr = ps;
       while (rr >= n - a3) { rr -= n - a3; ++a3; }
       const int b3 = a3 + rr;
-      // T layout [t][a3][b3][k1][k2] with k1 + q k2 = kk: element (k1, k2) at k1 + q k2
+      // T layout [t][a3][b3][k1 + q k2]
       const int ab3 = (a3 * n + b3) * q * q + k1, ba3 = (b3 * n + a3) * q * q + k1;
       float t00[q], t11[q], t22[q], tab[q], tba[q], tm[q];
 #pragma unroll
@@ -359,47 +454,37 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
       const int ap = a2 + n * a3;
 #pragma unroll 1
       for (int b2 = (a3 == b3 ? a2 : 0); b2 < n; ++b2) {
-        const float* y = py + (a2 * n + b2) * RW;  // 00, 11, 10, 01
+        const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);  // 00, 11, 10, 01
+        float y[RW];
+#pragma unroll
+        for (int v = 0; v < RW / 4; ++v) {
+          const float4 w4 = y4[v];
+          y[4 * v] = w4.x; y[4 * v + 1] = w4.y; y[4 * v + 2] = w4.z; y[4 * v + 3] = w4.w;
+        }
         float c11 = 0.f, c00a = 0.f, c00b = 0.f, cm = 0.f;
 #pragma unroll
         for (int k2 = 0; k2 < q; ++k2) {
-          const float y00 = y[k2], y11 = y[q + k2], y10 = y[2 * q + k2], y01 = y[3 * q + k2];
           if (DK) {
-            c11 = fmaf(y00, t00[k2], c11);
-            c00a = fmaf(y11, t11[k2], c00a);
-            c00b = fmaf(y00, t22[k2], c00b);
+            c11 = fmaf(y[k2], t00[k2], c11);
+            c00a = fmaf(y[q + k2], t11[k2], c00a);
+            c00b = fmaf(y[k2], t22[k2], c00b);
             if (GEN) {
-              c00a = fmaf(y10, tab[k2], c00a);
-              c00b = fmaf(y01, tba[k2], c00b);
+              c00a = fmaf(y[2 * q + k2], tab[k2], c00a);
+              c00b = fmaf(y[3 * q + k2], tba[k2], c00b);
             }
           }
-          if (DM) cm = fmaf(y00, tm[k2], cm);
+          if (DM) cm = fmaf(y[k2], tm[k2], cm);
         }
-        const int bp = b2 + n * b3;
-        if constexpr (BF) {
-          if (DK) {
-            const __nv_bfloat16 h11 = __float2bfloat16_rn(c11), h00 = __float2bfloat16_rn(c00a + c00b);
-            AK[(ap * Np + bp) * C::LDK + 0 * q + k1] = h11;
-            AK[(bp * Np + ap) * C::LDK + 0 * q + k1] = h11;
-            AK[(ap * Np + bp) * C::LDK + 1 * q + k1] = h00;
-            AK[(bp * Np + ap) * C::LDK + 1 * q + k1] = h00;
-          }
-          if (DM) {
-            const __nv_bfloat16 hm = __float2bfloat16_rn(cm);
-            AM[(ap * Np + bp) * C::LDM + k1] = hm;
-            AM[(bp * Np + ap) * C::LDM + k1] = hm;
-          }
-        } else {
-          const int pp = upper_index<Np>(ap, bp);
-          if (DK) {
-            Cs[(0 * NSp + pp) * q + k1] = c11;
-            Cs[(1 * NSp + pp) * q + k1] = c00a + c00b;
-          }
-          if (DM) Cs[(2 * NSp + pp) * q + k1] = cm;
+        const int pp = upper_index<Np>(ap, b2 + n * b3);
+        if (DK) {
+          AK[pp * C::LDA + 0 * q + k1] = c11;
+          AK[pp * C::LDA + 1 * q + k1] = c00a + c00b;
         }
+        if (DM) AM[pp * C::LDAM + k1] = cm;
       }
     }
-    // (b) C10[a'][b'][k1] for all (a', b'): item = (a3, b3, k1, a2)
+    // (b) C10[a'][b'] for all (a', b'): row pp(a',b') column 2q+k1 when a' <= b'
+    // and, as C01 of the row pp(b',a'), column 3q+k1 when b' <= a'
     if (GEN && DK) {
       for (int it = tid; it < n2 * q * n; it += NT) {
         const int a2 = it % n, r = it / n, k1 = r % q, ab = r / q;
@@ -414,115 +499,44 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
         const int ap = a2 + n * a3;
 #pragma unroll 1
         for (int b2 = 0; b2 < n; ++b2) {
-          const float* y = py + (a2 * n + b2) * RW;
+          const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);
+          float y[RW];
+#pragma unroll
+          for (int v = 0; v < RW / 4; ++v) {
+            const float4 w4 = y4[v];
+            y[4 * v] = w4.x; y[4 * v + 1] = w4.y; y[4 * v + 2] = w4.z; y[4 * v + 3] = w4.w;
+          }
           float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
           for (int k2 = 0; k2 < q; ++k2) {
             acc0 = fmaf(y[3 * q + k2], t01[k2], acc0);  // y01 with z00 D01 (term (0,1))
             acc1 = fmaf(y[k2], t02[k2], acc1);          // y00 with z01 D02 (term (0,2))
           }
+          const float val = acc0 + acc1;
           const int bp = b2 + n * b3;
-          if constexpr (BF) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(acc0 + acc1);
-            AK[(ap * Np + bp) * C::LDK + 2 * q + k1] = h;  // C10[a'][b']
-            AK[(bp * Np + ap) * C::LDK + 3 * q + k1] = h;  // C01[b'][a'] = C10[a'][b']
-          } else {
-            C10[(ap * Np + bp) * q + k1] = acc0 + acc1;
-          }
+          if (ap <= bp) AK[upper_index<Np>(ap, bp) * C::LDA + 2 * q + k1] = val;
+          if (bp <= ap) AK[upper_index<Np>(bp, ap) * C::LDA + 3 * q + k1] = val;
         }
       }
     }
   }
   __syncthreads();
 
-  if constexpr (BF) {
-#pragma unroll 1
-    for (int mat = 0; mat < 2; ++mat) {
-      const bool isK = mat == 0;
-      if ((isK && !DK) || (!isK && !DM)) continue;
-      float* dst = (float*)(isK ? A.K_out : A.M_out);
-      if (!dst) continue;
-      float* g = dst + e * (int64_t)N * N;
-      if (isK) gemm_scatter<C, C::LDK, C::KK / 16>(AK, BK, outs, g);
-      else gemm_scatter<C, C::LDM, C::KM / 16>(AM, BM, outs, g);
-      if (C::STAGE) {
-        __syncthreads();
-        for (int i = tid; i < N * N; i += NT) g[i] = outs[i];
-        __syncthreads();
-      }
-    }
-  } else {
-
-  // ---- stage 3 (FP32): item = (a', b'), a' <= b'; its stage-2 values in
-  // registers, the x pattern record of (a1, b1) streamed as float4 -------------
+  // ---- stage 3 on the tensor cores, one matrix at a time ---------------------------
 #pragma unroll 1
   for (int mat = 0; mat < 2; ++mat) {
-    const bool isK = (mat == 0);
+    const bool isK = mat == 0;
     if ((isK && !DK) || (!isK && !DM)) continue;
     float* dst = (float*)(isK ? A.K_out : A.M_out);
     if (!dst) continue;
     float* g = dst + e * (int64_t)N * N;
-    for (int pp = tid; pp < NSp; pp += NT) {
-      const int pr = pairs[pp];
-      const int ap = pr >> 16, bp = pr & 0xffff;
-      float c0[q], c1[q], c2[q], c3[q];
-#pragma unroll
-      for (int k = 0; k < q; ++k) {
-        if (isK) {
-          c0[k] = Cs[(0 * NSp + pp) * q + k];
-          c1[k] = Cs[(1 * NSp + pp) * q + k];
-          if (GEN) {
-            c2[k] = C10[(ap * Np + bp) * q + k];
-            c3[k] = C10[(bp * Np + ap) * q + k];
-          }
-        } else {
-          c1[k] = Cs[(2 * NSp + pp) * q + k];
-        }
-      }
-#pragma unroll 1
-      for (int a1 = 0; a1 < n; ++a1) {
-        const int ra = a1 + n * ap;
-#pragma unroll
-        for (int b1 = 0; b1 < n; ++b1) {
-          const float4* x4 = (const float4*)(px + (a1 * n + b1) * RW);
-          float xr[RW];
-#pragma unroll
-          for (int v = 0; v < RW / 4; ++v) {
-            const float4 t4 = x4[v];
-            xr[4 * v] = t4.x; xr[4 * v + 1] = t4.y; xr[4 * v + 2] = t4.z; xr[4 * v + 3] = t4.w;
-          }
-          float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-          for (int k = 0; k < q; ++k) {
-            if (isK) {
-              acc0 = fmaf(xr[k], c0[k], acc0);          // x11 * C11
-              acc1 = fmaf(xr[q + k], c1[k], acc1);      // x00 * C00
-              if (GEN) {
-                acc0 = fmaf(xr[2 * q + k], c2[k], acc0);  // x10 * C10
-                acc1 = fmaf(xr[3 * q + k], c3[k], acc1);  // x01 * C01
-              }
-            } else {
-              acc1 = fmaf(xr[q + k], c1[k], acc1);      // x00 * CM
-            }
-          }
-          const float val = acc0 + acc1;
-          const int rb = b1 + n * bp;
-          if (C::STAGE) {
-            outs[ra * N + rb] = val;
-            if (ap != bp) outs[rb * N + ra] = val;
-          } else {
-            g[(int64_t)ra * N + rb] = val;
-            if (ap != bp) g[(int64_t)rb * N + ra] = val;
-          }
-        }
-      }
-    }
+    if (isK) gemm_sym<C, C::LDA, C::LDB, C::KA / C::KSTEP>(AK, BK, pairs, outs, g);
+    else gemm_sym<C, C::LDAM, C::LDBM, C::KAM / C::KSTEP>(AM, BM, pairs, outs, g);
     if (C::STAGE) {
       __syncthreads();
-      for (int i = tid; i < N * N; i += NT) g[i] = outs[i];
+      copy_out<N * N, NT>(outs, g);
       __syncthreads();
     }
-  }
   }
 }
 
