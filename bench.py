@@ -33,6 +33,10 @@ L2_BYTES = 129 * 1024 * 1024
 # measurement and the derivation of the peak.
 DFMA_PER_SM_CLK = 2.0
 N_SM = 152
+# FP32 operations of one float-float multiply-add (product with its exact
+# error, two-sum, renormalisation); the float-float roofline divides the FP32
+# issue rate by this count.
+DF_OPS_PER_FMA = 14
 
 
 def flops_per_element(dim, p, q, stiffness, mass, general_geometry):
@@ -255,7 +259,7 @@ def run_ours(args, ws, rank, local):
     value = ws * E * args.steps / (total_ms / 1e3)
 
     # roofline of the dominant kernel (the element-matrix kernel)
-    esize = 8 if args.precision == "fp64" else 4
+    esize = 8 if args.precision in ("fp64", "fp64_df") else 4
     peaks, peak_src = measured_peaks()
     launch_ms = kern_ms / max(1, launches)
     if args.method == "sumfact":
@@ -263,16 +267,23 @@ def run_ours(args, ws, rank, local):
     else:
         f_el = classical_flops_per_element(len(sp.knots), sp.p, sp.q, True, mass)
     b_el = bytes_per_element(len(sp.knots), sp.p, sp.q, esize, True, mass, general, dof=False)
-    if args.precision == "fp64":
-        peak_tf = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if args.precision in ("fp64", "fp64_df"):
+        if args.precision == "fp64":
+            peak_tf = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = (f"FP64 CUDA cores: {N_SM} SMs x {DFMA_PER_SM_CLK:g} DFMA/clk x 2 x "
+                   f"{peaks.get('sm_max_mhz', 2070.0):g} MHz")
+        else:
+            # float-float: one FP64-equivalent multiply-add = DF_OPS_PER_FMA FP32 operations
+            peak_tf = (N_SM * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / DF_OPS_PER_FMA * 2) / 1e12
+            src = (f"FP32 pipes: {N_SM} SMs x 128 lanes x {peaks.get('sm_max_mhz', 2070.0):g} MHz / "
+                   f"{DF_OPS_PER_FMA} FP32 ops per float-float multiply-add x 2 flops")
         achieved = f_el * E / (launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
                 "traffic": None,
                 "flop_per_element": f_el, "elements_per_launch": E,
                 "launch_ms": round(launch_ms, 4),
-                "peak_source": f"FP64 CUDA cores: {N_SM} SMs x {DFMA_PER_SM_CLK:g} DFMA/clk x 2 x "
-                               f"{peaks.get('sm_max_mhz', 2070.0):g} MHz",
+                "peak_source": src,
                 "hbm_frac": round(b_el * E / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src}
     else:
@@ -342,7 +353,8 @@ def run_ours(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
+        "dtype": {"fp64": "f64", "fp64_df": "f32x2 (float-float, FP64-accurate)", "fp32": "f32",
+                  "bf16": "bf16"}[args.precision],
         "data": "synthetic (seeded lognormal kappa, open uniform knots)",
         "config": {"workload": args.workload, "dim": len(sp.knots), "degree": sp.p,
                    "elements": E, "gauss_per_dir": sp.q, "method": args.method,
@@ -384,6 +396,7 @@ FORM_ERR = {
     "classical_fp64": {"tolerance": 1e-12},
     "sumfact_fp32": {"tolerance": 1e-5},
     "sumfact_bf16": {"tolerance": 5e-3},
+    "sumfact_fp64_df": {"tolerance": 1e-12},
 }
 
 
@@ -403,7 +416,8 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
                                                  **FORM_ERR.get(f"{args.method}_{args.precision}", {})}}
     variants = [("classical", "fp64")]
     if args.method == "sumfact":
-        variants += [("sumfact", pr) for pr in ("fp64", "fp32", "bf16") if pr != args.precision]
+        variants += [("sumfact", pr) for pr in ("fp64", "fp64_df", "fp32", "bf16")
+                     if pr != args.precision]
     for meth, pr in variants:
         key = f"{meth}_{pr}"
         try:
@@ -541,7 +555,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_p3_32")
     ap.add_argument("--method", default="sumfact", choices=["sumfact", "classical"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_df", "fp32", "bf16"])
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-compare", dest="compare", action="store_false")

@@ -29,8 +29,8 @@
  *   jac:      [n_qp][d][d] doubles, jac[..][i][j] = d x_i / d xi_j with xi
  *             the knot (parametric) coordinate; |det| is the J(x^n) of eq. 10;
  *   K_out, M_out: per patch [E][N][N] row-major, patches concatenated
- *             (offsets in iga_plan_info.mat_offset), double for IGA_FP64,
- *             float for IGA_FP32 and IGA_BF16;
+ *             (offsets in iga_plan_info.mat_offset), double for IGA_FP64 and
+ *             IGA_FP64_DF, float for IGA_FP32 and IGA_BF16;
  *   dof_out:  per patch [E][N] int32, concatenated (iga_plan_info.dofmap_offset).
  *
  * Ownership: every pointer passed to iga_integrate/iga_integrate_backward is
@@ -68,7 +68,13 @@ typedef enum {
 } iga_status;
 
 enum { IGA_CLASSICAL = 0, IGA_SUMFACT = 1 };
-enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_BF16 = 2 };
+/* Precisions.  IGA_FP64: FP64 arithmetic.  IGA_FP32: FP64 Jacobian cofactors
+ * and determinant, FP32 contractions (stage 3 as 3xTF32 on the tensor cores).
+ * IGA_BF16: as FP32 with the last contraction in BF16 on the tensor cores (FP32
+ * accumulation).  IGA_FP64_DF: FP64-accurate results (double outputs, tested
+ * to <= 1e-12 per element like IGA_FP64) computed in float-float arithmetic
+ * (pairs of FP32 numbers) on the FP32 pipes; sum factorization in 3D only. */
+enum { IGA_FP64 = 0, IGA_FP32 = 1, IGA_BF16 = 2, IGA_FP64_DF = 3 };
 enum { IGA_MASS = 1, IGA_STIFF = 2 };
 
 /* Schedules (iga_plan_opts.schedule).  AUTO picks PERSISTENT_GRAPH for FP32 or
@@ -99,7 +105,8 @@ typedef struct {
 
 typedef struct {
   int method;     /* IGA_CLASSICAL or IGA_SUMFACT */
-  int precision;  /* IGA_FP64, IGA_FP32 or IGA_BF16 (sum factorization only) */
+  int precision;  /* IGA_FP64, IGA_FP32, IGA_BF16 or IGA_FP64_DF (the last three
+                     for sum factorization only) */
   int matrices;   /* bitmask of IGA_MASS | IGA_STIFF */
   int schedule;   /* IGA_SCHED_*; 0 = automatic (autotuned) */
   int blocking;   /* 1 = synchronize the stream and return the device status */
@@ -149,7 +156,8 @@ int iga_integrate(iga_plan_t plan, const double* kappa, const double* rho,
  * at every quadrature point, computed by sum-factorized interpolation of u and
  * v from the basis tables (no element matrix is formed), and
  *   J_out = sum_k kappa_k grad_kappa[k]   (deterministic fixed-order reduction).
- * u, v: [n_dofs] global vectors; double for IGA_FP64 plans, float otherwise.
+ * u, v: [n_dofs] global vectors; double for IGA_FP64 and IGA_FP64_DF plans
+ * (both use the FP64 adjoint), float otherwise.
  * grad_kappa: [n_qp], same dtype as u.  J_out: one double, may be NULL.
  * kappa may be NULL only if J_out is NULL.  jac as for iga_integrate. */
 int iga_integrate_backward(iga_plan_t plan, const double* kappa, const double* jac,

@@ -30,6 +30,7 @@ IGA_SUMFACT = 1
 IGA_FP64 = 0
 IGA_FP32 = 1
 IGA_BF16 = 2
+IGA_FP64_DF = 3
 IGA_MASS = 1
 IGA_STIFF = 2
 IGA_SCHED_AUTO = 0

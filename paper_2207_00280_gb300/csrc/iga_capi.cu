@@ -124,6 +124,7 @@ bool method_supported(const iga_plan_opts& o, int dim, int p, int q) {
   }
   if (o.precision == IGA_FP32 || o.precision == IGA_BF16)
     return o.method == IGA_SUMFACT && sumfact_f32_supported(dim, p, q);
+  if (o.precision == IGA_FP64_DF) return o.method == IGA_SUMFACT && sumfact_df_supported(dim, p, q);
   return false;
 }
 
@@ -186,11 +187,12 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   if (!out || !patches || n_patches < 1 || !opts) return IGA_ERR_ARG;
   const iga_plan_opts o = *opts;
   if (o.method != IGA_CLASSICAL && o.method != IGA_SUMFACT) return IGA_ERR_ARG;
-  if (o.precision < IGA_FP64 || o.precision > IGA_BF16) return IGA_ERR_ARG;
+  if (o.precision < IGA_FP64 || o.precision > IGA_FP64_DF) return IGA_ERR_ARG;
   if (o.matrices < 1 || o.matrices > 3) return IGA_ERR_ARG;
   if (o.method == IGA_CLASSICAL && o.precision != IGA_FP64) return IGA_ERR_UNSUPPORTED;
   if (o.schedule < IGA_SCHED_AUTO || o.schedule > IGA_SCHED_PERSISTENT_GRAPH) return IGA_ERR_ARG;
-  const bool lowprec_sf = o.method == IGA_SUMFACT && o.precision != IGA_FP64;
+  const bool lowprec_sf =
+      o.method == IGA_SUMFACT && (o.precision == IGA_FP32 || o.precision == IGA_BF16);
   if (!lowprec_sf && o.schedule > IGA_SCHED_PER_PATCH) return IGA_ERR_UNSUPPORTED;
   const int dim = patches[0].dim;
   if (dim != 2 && dim != 3) return IGA_ERR_ARG;
@@ -402,7 +404,8 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
     return finish(P, st, e);
   }
   e = run_prologue(&pctx, st);
-  const size_t esz = (P->opts.precision == IGA_FP64) ? sizeof(double) : sizeof(float);
+  const bool dbl_out = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
+  const size_t esz = dbl_out ? sizeof(double) : sizeof(float);
   std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
   if (e == cudaSuccess && P->opts.profile && (want_K || want_M)) {
     if (P->prof_used == P->prof_events.size()) {
@@ -430,7 +433,9 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
     a.K_out = want_K ? (char*)K_out + esz * pd.mat_offset : nullptr;
     a.M_out = want_M ? (char*)M_out + esz * pd.mat_offset : nullptr;
     a.err = P->d_err;
-    if (P->opts.method == IGA_SUMFACT && P->opts.precision != IGA_FP64)
+    if (P->opts.method == IGA_SUMFACT && P->opts.precision == IGA_FP64_DF)
+      e = launch_sumfact_df(a, pd.dim, pd.p, pd.q, st);
+    else if (P->opts.method == IGA_SUMFACT && P->opts.precision != IGA_FP64)
       e = launch_sumfact_f32(a, pd.dim, pd.p, pd.q, P->opts.precision == IGA_BF16, st);
     else if (P->opts.method == IGA_SUMFACT)
       e = launch_sumfact_f64(a, pd.dim, pd.p, pd.q, st);
@@ -456,7 +461,7 @@ extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const d
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const bool fp64 = P->opts.precision == IGA_FP64;
+  const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
   const size_t gsz = fp64 ? sizeof(double) : sizeof(float);
   cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
                                       P->d_tables, st);

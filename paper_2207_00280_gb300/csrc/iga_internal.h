@@ -123,6 +123,10 @@ cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, cudaStream
 cudaError_t launch_reduce_fixed(const double* partial, int64_t n, double* out, cudaStream_t st);
 bool adjoint_supported(int dim, int p, int q);
 
+// FP64-accurate sum factorization in float-float arithmetic (3D).
+cudaError_t launch_sumfact_df(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
+bool sumfact_df_supported(int dim, int p, int q);
+
 bool sumfact_f64_supported(int dim, int p, int q);
 bool sumfact_f32_supported(int dim, int p, int q);
 bool classical_f64_supported(int dim, int p, int q);

@@ -62,7 +62,7 @@ struct SF3F {
   static constexpr int LDBM = BF ? (KAM + 8) / 2 : KAM + 4;
   static constexpr size_t f_A = (size_t)MPs * ((DK ? LDA : 0) + (DM ? LDAM : 0));
   static constexpr size_t f_B = (size_t)2 * NPAD * ((DK ? LDB : 0) + (DM ? LDBM : 0));
-  static constexpr size_t f_out = al4((size_t)N * N);
+  static constexpr size_t f_out = al4((size_t)N * N + 4);
   static constexpr size_t d_geo = 3 * REC + 2 * (size_t)Q + (GEN ? 9 * (size_t)Q : 0);
   static constexpr size_t f_recf = al4(3 * REC);
   // aliased region: {T1, coef, geometry staging, FP32 records} until stage 2
@@ -217,8 +217,16 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
   }
 }
 
+// The staged matrix starts stage_offset(g) floats into the stage buffer, so
+// that entry i sits on a 16-byte shared-memory boundary exactly when g + i
+// sits on a 16-byte global boundary.
+__device__ __forceinline__ int stage_offset(const float* g) {
+  const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
+  return (4 - head) & 3;
+}
+
 // Copy one staged element matrix (N*N floats) to HBM: scalar head up to a
-// 16-byte boundary of the destination, 16-byte stores, scalar tail.
+// 16-byte boundary of the destination, 16-byte loads and stores, scalar tail.
 template <int NN, int NT>
 __device__ __forceinline__ void copy_out(const float* __restrict__ s, float* __restrict__ g) {
   const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
@@ -226,11 +234,28 @@ __device__ __forceinline__ void copy_out(const float* __restrict__ s, float* __r
   for (int i = threadIdx.x; i < h; i += NT) g[i] = s[i];
   const int nv = (NN - h) / 4;
   float4* g4 = (float4*)(g + h);
-  for (int i = threadIdx.x; i < nv; i += NT) {
-    const int j = h + 4 * i;
-    g4[i] = make_float4(s[j], s[j + 1], s[j + 2], s[j + 3]);
-  }
+  const float4* s4 = (const float4*)(s + h);
+  for (int i = threadIdx.x; i < nv; i += NT) g4[i] = s4[i];
   for (int i = h + 4 * nv + threadIdx.x; i < NN; i += NT) g[i] = s[i];
+}
+
+// Once per CTA, before its first element: the table of symmetric pairs
+// (a',b'), and zeros in the GEMM operands (their padding rows and columns are
+// never written by the element stages).
+template <int P, int QG, bool GEN, int MODE, bool BF>
+__device__ __forceinline__ void sf3_f32_cta_setup(float* smf) {
+  using C = SF3F<P, QG, GEN, MODE, BF>;
+  constexpr int Np = C::Np, NSp = C::NSp, NT = C::NT;
+  float* AK = smf + C::f_px + C::f_py + C::f_pz;
+  float* region = AK + C::f_A4 + C::f_B4;
+  int* pairs = (int*)(region + C::f_region);
+  for (int i = threadIdx.x; i < NSp; i += NT) {
+    int a = 0, r = i;
+    while (r >= Np - a) { r -= Np - a; ++a; }
+    pairs[i] = (a << 16) | (a + r);
+  }
+  for (int i = threadIdx.x; i < (int)C::f_A; i += NT) AK[i] = 0.f;
+  __syncthreads();
 }
 
 // One element, all stages.  Called by the per-patch kernel (e = blockIdx.x)
@@ -281,12 +306,6 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
     const double* G = A.jac + e * Q * 9;
     for (int i = tid; i < 9 * Q; i += NT) jac[i] = G[i];
   }
-  for (int i = tid; i < NSp; i += NT) {
-    int a = 0, r = i;
-    while (r >= Np - a) { r -= Np - a; ++a; }
-    pairs[i] = (a << 16) | (a + r);
-  }
-  for (int i = tid; i < (int)C::f_A; i += NT) AK[i] = 0.f;
   __syncthreads();
   for (int i = tid; i < 3 * REC; i += NT) recf[i] = (float)rec[i];
   __syncthreads();
@@ -384,9 +403,13 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   const float* Pz = pz;
   const float* Py = py;
   // ---- stage 1: T_t[a3][b3][k1][k2] = sum_k3 Z_t[a3][b3][k3] D_t[k1,k2,k3] -------
-  // item = (k1, k2, a3), coefficients of the item in registers, loop over b3
-  for (int it = tid; it < q * q * n; it += NT) {
-    const int a3 = it % n, kk = it / n;  // kk = k1 + q k2
+  // item = (k1, k2, a3, part of the b3 range), coefficients of the item in
+  // registers, loop over its b3
+  constexpr int S1 = (q * q * n >= NT) ? 1 : ((NT / (q * q * n)) < n ? (NT / (q * q * n)) : n);
+  constexpr int CH = (n + S1 - 1) / S1;
+  for (int it = tid; it < q * q * n * S1; it += NT) {
+    const int part = it % S1, rest = it / S1;
+    const int a3 = rest % n, kk = rest / n;  // kk = k1 + q k2
     float d0[q], d1[q], d2[q], d3[q], d4[q], d5[q], d6[q];
 #pragma unroll
     for (int k3 = 0; k3 < q; ++k3) {
@@ -398,8 +421,9 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
         d5[k3] = coef[5 * Q + o]; d6[k3] = coef[6 * Q + o];
       }
     }
+    const int b3e = (part + 1) * CH < n ? (part + 1) * CH : n;
 #pragma unroll 1
-    for (int b3 = 0; b3 < n; ++b3) {
+    for (int b3 = part * CH; b3 < b3e; ++b3) {
       const float* z = Pz + (a3 * n + b3) * 3 * q;
       float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f, t6 = 0.f;
 #pragma unroll
@@ -452,8 +476,10 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
         if (DM) tm[k2] = T1[3 * S + ab3 + q * k2];
       }
       const int ap = a2 + n * a3;
+      const int b2s = (a3 == b3 ? a2 : 0);
+      int pp = upper_index<Np>(ap, b2s + n * b3);  // consecutive b2 -> consecutive rows
 #pragma unroll 1
-      for (int b2 = (a3 == b3 ? a2 : 0); b2 < n; ++b2) {
+      for (int b2 = b2s; b2 < n; ++b2, ++pp) {
         const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);  // 00, 11, 10, 01
         float y[RW];
 #pragma unroll
@@ -475,7 +501,6 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
           }
           if (DM) cm = fmaf(y[k2], tm[k2], cm);
         }
-        const int pp = upper_index<Np>(ap, b2 + n * b3);
         if (DK) {
           AK[pp * C::LDA + 0 * q + k1] = c11;
           AK[pp * C::LDA + 1 * q + k1] = c00a + c00b;
@@ -530,11 +555,12 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
     float* dst = (float*)(isK ? A.K_out : A.M_out);
     if (!dst) continue;
     float* g = dst + e * (int64_t)N * N;
-    if (isK) gemm_sym<C, C::LDA, C::LDB, C::KA / C::KSTEP>(AK, BK, pairs, outs, g);
-    else gemm_sym<C, C::LDAM, C::LDBM, C::KAM / C::KSTEP>(AM, BM, pairs, outs, g);
+    float* stage = outs + stage_offset(g);
+    if (isK) gemm_sym<C, C::LDA, C::LDB, C::KA / C::KSTEP>(AK, BK, pairs, stage, g);
+    else gemm_sym<C, C::LDAM, C::LDBM, C::KAM / C::KSTEP>(AM, BM, pairs, stage, g);
     if (C::STAGE) {
       __syncthreads();
-      copy_out<N * N, NT>(outs, g);
+      copy_out<N * N, NT>(stage, g);
       __syncthreads();
     }
   }
@@ -543,7 +569,9 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
 template <int P, int QG, bool GEN, int MODE, bool BF>
 __global__ void __launch_bounds__(256) k_sf3_f32(const ElemArgs A) {
   extern __shared__ __align__(16) float smf[];
-  sf3_f32_element<P, QG, GEN, MODE, BF>(A, blockIdx.x, smf);
+  sf3_f32_cta_setup<P, QG, GEN, MODE, BF>(smf);
+  for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x)
+    sf3_f32_element<P, QG, GEN, MODE, BF>(A, e, smf);
 }
 
 // Persistent form: every CTA pops work items (patch, first element, count)
@@ -556,6 +584,7 @@ __global__ void __launch_bounds__(256) k_sf3_f32_queue(const QueueArgs B) {
   extern __shared__ __align__(16) float smf[];
   __shared__ int s_item;
   const unsigned long long t0 = global_timer_ns();
+  sf3_f32_cta_setup<P, QG, GEN, MODE, BF>(smf);
   for (;;) {
     if (threadIdx.x == 0) {
       int it = -1;
@@ -612,9 +641,19 @@ cudaError_t run(const ElemArgs& a, cudaStream_t st) {
   } else {
     static_assert(C::smem <= 227 * 1024, "shared memory");
     auto k = k_sf3_f32<P, QG, GEN, MODE, BF>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
-    if (e != cudaSuccess) return e;
-    k<<<(unsigned)a.n_elem, C::NT, C::smem, st>>>(a);
+    static int capacity = 0;  // resident CTAs on this GPU, looked up once
+    cudaError_t e = cudaSuccess;
+    if (capacity == 0) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+      int dev = 0, sms = 0, per_sm = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem);
+      if (e != cudaSuccess) return e;
+      capacity = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int64_t grid = a.n_elem < capacity ? a.n_elem : capacity;
+    k<<<(unsigned)grid, C::NT, C::smem, st>>>(a);
     return cudaGetLastError();
   }
 }

@@ -13,7 +13,8 @@ import torch
 from . import capi
 
 _METHODS = {"classical": capi.IGA_CLASSICAL, "sumfact": capi.IGA_SUMFACT}
-_PRECISIONS = {"fp64": capi.IGA_FP64, "fp32": capi.IGA_FP32, "bf16": capi.IGA_BF16}
+_PRECISIONS = {"fp64": capi.IGA_FP64, "fp32": capi.IGA_FP32, "bf16": capi.IGA_BF16,
+               "fp64_df": capi.IGA_FP64_DF}
 
 
 @dataclass
@@ -80,7 +81,7 @@ class IgaPlan:
         self.dof_offset = [info.dof_offset[i] for i in range(npt + 1)]
         self.mat_offset = [info.mat_offset[i] for i in range(npt + 1)]
         self.dofmap_offset = [info.dofmap_offset[i] for i in range(npt + 1)]
-        self.out_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.out_dtype = torch.float64 if precision in ("fp64", "fp64_df") else torch.float32
 
     # -- sizes ---------------------------------------------------------------
     @property
