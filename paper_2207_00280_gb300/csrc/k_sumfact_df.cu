@@ -8,11 +8,10 @@
 //   product a*b: p = a.hi*b.hi, its rounding error fma(a.hi, b.hi, -p) is
 //   exact, plus the cross terms a.hi*b.lo + a.lo*b.hi (Dekker/Kahan with FMA);
 //   sum: Knuth's two-sum of the high parts plus the low parts, renormalised.
-// GB300 issues FP32 FMAs 64 times faster than FP64 ones, so this trades ~14
+// GB300 issues FP32 FMAs 64 times faster than FP64 ones, so this trades 12
 // FP32 operations for one FP64 multiply-add.  The Jacobian cofactors and
-// determinant, the weights times kappa and the inputs' conversion use FP64;
-// the element matrices are assembled into doubles with integer operations
-// (hi + lo is exact in 53 bits up to the truncation of lo's lowest bits).
+// determinant, the weights times kappa and the conversions of the inputs and
+// of the outputs (exact) use the otherwise idle FP64 pipe.
 #include <cstdint>
 
 #include "iga_internal.h"
@@ -38,44 +37,33 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return {s, e - (s - p)};
 }
 
-// c + a * b
-__device__ __forceinline__ df df_fma(df a, df b, df c) {
+// hi + lo as a double.  Both halves convert exactly and their sum has at most
+// 48 significant bits, so the double addition is exact: three FP64-pipe
+// instructions per warp of entries, on a pipe this kernel otherwise leaves idle.
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// Dot-product accumulator: the running sum s of the high products (kept exact
+// by two-sum) and the running sum e of all low-order terms; one
+// renormalisation at the end (12 FP32 operations per multiply-add).
+struct dacc {
+  float s, e;
+};
+
+__device__ __forceinline__ void acc_fma(dacc& A, df a, df b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
-  const float s = p + c.hi;
-  const float bb = s - p;
-  const float err = (p - (s - bb)) + (c.hi - bb);
-  const float t = err + e + c.lo;
-  const float hi = s + t;
-  return {hi, t - (hi - s)};
+  const float s = A.s + p;
+  const float bb = s - A.s;
+  const float err = (A.s - (s - bb)) + (p - bb);
+  A.s = s;
+  A.e += err + e;
 }
 
-// hi + lo as a double, built from the bit patterns with integer operations.
-// For a normal hi, |lo| <= ulp(hi)/2, so the sum needs at most 53 + 5 bits;
-// the bits of lo below the double's last place are truncated (< 2^-52 relative).
-__device__ __forceinline__ double df_to_double(df a) {
-  const uint32_t H = __float_as_uint(a.hi), L = __float_as_uint(a.lo);
-  const int eh = (int)((H >> 23) & 0xffu);
-  if (eh == 0 || eh == 255) return (double)a.hi + (double)a.lo;  // zero, subnormal, inf/nan
-  uint64_t m = (uint64_t)((H & 0x7fffffu) | 0x800000u) << 29;     // leading bit at 52
-  int e = eh;
-  const int el = (int)((L >> 23) & 0xffu);
-  if (el != 0) {
-    const uint64_t ml = (uint64_t)((L & 0x7fffffu) | 0x800000u);
-    const int sh = eh - el;
-    uint64_t add = 0;
-    if (sh <= 29) add = ml << (29 - sh);
-    else if (sh - 29 < 64) add = ml >> (sh - 29);
-    if ((H ^ L) >> 31) m -= add;
-    else m += add;
-    if (m >= (1ull << 53)) { m >>= 1; ++e; }
-    else if (m < (1ull << 52)) { m <<= 1; --e; }
-  }
-  const uint64_t bits = ((uint64_t)(H >> 31) << 63) | ((uint64_t)(e + 896) << 52) |
-                        (m & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
+__device__ __forceinline__ df acc_value(dacc A) {
+  const float hi = A.s + A.e;
+  return {hi, A.e - (hi - A.s)};
 }
 
 template <int P, int QG, bool GEN>
@@ -151,11 +139,9 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
   // coefficients: weights times kappa (and the geometry) in FP64, then split
   for (int k = tid; k < Q; k += NT) {
     const int k1 = k % q, k2 = (k / q) % q, k3 = k / (q * q);
-    const double* w = A.tab[0];  // weights are read from the double records
     const double W = A.tab[0][(int64_t)e1 * REC + 2 * q * n + k1] *
                      A.tab[1][(int64_t)e2 * REC + 2 * q * n + k2] *
                      A.tab[2][(int64_t)e3 * REC + 2 * q * n + k3];
-    (void)w;
     const double kap = A.kappa ? A.kappa[e * Q + k] : 1.0;
     const double rh = A.rho ? A.rho[e * Q + k] : 1.0;
     if (GEN) {
@@ -188,8 +174,7 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
   const df* Pz = pat + 2 * 3 * n2 * q;
   const df* Py = pat + 1 * 3 * n2 * q;
   const df* Px = pat;
-  const df zero = {0.f, 0.f};
-
+  
   for (int c0 = 0; c0 < q; c0 += QC) {
     constexpr int nsym_items = C::NSYM * NS1 * QC * q;
     constexpr int n_items1 = nsym_items + C::NFULL * n2 * QC * q;
@@ -215,11 +200,12 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
       else { zp = t == 2 ? 1 : 0; ci = t == 1 ? 1 : 0; }
       const df* D = coef + ci * Q + (c0 + q1c) + q * q2;
       const df* Z = zp < 2 ? Pz + zp * n2 * q + (a3 * n + b3) * q : Pz + 2 * n2 * q + (b3 * n + a3) * q;
-      df acc = zero;
+      dacc acc = {0.f, 0.f};
 #pragma unroll
-      for (int k3 = 0; k3 < q; ++k3) acc = df_fma(Z[k3], D[q * q * k3], acc);
-      T1[((t * n2 + a3 * n + b3) * QC + q1c) * q + q2] = acc;
-      if (t < C::NSYM && a3 != b3) T1[((t * n2 + b3 * n + a3) * QC + q1c) * q + q2] = acc;
+      for (int k3 = 0; k3 < q; ++k3) acc_fma(acc, Z[k3], D[q * q * k3]);
+      const df v = acc_value(acc);
+      T1[((t * n2 + a3 * n + b3) * QC + q1c) * q + q2] = v;
+      if (t < C::NSYM && a3 != b3) T1[((t * n2 + b3 * n + a3) * QC + q1c) * q + q2] = v;
     }
     __syncthreads();
     constexpr int n_sym2 = 3 * NSp * QC;
@@ -237,18 +223,18 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
         auto t1 = [&](int t, int x3, int y3) -> const df* {
           return T1 + ((t * n2 + x3 * n + y3) * QC + q1c) * q;
         };
-        df acc = zero;
+        dacc acc = {0.f, 0.f};
         if (X == 0) {
           const df* T = t1(C::T_00, a3, b3);
 #pragma unroll
-          for (int k2 = 0; k2 < q; ++k2) acc = df_fma(y00[k2], T[k2], acc);
+          for (int k2 = 0; k2 < q; ++k2) acc_fma(acc, y00[k2], T[k2]);
         } else if (X == 1) {
           const df* Ta = t1(C::T_11, a3, b3);
           const df* Tb = t1(C::T_22, a3, b3);
 #pragma unroll
           for (int k2 = 0; k2 < q; ++k2) {
-            acc = df_fma(y11[k2], Ta[k2], acc);
-            acc = df_fma(y00[k2], Tb[k2], acc);
+            acc_fma(acc, y11[k2], Ta[k2]);
+            acc_fma(acc, y00[k2], Tb[k2]);
           }
           if (GEN) {
             const df* y10 = Py + 2 * n2 * q + (a2 * n + b2) * q;
@@ -257,16 +243,16 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
             const df* Td = t1(C::T_12, b3, a3);
 #pragma unroll
             for (int k2 = 0; k2 < q; ++k2) {
-              acc = df_fma(y10[k2], Tc[k2], acc);
-              acc = df_fma(y01[k2], Td[k2], acc);
+              acc_fma(acc, y10[k2], Tc[k2]);
+              acc_fma(acc, y01[k2], Td[k2]);
             }
           }
         } else {
           const df* T = t1(C::T_M, a3, b3);
 #pragma unroll
-          for (int k2 = 0; k2 < q; ++k2) acc = df_fma(y00[k2], T[k2], acc);
+          for (int k2 = 0; k2 < q; ++k2) acc_fma(acc, y00[k2], T[k2]);
         }
-        Cs[(X * NSp + pp) * q + c0 + q1c] = acc;
+        Cs[(X * NSp + pp) * q + c0 + q1c] = acc_value(acc);
       } else if (GEN) {
         const int r = it - n_sym2;
         const int ab = r / QC, q1c = r % QC;
@@ -276,13 +262,13 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
         const df* y01 = Py + 2 * n2 * q + (b2 * n + a2) * q;
         const df* Ta = T1 + ((C::T_01 * n2 + a3 * n + b3) * QC + q1c) * q;
         const df* Tb = T1 + ((C::T_02 * n2 + a3 * n + b3) * QC + q1c) * q;
-        df acc = zero;
+        dacc acc = {0.f, 0.f};
 #pragma unroll
         for (int k2 = 0; k2 < q; ++k2) {
-          acc = df_fma(y01[k2], Ta[k2], acc);
-          acc = df_fma(y00[k2], Tb[k2], acc);
+          acc_fma(acc, y01[k2], Ta[k2]);
+          acc_fma(acc, y00[k2], Tb[k2]);
         }
-        C10[(ap * Np + bp) * q + c0 + q1c] = acc;
+        C10[(ap * Np + bp) * q + c0 + q1c] = acc_value(acc);
       }
     }
     __syncthreads();
@@ -315,31 +301,31 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
       if (Ke) {
         const df* p11 = x11 + (a1 * n + b1) * q;
         const df* p00 = x00 + (a1 * n + b1) * q;
-        df acc = zero;
+        dacc acc = {0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < q; ++k) {
-          acc = df_fma(p11[k], c11[k], acc);
-          acc = df_fma(p00[k], c00[k], acc);
+          acc_fma(acc, p11[k], c11[k]);
+          acc_fma(acc, p00[k], c00[k]);
         }
         if (GEN) {
           const df* p10 = x10 + (a1 * n + b1) * q;
           const df* p01 = x10 + (b1 * n + a1) * q;
 #pragma unroll
           for (int k = 0; k < q; ++k) {
-            acc = df_fma(p10[k], c10[k], acc);
-            acc = df_fma(p01[k], c01[k], acc);
+            acc_fma(acc, p10[k], c10[k]);
+            acc_fma(acc, p01[k], c01[k]);
           }
         }
-        const double v = df_to_double(acc);
+        const double v = df_to_double(acc_value(acc));
         Ke[rowa + b1 + n * bp] = v;
         Ke[rowb + a1 + n * ap] = v;
       }
       if (Me) {
         const df* p00 = x00 + (a1 * n + b1) * q;
-        df acc = zero;
+        dacc acc = {0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < q; ++k) acc = df_fma(p00[k], cM[k], acc);
-        const double v = df_to_double(acc);
+        for (int k = 0; k < q; ++k) acc_fma(acc, p00[k], cM[k]);
+        const double v = df_to_double(acc_value(acc));
         Me[rowa + b1 + n * bp] = v;
         Me[rowb + a1 + n * ap] = v;
       }
