@@ -45,11 +45,17 @@ class _Patch(ctypes.Structure):
 
 
 def lib():
+    """Load the oracle.  IGA_ORACLE_SO may name another build of iga_oracle.c
+    (the mutation tests use it to check that the pins reject planted bugs)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_SO)
+            alt = os.environ.get("IGA_ORACLE_SO")
+            if alt:
+                L = ctypes.CDLL(alt)
+            else:
+                build()
+                L = ctypes.CDLL(_SO)
             dp = ctypes.c_void_p
             L.ora_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
             L.ora_gauss_legendre.restype = ctypes.c_int

@@ -1,0 +1,55 @@
+"""The oracle's pins reject plausible mistakes.  Each case plants one bug in a
+copy of oracle/iga_oracle.c (on the CPU), builds it, and runs the pin tests
+against it in a subprocess: they must fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "iga_oracle.c")
+
+MUTANTS = {
+    # transposed inverse Jacobian in the physical gradient
+    "transposed_Ginv": ("s2 += Gi[j * d + i] * gr[j];", "s2 += Gi[i * d + j] * gr[j];"),
+    # off-diagonal stiffness terms dropped in sum factorization
+    "dropped_cross_terms": ("for (int be = 0; be < d; ++be) {", "for (int be = al; be <= al; ++be) {"),
+    # sign error in the second Cox--de Boor term
+    "coxdeboor_sign": ("right = (t[i + p + 1] - xi) / d2", "right = (xi - t[i + p + 1]) / d2"),
+    # wrong index in the recursion
+    "coxdeboor_index": ("right = (t[i + p + 1] - xi) / d2 * ora_bspline(t, i + 1, p - 1, xi);",
+                        "right = (t[i + p + 1] - xi) / d2 * ora_bspline(t, i, p - 1, xi);"),
+    # derivative identity with the wrong sign
+    "derivative_sign": ("  return a - b;\n}", "  return a + b;\n}"),
+    # Gauss weights missing the factor 2 of the Golub--Welsch formula
+    "gauss_weight": ("w[i] = 2.0 * V[0 * q + i] * V[0 * q + i];", "w[i] = V[0 * q + i] * V[0 * q + i];"),
+    # span half-length missing from the mapped weights
+    "weight_map": ("w[j] = half * wr[j];", "w[j] = wr[j];"),
+    # dof stride by elements instead of functions
+    "dof_stride": ("stride *= nf[k];", "stride *= L.K[k];"),
+    # adjoint product of u with itself
+    "adjoint_product": ("dot += pu * pv;", "dot += pu * pu;"),
+    # y-direction weight dropped in stage 2 of Algorithm 2
+    "sf_stage2_weight": ("Dbuf[((i3 * n + j3) * q + k1) * q + k2] * B->w[1][k2];",
+                         "Dbuf[((i3 * n + j3) * q + k1) * q + k2];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site not found: {old}"
+    mutated = src.replace(old, new, 1)
+    cfile = tmp_path / "iga_oracle.c"
+    cfile.write_text(mutated)
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared",
+                    "-I", os.path.join(ROOT, "oracle"), "-o", str(so), str(cfile), "-lm"], check=True)
+    env = dict(os.environ, IGA_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
+    assert " failed" in r.stdout, f"mutant {name} did not fail a pin cleanly:\n{r.stdout[-2000:]}"
