@@ -93,6 +93,16 @@ __device__ __forceinline__ void mma_tf32_1688(float* c, const uint32_t* a, const
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Asynchronous 8-byte global -> shared copy (cp.async); all of a thread's
+// copies are in flight together and complete at cp_async_wait_all().
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -191,26 +201,34 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
       rm[h] = n * (bp * N + ap);
       off[h] = ap != bp;
     }
+    float c[NTN][4];
+#pragma unroll
+    for (int nt = 0; nt < NTN; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+    // the N tiles' accumulation chains are independent: interleave them
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      if (BF) {
+#pragma unroll
+        for (int nt = 0; nt < NTN; ++nt) mma_bf16_16816(c[nt], ah[ks], bh[nt][ks]);
+#pragma unroll
+        for (int nt = 0; nt < NTN; ++nt) mma_bf16_16816(c[nt], ah[ks], bl[nt][ks]);
+      } else {
+#pragma unroll
+        for (int nt = 0; nt < NTN; ++nt) mma_tf32_1688(c[nt], ah[ks], bh[nt][ks]);
+#pragma unroll
+        for (int nt = 0; nt < NTN; ++nt) mma_tf32_1688(c[nt], ah[ks], bl[nt][ks]);
+#pragma unroll
+        for (int nt = 0; nt < NTN; ++nt) mma_tf32_1688(c[nt], al[ks], bh[nt][ks]);
+      }
+    }
 #pragma unroll
     for (int nt = 0; nt < NTN; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int ks = 0; ks < KS; ++ks) {
-        if (BF) {
-          mma_bf16_16816(c, ah[ks], bh[nt][ks]);
-          mma_bf16_16816(c, ah[ks], bl[nt][ks]);
-        } else {
-          mma_tf32_1688(c, ah[ks], bh[nt][ks]);
-          mma_tf32_1688(c, ah[ks], bl[nt][ks]);
-          mma_tf32_1688(c, al[ks], bh[nt][ks]);
-        }
-      }
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         const int r = h >> 1, cc = h & 1;
         if (rv[r] && cd[nt][cc] >= 0) {
-          dst[rd[r] + cd[nt][cc]] = c[h];
-          if (off[r]) dst[rm[r] + cm[nt][cc]] = c[h];
+          dst[rd[r] + cd[nt][cc]] = c[nt][h];
+          if (off[r]) dst[rm[r] + cm[nt][cc]] = c[nt][h];
         }
       }
     }
@@ -292,20 +310,24 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   __syncthreads();  // shared memory of the previous element is no longer read
 
   // ---- coalesced staging of this element's inputs; zero the GEMM operands -------
+  // every copy of this thread is issued before any completes (cp.async)
   for (int i = tid; i < 3 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
     const double* tb = d == 0 ? A.tab[0] : (d == 1 ? A.tab[1] : A.tab[2]);
-    rec[i] = tb[(int64_t)ek * REC + j];
+    cp_async8(rec + i, tb + (int64_t)ek * REC + j);
   }
   for (int k = tid; k < Q; k += NT) {
-    kap[k] = A.kappa ? A.kappa[e * Q + k] : 1.0;
-    rho[k] = A.rho ? A.rho[e * Q + k] : 1.0;
+    if (A.kappa) cp_async8(kap + k, A.kappa + e * Q + k);
+    else kap[k] = 1.0;
+    if (A.rho) cp_async8(rho + k, A.rho + e * Q + k);
+    else rho[k] = 1.0;
   }
   if (GEN) {
     const double* G = A.jac + e * Q * 9;
-    for (int i = tid; i < 9 * Q; i += NT) jac[i] = G[i];
+    for (int i = tid; i < 9 * Q; i += NT) cp_async8(jac + i, G + i);
   }
+  cp_async_wait_all();
   __syncthreads();
   for (int i = tid; i < 3 * REC; i += NT) recf[i] = (float)rec[i];
   __syncthreads();
@@ -422,8 +444,10 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
       }
     }
     const int b3e = (part + 1) * CH < n ? (part + 1) * CH : n;
-#pragma unroll 1
-    for (int b3 = part * CH; b3 < b3e; ++b3) {
+#pragma unroll
+    for (int bo = 0; bo < CH; ++bo) {
+      const int b3 = part * CH + bo;
+      if (b3 >= b3e) break;
       const float* z = Pz + (a3 * n + b3) * 3 * q;
       float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f, t6 = 0.f;
 #pragma unroll
@@ -477,9 +501,11 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
       }
       const int ap = a2 + n * a3;
       const int b2s = (a3 == b3 ? a2 : 0);
-      int pp = upper_index<Np>(ap, b2s + n * b3);  // consecutive b2 -> consecutive rows
-#pragma unroll 1
-      for (int b2 = b2s; b2 < n; ++b2, ++pp) {
+      const int pp0 = upper_index<Np>(ap, b2s + n * b3) - b2s;  // rows are consecutive in b2
+#pragma unroll
+      for (int b2 = 0; b2 < n; ++b2) {
+        if (b2 < b2s) continue;
+        const int pp = pp0 + b2;
         const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);  // 00, 11, 10, 01
         float y[RW];
 #pragma unroll
@@ -522,7 +548,7 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
           t02[k2] = T1[5 * S + o + q * k2];
         }
         const int ap = a2 + n * a3;
-#pragma unroll 1
+#pragma unroll
         for (int b2 = 0; b2 < n; ++b2) {
           const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);
           float y[RW];
