@@ -446,6 +446,17 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
                 v["speedup_vs_classical_fp64"] = round(base / v["ms_per_step"], 3)
     if not args.extra_forms:
         return forms
+    # 2D p=2 16x16 (256 elements, kappa = 1): launch-latency bound, reported in microseconds
+    W2 = wl.WORKLOADS["2d_p2_16"]
+    s2 = W2.spec
+    small = {"elements": s2.E}
+    for meth in ("sumfact", "classical"):
+        pl = IgaPlan(Patch(s2.knots, s2.p, s2.q), method=meth, precision="fp64", blocking=False)
+        K2, M2, D2 = pl.empty_outputs(device=dev)
+        ms = _time_steps(lambda: pl.integrate(K=K2, M=M2, dof=D2, stream=stream), 20, stream, flush)
+        small[f"{meth}_fp64_us_per_step"] = round(ms * 1e3, 2)
+        pl.close()
+    forms["2d_p2_16"] = small
     # 64-patch mixed batch, FP32 mass + stiffness: one persistent graph vs per-patch launches
     specs = wl.batch_specs()
     nqp = sum(s.E * s.Q for s in specs)

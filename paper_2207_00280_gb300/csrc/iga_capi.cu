@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "iga_batch.h"
 #include "iga_internal.h"
 
@@ -47,6 +49,13 @@ struct iga_plan_s {
 namespace {
 
 bool g_log = false;
+
+// NVTX range around a public call (visible in Nsight timelines; a no-op
+// without a profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 void log_msg(const char* msg) {
   if (g_log) fprintf(stderr, "[iga] %s\n", msg);
@@ -359,6 +368,7 @@ static int finish(iga_plan_s* P, cudaStream_t st, cudaError_t launch_err) {
 extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rho,
                              const double* jac, void* K_out, void* M_out, int32_t* dof_out,
                              void* cuda_stream) {
+  NvtxRange range("iga_integrate");
   if (!P) return IGA_ERR_ARG;
   if (P->sticky != IGA_OK) return P->sticky;
   const bool want_K = (P->opts.matrices & IGA_STIFF) && K_out;
@@ -453,6 +463,7 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
 extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const double* jac,
                                       const void* u, const void* v, void* grad_kappa,
                                       double* J_out, void* cuda_stream) {
+  NvtxRange range("iga_integrate_backward");
   if (!P) return IGA_ERR_ARG;
   if (P->sticky != IGA_OK) return P->sticky;
   if (!u || !v || (!grad_kappa && !J_out) || (J_out && !kappa)) return IGA_ERR_ARG;
