@@ -76,6 +76,12 @@ def lib():
             L.ora_dofmap.restype = ctypes.c_int
             L.ora_adjoint.argtypes = [pp, dp, ctypes.c_int64, dp, dp, dp, dp, dp, dp]
             L.ora_adjoint.restype = ctypes.c_int
+            L.ora_csr_pattern.argtypes = [pp, dp, dp]
+            L.ora_csr_pattern.restype = ctypes.c_int
+            L.ora_assemble.argtypes = [pp, dp, dp, dp, dp]
+            L.ora_assemble.restype = ctypes.c_int
+            L.ora_apply.argtypes = [pp, dp, dp, dp, dp, dp, dp]
+            L.ora_apply.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -204,3 +210,43 @@ class Patch:
         if rc != 0:
             raise ValueError("oracle rejected its arguments")
         return g, float(J[0])
+
+    def csr_pattern(self):
+        """(row_ptr[n_dofs + 1] int64, col_idx[nnz] int32) of the assembled global matrix."""
+        row_ptr = np.zeros(self.n_dofs + 1, dtype=np.int64)
+        if lib().ora_csr_pattern(ctypes.byref(self._s), _ptr(row_ptr), None) != 0:
+            raise ValueError("oracle rejected its arguments")
+        col_idx = np.zeros(int(row_ptr[-1]), dtype=np.int32)
+        if lib().ora_csr_pattern(ctypes.byref(self._s), _ptr(row_ptr), _ptr(col_idx)) != 0:
+            raise ValueError("oracle rejected its arguments")
+        return row_ptr, col_idx
+
+    def assemble(self, Ae, row_ptr, col_idx):
+        """CSR values of sum_e P_e^T Ae[e] P_e for element matrices Ae[E][N][N]."""
+        Ae = _f64(Ae)
+        if Ae.size != self.E * self.N * self.N:
+            raise ValueError("Ae must hold every element's matrix")
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        vals = np.zeros(len(col_idx))
+        rc = lib().ora_assemble(ctypes.byref(self._s), _ptr(row_ptr), _ptr(col_idx), _ptr(Ae),
+                                _ptr(vals))
+        if rc != 0:
+            raise ValueError(f"oracle assembly failed ({rc})")
+        return vals
+
+    def apply(self, x, kappa=None, rho=None, G=None, stiffness=True, mass=True):
+        """(K x, M x) of the assembled operators (either may be None if not asked for)."""
+        x = _f64(x)
+        if x.size != self.n_dofs:
+            raise ValueError("x must have one value per global dof")
+        kappa = self._check_qp(kappa, 1)
+        rho = self._check_qp(rho, 1)
+        G = self._check_qp(G, self.dim * self.dim)
+        yK = np.zeros(self.n_dofs) if stiffness else None
+        yM = np.zeros(self.n_dofs) if mass else None
+        rc = lib().ora_apply(ctypes.byref(self._s), _ptr(kappa), _ptr(rho), _ptr(G), _ptr(x),
+                             _ptr(yK), _ptr(yM))
+        if rc != 0:
+            raise ValueError("oracle rejected its arguments")
+        return yK, yM

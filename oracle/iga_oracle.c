@@ -559,3 +559,131 @@ int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
   free_layout(&L);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Global assembly: the global matrix is the sum of the element matrices     */
+/* placed at their support index sets (Sec. 3.1, eq. 10 and the Remark on    */
+/* K^Delta_alpha; the insertion step of Table 3).                            */
+/* ------------------------------------------------------------------------ */
+static int64_t n_global_dofs(const ora_patch* pt, const layout* L) {
+  int64_t nd = 1;
+  for (int k = 0; k < L->d; ++k) nd *= pt->m[k] - pt->p - 1;
+  return nd;
+}
+
+static int cmp_i32(const void* x, const void* y) {
+  int32_t a = *(const int32_t*)x, b = *(const int32_t*)y;
+  return (a > b) - (a < b);
+}
+
+int ora_csr_pattern(const ora_patch* pt, int64_t* row_ptr, int32_t* col_idx) {
+  layout L;
+  if (!row_ptr || make_layout(pt, &L)) { free_layout(&L); return -1; }
+  const int64_t E = n_elements(&L), nd = n_global_dofs(pt, &L);
+  const int N = L.N;
+  /* the elements that hold each dof: counts, prefix sums, lists */
+  int64_t* first = (int64_t*)calloc((size_t)nd + 1, sizeof(int64_t));
+  int64_t* fill = (int64_t*)calloc((size_t)nd, sizeof(int64_t));
+  int64_t* owner = (int64_t*)malloc(sizeof(int64_t) * (size_t)(E * N > 0 ? E * N : 1));
+  int32_t* dof = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
+  int32_t* row = NULL;
+  int64_t row_cap = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    ora_dofmap(pt, &e, 1, dof);
+    for (int a = 0; a < N; ++a) first[dof[a] + 1]++;
+  }
+  for (int64_t i = 0; i < nd; ++i) first[i + 1] += first[i];
+  for (int64_t e = 0; e < E; ++e) {
+    ora_dofmap(pt, &e, 1, dof);
+    for (int a = 0; a < N; ++a) owner[first[dof[a]] + fill[dof[a]]++] = e;
+  }
+  for (int64_t i = 0; i < nd; ++i) mark[i] = -1;
+  row_ptr[0] = 0;
+  for (int64_t i = 0; i < nd; ++i) {
+    int64_t cnt = 0;
+    const int64_t need = (first[i + 1] - first[i]) * N;
+    if (need > row_cap) {
+      row_cap = need;
+      row = (int32_t*)realloc(row, sizeof(int32_t) * (size_t)row_cap);
+    }
+    for (int64_t o = first[i]; o < first[i + 1]; ++o) {
+      ora_dofmap(pt, &owner[o], 1, dof);
+      for (int b = 0; b < N; ++b)
+        if (mark[dof[b]] != i) { mark[dof[b]] = i; row[cnt++] = dof[b]; }
+    }
+    qsort(row, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    if (col_idx) memcpy(col_idx + row_ptr[i], row, sizeof(int32_t) * (size_t)cnt);
+    row_ptr[i + 1] = row_ptr[i] + cnt;
+  }
+  free(first); free(fill); free(owner); free(dof); free(mark); free(row);
+  free_layout(&L);
+  return 0;
+}
+
+int ora_assemble(const ora_patch* pt, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* Ae, double* values) {
+  layout L;
+  if (!row_ptr || !col_idx || !Ae || !values || make_layout(pt, &L)) { free_layout(&L); return -1; }
+  const int64_t E = n_elements(&L), nd = n_global_dofs(pt, &L);
+  const int N = L.N;
+  int32_t* dof = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  int rc = 0;
+  for (int64_t z = 0; z < row_ptr[nd]; ++z) values[z] = 0.0;
+  for (int64_t e = 0; e < E && rc == 0; ++e) {
+    ora_dofmap(pt, &e, 1, dof);
+    for (int a = 0; a < N && rc == 0; ++a) {
+      const int64_t lo = row_ptr[dof[a]], hi = row_ptr[dof[a] + 1];
+      for (int b = 0; b < N; ++b) {
+        /* binary search of column dof[b] in row dof[a] */
+        int64_t l = lo, h = hi;
+        while (l < h) {
+          int64_t mid = l + (h - l) / 2;
+          if (col_idx[mid] < dof[b]) l = mid + 1; else h = mid;
+        }
+        if (l >= hi || col_idx[l] != dof[b]) { rc = -2; break; }
+        values[l] += Ae[((size_t)e * N + a) * N + b];
+      }
+    }
+  }
+  free(dof);
+  free_layout(&L);
+  return rc;
+}
+
+int ora_apply(const ora_patch* pt, const double* kappa, const double* rho, const double* G,
+              const double* x, double* yK, double* yM) {
+  layout L;
+  if (!x || (!yK && !yM) || make_layout(pt, &L)) { free_layout(&L); return -1; }
+  const int64_t E = n_elements(&L), nd = n_global_dofs(pt, &L);
+  const int N = L.N, Q = L.Q;
+  double* ones = NULL;
+  if (yK && !kappa) {
+    ones = (double*)malloc(sizeof(double) * (size_t)(E * Q));
+    for (int64_t i = 0; i < E * Q; ++i) ones[i] = 1.0;
+    kappa = ones;
+  }
+  double* Ke = yK ? (double*)malloc(sizeof(double) * (size_t)N * N) : NULL;
+  double* Me = yM ? (double*)malloc(sizeof(double) * (size_t)N * N) : NULL;
+  int32_t* dof = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  for (int64_t i = 0; i < nd; ++i) {
+    if (yK) yK[i] = 0.0;
+    if (yM) yM[i] = 0.0;
+  }
+  for (int64_t e = 0; e < E; ++e) {
+    ora_classical(pt, &e, 1, kappa, rho, G, Ke, Me);
+    ora_dofmap(pt, &e, 1, dof);
+    for (int a = 0; a < N; ++a) {
+      double sK = 0.0, sM = 0.0;
+      for (int b = 0; b < N; ++b) {
+        if (Ke) sK += Ke[(size_t)a * N + b] * x[dof[b]];
+        if (Me) sM += Me[(size_t)a * N + b] * x[dof[b]];
+      }
+      if (yK) yK[dof[a]] += sK;
+      if (yM) yM[dof[a]] += sM;
+    }
+  }
+  free(ones); free(Ke); free(Me); free(dof);
+  free_layout(&L);
+  return 0;
+}

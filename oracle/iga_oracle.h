@@ -94,6 +94,33 @@ int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
                 const double* kappa, const double* G, const double* u,
                 const double* v, double* g, double* J);
 
+/* Sparsity pattern of the assembled global matrix.  The global matrix sums
+ * the element matrices over the support index sets of the elements (Sec. 3.1,
+ * eq. 10 and the Remark on K^Delta_alpha; the insertion step of Table 3,
+ * Sec. 3.3), so entry (i, j) is present iff at least one element holds both
+ * functions i and j.  Rows in global dof order, columns ascending.
+ * row_ptr[n_dofs + 1] is always written; col_idx[row_ptr[n_dofs]] only if
+ * non-NULL.  Returns 0, or -1 on bad arguments. */
+int ora_csr_pattern(const ora_patch* pt, int64_t* row_ptr, int32_t* col_idx);
+
+/* Global assembly of element matrices Ae[E][N][N] (every element of the
+ * patch, in element order) into CSR values on the pattern of
+ * ora_csr_pattern: values[z] of entry (i, j) is the sum over elements e, in
+ * ascending e, of Ae[e][a][b] with dof(e,a) = i and dof(e,b) = j.  Returns 0,
+ * -1 on bad arguments, -2 if an entry is missing from the pattern. */
+int ora_assemble(const ora_patch* pt, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* Ae, double* values);
+
+/* Application of the assembled operators to a global vector x[n_dofs] (not in
+ * the paper as such: the products K u and M u of the forward-Euler step of
+ * Sec. 2.2, eq. Euler):
+ *   yK = sum_e P_e^T K_e P_e x,   yM = sum_e P_e^T M_e P_e x,
+ * with K_e, M_e the element matrices of ora_classical and P_e the gather
+ * through the dof map; elements in ascending order.  kappa may be NULL (= 1)
+ * only for the mass; yK or yM may be NULL (skip).  Returns 0, or -1. */
+int ora_apply(const ora_patch* pt, const double* kappa, const double* rho, const double* G,
+              const double* x, double* yK, double* yM);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,12 +33,22 @@ MUTANTS = {
     # y-direction weight dropped in stage 2 of Algorithm 2
     "sf_stage2_weight": ("Dbuf[((i3 * n + j3) * q + k1) * q + k2] * B->w[1][k2];",
                          "Dbuf[((i3 * n + j3) * q + k1) * q + k2];"),
+    # global assembly: element matrix inserted transposed
+    "assemble_transposed": ("values[l] += Ae[((size_t)e * N + a) * N + b];",
+                            "values[l] += Ae[((size_t)e * N + b) * N + a];", "test_oracle_assembly.py"),
+    # operator application gathers the test function's dof instead of the trial's
+    "apply_gather": ("if (Ke) sK += Ke[(size_t)a * N + b] * x[dof[b]];",
+                     "if (Ke) sK += Ke[(size_t)a * N + b] * x[dof[a]];", "test_oracle_assembly.py"),
+    # sparsity pattern misses the first function of every element
+    "pattern_drop": ("for (int b = 0; b < N; ++b)\n        if (mark[dof[b]] != i)",
+                     "for (int b = 1; b < N; ++b)\n        if (mark[dof[b]] != i)", "test_oracle_assembly.py"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_reject_mutant(tmp_path, name):
-    old, new = MUTANTS[name]
+    old, new = MUTANTS[name][:2]
+    pins = MUTANTS[name][2] if len(MUTANTS[name]) > 2 else "test_oracle_pins.py"
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation site not found: {old}"
     mutated = src.replace(old, new, 1)
@@ -49,7 +59,7 @@ def test_pins_reject_mutant(tmp_path, name):
                     "-I", os.path.join(ROOT, "oracle"), "-o", str(so), str(cfile), "-lm"], check=True)
     env = dict(os.environ, IGA_ORACLE_SO=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
     assert " failed" in r.stdout, f"mutant {name} did not fail a pin cleanly:\n{r.stdout[-2000:]}"
