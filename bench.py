@@ -494,7 +494,75 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
         adj[pr] = {"ms_per_step": round(ms, 4), "qp_per_s": round(sa.E * sa.Q / (ms * 1e-3), 1)}
         pl.close()
     forms["adjoint_3d_p3_40"] = adj
+    forms["apply_3d_p3_40"] = measure_apply(A, ka, stream, flush, dev)
+    forms["assembly_3d_p3_32"] = measure_assembly(W, kappa, stream, flush, dev)
     return forms
+
+
+def apply_flops_per_element(p, q):
+    """Algorithmic flops of the matrix-free operator per element (3D, identity
+    geometry, multiply-add = 2): interpolation a1, a2, a3 (value and gradient),
+    the flux, then the transposed contractions q3, q2, q1."""
+    n = p + 1
+    fma = 2 * n ** 3 * q + 3 * n * n * q * q + 4 * n * q ** 3   # interpolation
+    fma += 4 * q ** 3                                          # flux and mass weight
+    fma += 4 * n * q ** 3 + 3 * n * n * q * q + 2 * n ** 3 * q   # test side
+    return 2 * fma
+
+
+def measure_apply(A, kappa, stream, flush, dev):
+    """Matrix-free y = K(kappa) x + M x on the 40^3 p=3 workload, FP64 and FP32."""
+    import torch
+    from paper_2207_00280_gb300 import workloads as wl
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+    sa = A.spec
+    peaks = measured_peaks()[0]
+    f_el = apply_flops_per_element(sa.p, sa.q)
+    out = {"elements": sa.E, "dofs": sa.n_dofs, "flop_per_element": f_el}
+    for pr, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        pl = IgaPlan(Patch(sa.knots, sa.p, sa.q), method="sumfact", precision=pr, blocking=False)
+        x = torch.as_tensor(wl.normal(sa.n_dofs, wl.SEED_ADJ_U), device=dev, dtype=dt)
+        y = torch.empty_like(x)
+        ms = _time_steps(lambda: pl.apply(x, kappa=kappa, alpha=1.0, beta=1.0, y=y, stream=stream),
+                         10, stream, flush)
+        esz = 8 if pr == "fp64" else 4
+        # kappa, the per-element results written and read back, x gathered, y written
+        bytes_ = sa.E * sa.Q * 8 + 2 * sa.E * (sa.p + 1) ** 3 * esz + 2 * sa.n_dofs * esz
+        ent = {"ms_per_step": round(ms, 4), "elements_per_s": round(sa.E / (ms * 1e-3), 1),
+               "gflops": round(f_el * sa.E / (ms * 1e-3) / 1e9, 1),
+               "hbm_frac": round(bytes_ / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+        if pr == "fp64":
+            peak = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            ent["fp64_frac"] = round(f_el * sa.E / (ms * 1e-3) / peak, 4)
+        out[pr] = ent
+        pl.close()
+    return out
+
+
+def measure_assembly(W, kappa, stream, flush, dev):
+    """Global CSR assembly of the 32^3 p=3 element matrices (FP64 K and M, and
+    FP32 K): HBM-bound gather, bytes = element matrices read + values written."""
+    import torch
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+    sp = W.spec
+    peaks = measured_peaks()[0]
+    out = {"elements": sp.E, "dofs": sp.n_dofs}
+    for pr in ("fp64", "fp32"):
+        pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="sumfact", precision=pr, blocking=False)
+        K, M, _ = pl.empty_outputs(device=dev, dof=False)
+        pl.integrate(kappa=kappa, K=K, M=M, stream=stream)
+        vals = torch.empty(pl.n_csr_nnz, dtype=pl.out_dtype, device=dev)
+        ms = _time_steps(lambda: pl.assemble(K, values=vals, stream=stream), 10, stream, flush)
+        esz = 8 if pr == "fp64" else 4
+        bytes_ = (K.numel() + pl.n_csr_nnz) * esz
+        out[pr] = {"nnz": pl.n_csr_nnz, "ms_per_matrix": round(ms, 4),
+                   "achieved_gbs": round(bytes_ / (ms * 1e-3) / 1e9, 1),
+                   "hbm_frac": round(bytes_ / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                   "bytes_per_launch": bytes_}
+        del K, M, vals
+        pl.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def traffic_from_profiles(args, esize):

@@ -129,6 +129,7 @@ typedef struct {
   const int64_t* dof_offset;
   const int64_t* mat_offset;
   const int64_t* dofmap_offset;
+  int64_t n_csr_nnz;        /* entries of the assembled (CSR) global matrix */
 } iga_plan_info;
 
 /* Validate the patches, build the element spans, Gauss rules and dof strides
@@ -172,6 +173,46 @@ int iga_integrate_backward(iga_plan_t plan, const double* kappa, const double* j
  * weights times half the element length.  iga_integrate computes the same
  * tables internally; this entry exposes them for inspection. */
 int iga_basis_tables(iga_plan_t plan, double* out, void* cuda_stream);
+
+/* Sparsity pattern of the assembled global matrix (Sec. 3.1: the global
+ * matrix sums the element matrices over the support index sets of the
+ * elements, eq. 10 and the Remark on K^Delta_alpha; the insertion step of
+ * Table 3, Sec. 3.3).  Entry (i, j) is present iff some element holds both
+ * global functions i and j; patches are independent diagonal blocks.
+ *   row_ptr: device, [n_dofs + 1] int64, row_ptr[n_dofs] = info.n_csr_nnz;
+ *   col_idx: device, [n_csr_nnz] int32, ascending within each row.
+ * Both are written on `cuda_stream` (caller-owned buffers; the pattern
+ * depends on the plan only, so it needs computing once). */
+int iga_csr_pattern(iga_plan_t plan, int64_t* row_ptr, int32_t* col_idx, void* cuda_stream);
+
+/* Global assembly of element matrices into the values of the CSR pattern of
+ * iga_csr_pattern (same Sec. 3.1 sum, the paper's insert-into-global step of
+ * Table 3): values[z] of entry (i, j) is the sum, over the elements e that
+ * hold both i and j in ascending element order, of A_elem[e][a][b] with
+ * dof(e, a) = i and dof(e, b) = j.  A_elem is any per-element [E][N][N]
+ * array laid out like K_out/M_out of iga_integrate ([n_mat_entries], device);
+ * values is [n_csr_nnz], device.  Both are double for IGA_FP64/IGA_FP64_DF
+ * plans and float otherwise; sums are formed in FP64 and rounded once.  No
+ * atomics: the result does not depend on scheduling. */
+int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_stream);
+
+/* Matrix-free operator application (3D, every patch):
+ *   y = alpha K(kappa) x + beta M(rho) x,
+ * the products K u and M u of the forward-Euler step of Sec. 2.2 (eq. Euler)
+ * for the stiffness and mass of iga_integrate, without forming a global or
+ * an element matrix: per element, x is interpolated at the quadrature points
+ * by sum factorization (one direction at a time, as in Algorithm 2 of
+ * Sec. 3.2), multiplied by the coefficient and geometry factors, and
+ * integrated back against the test functions; the element results are then
+ * summed per dof in ascending element order (deterministic, no atomics).
+ *   kappa, rho: [n_qp] or NULL (= 1);  jac: [n_qp][3][3] or NULL (= identity);
+ *   x, y: [n_dofs] device vectors, double for IGA_FP64/IGA_FP64_DF plans,
+ *         float otherwise (FP32 arithmetic with FP64 Jacobian cofactors and
+ *         determinant); y is overwritten and must not alias x.
+ * The first call allocates plan-owned scratch of n_dofmap_entries values
+ * (freed by iga_destroy). */
+int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const double* jac,
+              const void* x, double alpha, double beta, void* y, void* cuda_stream);
 
 /* With opts.profile = 1: synchronize on the last recorded event and return
  * the summed device time (ms) of the element-matrix kernel launches since the

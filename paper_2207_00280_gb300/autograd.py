@@ -1,10 +1,15 @@
-"""torch.autograd.Function for J(kappa) = u^T K(kappa) v.
+"""torch.autograd.Functions over the library's matrix-free kernels.
 
-Forward and backward both call the library's matrix-free adjoint
-(iga_integrate_backward): the forward asks for J only, the backward recomputes
+IgaBilinear: J(kappa, u, v) = u^T K(kappa) v.  The forward asks the adjoint
+kernel (iga_integrate_backward) for J only; the backward recomputes
 g = dJ/dkappa from the basis tables (no element matrix and no g is stored
-between the two; only kappa, u, v and the plan are kept).  Gradients with
-respect to u and v are not provided (they would be K v and K^T u).
+between the two) and, when u or v need gradients, applies the operator:
+dJ/du = K(kappa) v and dJ/dv = K(kappa)^T u = K(kappa) u (iga_apply).
+
+IgaApply: y = alpha K(kappa) x + beta M(rho) x.  Both operators are symmetric,
+so dL/dx = alpha K g_y + beta M g_y (one more iga_apply), and since y is linear
+in kappa, dL/dkappa_q = alpha * (dJ/dkappa_q of J = g_y^T K(kappa) x), the
+adjoint kernel with u = g_y, v = x.  rho is not differentiated.
 """
 from __future__ import annotations
 
@@ -26,12 +31,53 @@ class IgaBilinear(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gJ):
         kappa, u, v = ctx.saved_tensors
-        g = torch.empty(kappa.numel(), dtype=u.dtype, device=kappa.device)
-        ctx.plan.backward(kappa.contiguous(), u.contiguous(), v.contiguous(), grad=g, J=None,
-                          jac=ctx.jac)
-        return gJ * g.to(torch.float64).view_as(kappa), None, None, None, None
+        plan, jac = ctx.plan, ctx.jac
+        gk = gu = gv = None
+        kc = kappa.detach().contiguous()
+        if ctx.needs_input_grad[0]:
+            g = torch.empty(kappa.numel(), dtype=u.dtype, device=kappa.device)
+            plan.backward(kc, u.detach().contiguous(), v.detach().contiguous(), grad=g, J=None,
+                          jac=jac)
+            gk = gJ * g.to(torch.float64).view_as(kappa)
+        if ctx.needs_input_grad[1]:
+            gu = gJ.to(u.dtype) * plan.apply(v.detach().contiguous(), kappa=kc, jac=jac)
+        if ctx.needs_input_grad[2]:
+            gv = gJ.to(v.dtype) * plan.apply(u.detach().contiguous(), kappa=kc, jac=jac)
+        return gk, gu, gv, None, None
 
 
 def iga_bilinear(kappa, u, v, plan, jac=None):
-    """J = u^T K(kappa) v, differentiable with respect to kappa."""
+    """J = u^T K(kappa) v, differentiable with respect to kappa, u and v."""
     return IgaBilinear.apply(kappa, u, v, plan, jac)
+
+
+class IgaApply(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, kappa, x, plan, alpha=1.0, beta=0.0, rho=None, jac=None):
+        if kappa is not None and kappa.dtype != torch.float64:
+            raise TypeError("kappa must be float64 (one value per quadrature point)")
+        kc = kappa.contiguous() if kappa is not None else None
+        y = plan.apply(x.contiguous(), kappa=kc, rho=rho, jac=jac, alpha=alpha, beta=beta)
+        ctx.save_for_backward(kappa, x)
+        ctx.plan, ctx.alpha, ctx.beta, ctx.rho, ctx.jac = plan, alpha, beta, rho, jac
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        kappa, x = ctx.saved_tensors
+        plan = ctx.plan
+        gy = gy.contiguous().to(x.dtype)
+        kc = kappa.detach().contiguous() if kappa is not None else None
+        gk = gx = None
+        if ctx.needs_input_grad[1]:
+            gx = plan.apply(gy, kappa=kc, rho=ctx.rho, jac=ctx.jac, alpha=ctx.alpha, beta=ctx.beta)
+        if ctx.needs_input_grad[0] and kappa is not None:
+            g = torch.empty(kappa.numel(), dtype=x.dtype, device=x.device)
+            plan.backward(kc, gy, x.detach().contiguous(), grad=g, J=None, jac=ctx.jac)
+            gk = ctx.alpha * g.to(torch.float64).view_as(kappa)
+        return gk, gx, None, None, None, None, None
+
+
+def iga_apply(kappa, x, plan, alpha=1.0, beta=0.0, rho=None, jac=None):
+    """y = alpha K(kappa) x + beta M(rho) x, differentiable with respect to kappa and x."""
+    return IgaApply.apply(kappa, x, plan, alpha, beta, rho, jac)

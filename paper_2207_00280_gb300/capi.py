@@ -40,6 +40,7 @@ IGA_SCHED_PERSISTENT_GRAPH = 3
 
 # Every exported symbol of include/iga.h (checked by tests/test_capi_symbols.py).
 EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_basis_tables",
+            "iga_csr_pattern", "iga_assemble", "iga_apply",
             "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str")
 
 
@@ -70,7 +71,8 @@ class PlanInfo(ctypes.Structure):
                 ("qp_offset", ctypes.POINTER(ctypes.c_int64)),
                 ("dof_offset", ctypes.POINTER(ctypes.c_int64)),
                 ("mat_offset", ctypes.POINTER(ctypes.c_int64)),
-                ("dofmap_offset", ctypes.POINTER(ctypes.c_int64))]
+                ("dofmap_offset", ctypes.POINTER(ctypes.c_int64)),
+                ("n_csr_nnz", ctypes.c_int64)]
 
 
 _lib = None
@@ -97,6 +99,12 @@ def lib() -> ctypes.CDLL:
             L.iga_integrate_backward.restype = i32
             L.iga_basis_tables.argtypes = [vp, vp, vp]
             L.iga_basis_tables.restype = i32
+            L.iga_csr_pattern.argtypes = [vp, vp, vp, vp]
+            L.iga_csr_pattern.restype = i32
+            L.iga_assemble.argtypes = [vp, vp, vp, vp]
+            L.iga_assemble.restype = i32
+            L.iga_apply.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
+            L.iga_apply.restype = i32
             L.iga_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
             L.iga_profile_read.restype = i32
@@ -137,6 +145,18 @@ def iga_integrate_backward(plan, kappa, jac, u, v, grad_kappa, J_out, stream) ->
 
 def iga_basis_tables(plan, out, stream) -> int:
     return lib().iga_basis_tables(plan, out, stream)
+
+
+def iga_csr_pattern(plan, row_ptr, col_idx, stream) -> int:
+    return lib().iga_csr_pattern(plan, row_ptr, col_idx, stream)
+
+
+def iga_assemble(plan, A_elem, values, stream) -> int:
+    return lib().iga_assemble(plan, A_elem, values, stream)
+
+
+def iga_apply(plan, kappa, rho, jac, x, alpha, beta, y, stream) -> int:
+    return lib().iga_apply(plan, kappa, rho, jac, x, float(alpha), float(beta), y, stream)
 
 
 def iga_profile_read(plan):

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -23,7 +24,7 @@ struct iga_plan_s {
   int dim = 0;
   int n_patches = 0;
   std::vector<PatchDev> ph;          // host copy of the patch descriptions
-  std::vector<std::vector<int>> spans_h;  // [patch*3 + k]
+  std::vector<std::vector<int>> spans_h;  // [patch*dim + k]
   PatchDev* d_patches = nullptr;
   double* d_knots = nullptr;
   int* d_spans = nullptr;
@@ -43,6 +44,12 @@ struct iga_plan_s {
   size_t prof_used = 0;
   int64_t prof_launches = 0;
   std::vector<int64_t> elem_off, qp_off, dof_off, mat_off, dofmap_off;
+  // assembled form: per-patch coupling data (host) and the 1D records (device)
+  std::vector<CsrPatch> csr;
+  FnCouple* d_fc = nullptr;
+  // operator application: per-element results [N][E] per patch, allocated by
+  // the first iga_apply call
+  void* d_apply_scratch = nullptr;
   iga_plan_info info{};
 };
 
@@ -126,6 +133,27 @@ std::vector<int> knot_spans(const double* t, int m, int p) {
   return s;
 }
 
+// Coupling records of the nf functions of one direction.  Function i is
+// non-zero on the elements whose span s satisfies s - p <= i <= s (Sec. 3.1,
+// Remark on the support set), a contiguous run of elements because the spans
+// increase; the functions sharing an element with i are then
+// s(elo) - p .. s(ehi).
+std::vector<FnCouple> couple_1d(const std::vector<int>& spans, int p, int nf) {
+  std::vector<FnCouple> out(nf);
+  int64_t S = 0;
+  for (int i = 0; i < nf; ++i) {
+    FnCouple f;
+    f.elo = (int)(std::lower_bound(spans.begin(), spans.end(), i) - spans.begin());
+    f.ehi = (int)(std::upper_bound(spans.begin(), spans.end(), i + p) - spans.begin()) - 1;
+    f.flo = spans[f.elo] - p;
+    f.fhi = spans[f.ehi];
+    f.S = S;
+    S += f.fhi - f.flo + 1;
+    out[i] = f;
+  }
+  return out;
+}
+
 bool method_supported(const iga_plan_opts& o, int dim, int p, int q) {
   if (o.precision == IGA_FP64) {
     if (o.method == IGA_SUMFACT) return sumfact_f64_supported(dim, p, q);
@@ -161,6 +189,8 @@ void free_plan_memory(iga_plan_s* P) {
   cudaFree(P->d_jobs);
   cudaFree(P->d_err);
   cudaFree(P->d_partial);
+  cudaFree(P->d_fc);
+  cudaFree(P->d_apply_scratch);
 }
 
 int map_cuda(cudaError_t e) {
@@ -283,12 +313,42 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   P->mat_off.push_back(mat_off); P->dofmap_off.push_back(dm_off);
   P->n_jobs = (int)jobs.size();
 
+  // coupling data of the assembled form (tensor product of 1D ranges)
+  std::vector<FnCouple> fc_all;
+  int64_t nnz_off = 0;
+  for (int ip = 0; ip < n_patches; ++ip) {
+    const PatchDev& pd = P->ph[ip];
+    CsrPatch c{};
+    c.dim = pd.dim; c.p = pd.p; c.n = pd.n; c.N = pd.N;
+    c.dof_offset = pd.dof_offset; c.mat_offset = pd.mat_offset; c.elem_offset = pd.elem_offset;
+    c.nnz_offset = nnz_off;
+    int64_t nnz = 1;
+    int64_t lmax = 1;
+    for (int k = 0; k < 3; ++k) {
+      c.K[k] = pd.K[k]; c.nf[k] = pd.nf[k];
+      c.span_offset[k] = pd.span_offset[k];
+      if (k >= pd.dim) { c.fn_offset[k] = -1; c.W[k] = 1; continue; }
+      std::vector<FnCouple> f = couple_1d(P->spans_h[(size_t)ip * dim + k], pd.p, pd.nf[k]);
+      c.fn_offset[k] = (int)fc_all.size();
+      c.W[k] = f.back().S + (f.back().fhi - f.back().flo + 1);
+      int wmax = 0;
+      for (const FnCouple& x : f) wmax = std::max(wmax, x.fhi - x.flo + 1);
+      lmax *= wmax;
+      nnz *= c.W[k];
+      fc_all.insert(fc_all.end(), f.begin(), f.end());
+    }
+    c.lmax = (int)lmax;
+    nnz_off += nnz;
+    P->csr.push_back(c);
+  }
+
   cudaError_t ce = cudaGetDevice(&P->device);
   if (ce == cudaSuccess) ce = upload(&P->d_patches, P->ph.data(), P->ph.size());
   if (ce == cudaSuccess) ce = upload(&P->d_knots, knots_all.data(), knots_all.size());
   if (ce == cudaSuccess) ce = upload(&P->d_spans, spans_all.data(), spans_all.size());
   if (ce == cudaSuccess) ce = upload(&P->d_gauss, gauss_all.data(), gauss_all.size());
   if (ce == cudaSuccess) ce = upload(&P->d_jobs, jobs.data(), jobs.size());
+  if (ce == cudaSuccess) ce = upload(&P->d_fc, fc_all.data(), fc_all.size());
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_tables, sizeof(double) * (size_t)tab_off);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_err, sizeof(int));
   if (ce == cudaSuccess) ce = cudaMemset(P->d_err, 0, sizeof(int));
@@ -323,6 +383,7 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   I.elem_offset = P->elem_off.data(); I.qp_offset = P->qp_off.data();
   I.dof_offset = P->dof_off.data(); I.mat_offset = P->mat_off.data();
   I.dofmap_offset = P->dofmap_off.data();
+  I.n_csr_nnz = nnz_off;
   if (info_out) *info_out = I;
   log_msg("plan built");
   *out = P;
@@ -506,6 +567,81 @@ extern "C" int iga_basis_tables(iga_plan_t P, double* out, void* cuda_stream) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss, out, st);
+  return finish(P, st, e);
+}
+
+extern "C" int iga_csr_pattern(iga_plan_t P, int64_t* row_ptr, int32_t* col_idx,
+                               void* cuda_stream) {
+  NvtxRange range("iga_csr_pattern");
+  if (!P || !row_ptr || !col_idx) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSuccess;
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip)
+    e = launch_csr_pattern(P->csr[ip], P->d_fc, row_ptr, col_idx, st);
+  return finish(P, st, e);
+}
+
+extern "C" int iga_assemble(iga_plan_t P, const void* A_elem, void* values, void* cuda_stream) {
+  NvtxRange range("iga_assemble");
+  if (!P || !A_elem || !values) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
+  cudaError_t e = cudaSuccess;
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip)
+    e = launch_assemble(P->csr[ip], P->d_fc, P->d_spans, A_elem, values, fp64, st);
+  return finish(P, st, e);
+}
+
+extern "C" int iga_apply(iga_plan_t P, const double* kappa, const double* rho, const double* jac,
+                         const void* x, double alpha, double beta, void* y, void* cuda_stream) {
+  NvtxRange range("iga_apply");
+  if (!P || !x || !y) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  for (const PatchDev& pd : P->ph)
+    if (!apply_supported(pd.dim, pd.p, pd.q)) return IGA_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  if (!P->d_apply_scratch) {
+    // one value per (element, local function): the size of the dof map
+    cudaError_t ae = cudaMalloc(&P->d_apply_scratch, esz * (size_t)P->info.n_dofmap_entries);
+    if (ae != cudaSuccess) {
+      P->d_apply_scratch = nullptr;
+      cudaGetLastError();
+      return map_cuda(ae);
+    }
+  }
+  cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
+                                      P->d_tables, st);
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip) {
+    const PatchDev& pd = P->ph[ip];
+    ApplyArgs a{};
+    a.n_elem = (int64_t)pd.K[0] * pd.K[1] * pd.K[2];
+    a.K1 = pd.K[0]; a.K2 = pd.K[1]; a.K3 = pd.K[2];
+    for (int k = 0; k < 3; ++k) {
+      a.tab[k] = P->d_tables + pd.tab_offset[k];
+      a.span[k] = P->d_spans + pd.span_offset[k];
+    }
+    a.nf0 = pd.nf[0]; a.nf1 = pd.nf[1];
+    a.dof_offset = pd.dof_offset;
+    a.kappa = kappa ? kappa + pd.qp_offset : nullptr;
+    a.rho = rho ? rho + pd.qp_offset : nullptr;
+    a.jac = jac ? jac + pd.qp_offset * 9 : nullptr;
+    a.x = x;
+    a.alpha = alpha; a.beta = beta;
+    a.scratch = (char*)P->d_apply_scratch + esz * pd.dofmap_offset;
+    e = launch_apply(a, pd.p, pd.q, fp64, st);
+    if (e == cudaSuccess)
+      e = launch_apply_gather(P->csr[ip], P->d_fc, P->d_spans, a.scratch, y, fp64, st);
+  }
   return finish(P, st, e);
 }
 

@@ -131,4 +131,58 @@ bool sumfact_f64_supported(int dim, int p, int q);
 bool sumfact_f32_supported(int dim, int p, int q);
 bool classical_f64_supported(int dim, int p, int q);
 
+// ---- assembled (CSR) form and operator application -------------------------
+// Coupling data of one global 1D function of one direction: the elements that
+// hold it (elo..ehi, indices into the direction's element list), the functions
+// it shares an element with (flo..fhi, a contiguous range) and the prefix sum S
+// of the widths fhi - flo + 1 over the functions before it.
+struct FnCouple {
+  int flo, fhi, elo, ehi;
+  int64_t S;
+};
+
+// One patch of the assembled form.  Rows (and columns) are global dofs
+// i = i1 + nf0 (i2 + nf1 i3); the pattern is the tensor product of the 1D
+// coupling ranges, so the row start of i is
+//   nnz_offset + S3(i3) W1 W0 + w3(i3) S2(i2) W0 + w3(i3) w2(i2) S1(i1).
+struct CsrPatch {
+  int dim, p, n, N;
+  int K[3], nf[3];
+  int64_t dof_offset, mat_offset, nnz_offset, elem_offset;
+  int64_t W[3];          // sum of the widths per direction (1 for a missing direction)
+  int fn_offset[3];      // first FnCouple of direction k (-1: missing direction)
+  int span_offset[3];
+  int lmax;              // longest row
+};
+
+// CSR row pointers (int64, n_dofs + 1) and column indices (int32) of one patch.
+cudaError_t launch_csr_pattern(const CsrPatch& c, const FnCouple* fc, int64_t* row_ptr,
+                               int32_t* col_idx, cudaStream_t st);
+// values[nnz of the patch] = sum over elements (ascending) of the element
+// matrices A (patch block of a [E][N][N] array); accumulation in FP64.
+cudaError_t launch_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                            const void* A, void* values, bool fp64, cudaStream_t st);
+
+// y = alpha K(kappa) x + beta M(rho) x, matrix-free (3D).  Phase 1 writes each
+// element's local result to scratch[a * E + e]; phase 2 sums them per dof in
+// ascending element order.
+struct ApplyArgs {
+  int64_t n_elem;
+  int K1, K2, K3;
+  const double* tab[3];
+  const int* span[3];
+  int nf0, nf1;
+  int64_t dof_offset;
+  const double* kappa;   // patch-local [E][Q] or null (= 1)
+  const double* rho;     // patch-local [E][Q] or null (= 1)
+  const double* jac;     // patch-local [E][Q][9] or null
+  const void* x;         // global [n_dofs], double or float
+  double alpha, beta;
+  void* scratch;         // patch-local [N][E], double or float
+};
+cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, cudaStream_t st);
+cudaError_t launch_apply_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                                const void* scratch, void* y, bool fp64, cudaStream_t st);
+bool apply_supported(int dim, int p, int q);
+
 }  // namespace iga

@@ -1,0 +1,290 @@
+// k_assemble.cu -- global assembly of element matrices into CSR form and the
+// per-dof gather of the matrix-free operator.
+//
+// The global matrix is the sum of the element matrices placed at the support
+// index sets of the elements (Sec. 3.1, eq. 10 and the Remark on K^Delta_alpha;
+// the insertion step of Table 3, Sec. 3.3).  Here it is formed as a gather,
+// not a scatter: one warp owns one global row i, walks the elements that hold
+// function i in ascending element order, reads row a(i, e) of each element
+// matrix (N contiguous values: coalesced, and read by no other warp) and adds
+// it into a shared-memory copy of the row.  No atomics; every entry is summed
+// in ascending element order, so the result is deterministic (and identical,
+// in FP64, to a sequential sum in element order).
+//
+// The pattern is the tensor product of 1D coupling ranges: in each direction
+// the functions that share an element with i_k form the range flo..fhi, so a
+// row holds (j3, j2, j1) in flo..fhi of each direction, ascending.
+#include "iga_internal.h"
+
+namespace iga {
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+struct RowGeom {
+  FnCouple f[3];
+  int w[3];
+  int64_t start;   // first entry of the row in the patch's CSR arrays
+  int len;
+};
+
+__device__ __forceinline__ FnCouple fn_couple(const CsrPatch& c, const FnCouple* fc, int k, int i) {
+  if (c.fn_offset[k] < 0) {
+    FnCouple t;
+    t.flo = t.fhi = t.elo = t.ehi = 0;
+    t.S = 0;
+    return t;
+  }
+  return fc[c.fn_offset[k] + i];
+}
+
+__device__ __forceinline__ RowGeom row_geom(const CsrPatch& c, const FnCouple* fc, int64_t row,
+                                            int* ii) {
+  RowGeom g;
+  ii[0] = (int)(row % c.nf[0]);
+  ii[1] = (int)((row / c.nf[0]) % c.nf[1]);
+  ii[2] = (int)(row / ((int64_t)c.nf[0] * c.nf[1]));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    g.f[k] = fn_couple(c, fc, k, ii[k]);
+    g.w[k] = g.f[k].fhi - g.f[k].flo + 1;
+  }
+  g.start = c.nnz_offset + g.f[2].S * c.W[1] * c.W[0] + (int64_t)g.w[2] * g.f[1].S * c.W[0] +
+            (int64_t)g.w[2] * g.w[1] * g.f[0].S;
+  g.len = g.w[0] * g.w[1] * g.w[2];
+  return g;
+}
+
+__device__ __forceinline__ int first_fn(const CsrPatch& c, const int* spans, int k, int e) {
+  return c.fn_offset[k] < 0 ? 0 : spans[c.span_offset[k] + e] - c.p;
+}
+
+// One warp per row: row pointer (lane 0) and the row's column indices.
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+    k_csr_pattern(const CsrPatch c, const FnCouple* __restrict__ fc, int64_t* __restrict__ row_ptr,
+                  int32_t* __restrict__ col_idx) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  const int64_t row = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (row >= n_rows) return;
+  int ii[3];
+  const RowGeom g = row_geom(c, fc, row, ii);
+  if (lane == 0) {
+    row_ptr[c.dof_offset + row] = g.start;
+    if (row == n_rows - 1) row_ptr[c.dof_offset + n_rows] = g.start + g.len;
+  }
+  for (int z = lane; z < g.len; z += 32) {
+    const int j1 = g.f[0].flo + z % g.w[0];
+    const int j2 = g.f[1].flo + (z / g.w[0]) % g.w[1];
+    const int j3 = g.f[2].flo + z / (g.w[0] * g.w[1]);
+    col_idx[g.start + z] =
+        (int32_t)(c.dof_offset + j1 + (int64_t)c.nf[0] * (j2 + (int64_t)c.nf[1] * j3));
+  }
+}
+
+// One warp per row.  For each (e3, e2) the rows of up to n elements along x
+// are loaded into registers first (all loads in flight together), then added
+// in ascending e1; __syncwarp orders the additions of successive elements.
+template <typename T, int P, int DIM>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+    k_assemble(const CsrPatch c, const FnCouple* __restrict__ fc, const int* __restrict__ spans,
+               const T* __restrict__ A, T* __restrict__ values) {
+  constexpr int n = P + 1, N = DIM == 3 ? n * n * n : n * n, NB = (N + 31) / 32;
+  extern __shared__ double sbuf[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* buf = sbuf + (size_t)warp * c.lmax;
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  const int64_t row = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (row >= n_rows) return;
+  int ii[3];
+  const RowGeom g = row_geom(c, fc, row, ii);
+  for (int z = lane; z < g.len; z += 32) buf[z] = 0.0;
+  // this lane's local columns b = lane + 32 nb and their per-direction parts
+  int bl[NB][3];
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    const int b = lane + 32 * nb;
+    bl[nb][0] = b % n;
+    bl[nb][1] = (b / n) % n;
+    bl[nb][2] = b / (n * n);
+  }
+  __syncwarp();
+  for (int e3 = g.f[2].elo; e3 <= g.f[2].ehi; ++e3) {
+    const int s3 = first_fn(c, spans, 2, e3);
+    for (int e2 = g.f[1].elo; e2 <= g.f[1].ehi; ++e2) {
+      const int s2 = first_fn(c, spans, 1, e2);
+      const int64_t ebase = (int64_t)c.K[0] * (e2 + (int64_t)c.K[1] * e3);
+      const int arow23 = n * ((ii[1] - s2) + n * (ii[2] - s3));
+      T v[n][NB];
+      int s1v[n];
+#pragma unroll
+      for (int t = 0; t < n; ++t) {
+        const int e1 = g.f[0].elo + t;
+        s1v[t] = 0;
+        if (e1 <= g.f[0].ehi) {
+          const int s1 = first_fn(c, spans, 0, e1);
+          s1v[t] = s1;
+          const int a = (ii[0] - s1) + arow23;
+          const T* Arow = A + c.mat_offset + ((ebase + e1) * N + a) * (int64_t)N;
+#pragma unroll
+          for (int nb = 0; nb < NB; ++nb) {
+            const int b = lane + 32 * nb;
+            v[t][nb] = (b < N) ? Arow[b] : (T)0;
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < n; ++t) {
+        if (g.f[0].elo + t <= g.f[0].ehi) {
+#pragma unroll
+          for (int nb = 0; nb < NB; ++nb) {
+            if (lane + 32 * nb < N) {
+              const int z = ((s3 + bl[nb][2] - g.f[2].flo) * g.w[1] + (s2 + bl[nb][1] - g.f[1].flo)) *
+                                g.w[0] +
+                            (s1v[t] + bl[nb][0] - g.f[0].flo);
+              buf[z] += (double)v[t][nb];
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  for (int z = lane; z < g.len; z += 32) values[g.start + z] = (T)buf[z];
+}
+
+// Phase 2 of the operator: one thread per dof, y[i] = sum over the elements
+// holding i (ascending) of scratch[a(i, e) * E + e].  Adjacent threads read
+// adjacent elements at the same local index: coalesced.
+template <typename T, int P>
+__global__ void __launch_bounds__(256)
+    k_apply_gather(const CsrPatch c, const FnCouple* __restrict__ fc, const int* __restrict__ spans,
+                   const T* __restrict__ scratch, T* __restrict__ y) {
+  constexpr int n = P + 1;
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  const int64_t E = (int64_t)c.K[0] * c.K[1] * c.K[2];
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n_rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    int ii[3];
+    FnCouple f[3];
+    ii[0] = (int)(row % c.nf[0]);
+    ii[1] = (int)((row / c.nf[0]) % c.nf[1]);
+    ii[2] = (int)(row / ((int64_t)c.nf[0] * c.nf[1]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = fn_couple(c, fc, k, ii[k]);
+    double acc = 0.0;
+    for (int e3 = f[2].elo; e3 <= f[2].ehi; ++e3) {
+      const int a3 = ii[2] - first_fn(c, spans, 2, e3);
+      for (int e2 = f[1].elo; e2 <= f[1].ehi; ++e2) {
+        const int a2 = ii[1] - first_fn(c, spans, 1, e2);
+        const int64_t eb = (int64_t)c.K[0] * (e2 + (int64_t)c.K[1] * e3);
+        T v[n];
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+          const int e1 = f[0].elo + t;
+          v[t] = (T)0;
+          if (e1 <= f[0].ehi) {
+            const int a1 = ii[0] - first_fn(c, spans, 0, e1);
+            v[t] = scratch[(int64_t)(a1 + n * (a2 + n * a3)) * E + eb + e1];
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < n; ++t)
+          if (f[0].elo + t <= f[0].ehi) acc += (double)v[t];
+      }
+    }
+    y[c.dof_offset + row] = (T)acc;
+  }
+}
+
+template <typename T, int P, int DIM>
+cudaError_t run_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans, const void* A,
+                         void* values, cudaStream_t st) {
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  if (n_rows == 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * (size_t)c.lmax * kWarpsPerBlock;
+  auto k = k_assemble<T, P, DIM>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t blocks = (n_rows + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k<<<(unsigned)blocks, 32 * kWarpsPerBlock, smem, st>>>(c, fc, spans, (const T*)A, (T*)values);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                              const void* A, void* values, cudaStream_t st) {
+  if (c.dim == 3) {
+    switch (c.p) {
+      case 1: return run_assemble<T, 1, 3>(c, fc, spans, A, values, st);
+      case 2: return run_assemble<T, 2, 3>(c, fc, spans, A, values, st);
+      case 3: return run_assemble<T, 3, 3>(c, fc, spans, A, values, st);
+      case 4: return run_assemble<T, 4, 3>(c, fc, spans, A, values, st);
+      case 5: return run_assemble<T, 5, 3>(c, fc, spans, A, values, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (c.p) {
+    case 1: return run_assemble<T, 1, 2>(c, fc, spans, A, values, st);
+    case 2: return run_assemble<T, 2, 2>(c, fc, spans, A, values, st);
+    case 3: return run_assemble<T, 3, 2>(c, fc, spans, A, values, st);
+    case 4: return run_assemble<T, 4, 2>(c, fc, spans, A, values, st);
+    case 5: return run_assemble<T, 5, 2>(c, fc, spans, A, values, st);
+    case 6: return run_assemble<T, 6, 2>(c, fc, spans, A, values, st);
+    case 7: return run_assemble<T, 7, 2>(c, fc, spans, A, values, st);
+    case 8: return run_assemble<T, 8, 2>(c, fc, spans, A, values, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int P>
+cudaError_t run_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                       const void* scratch, void* y, cudaStream_t st) {
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  if (n_rows == 0) return cudaSuccess;
+  int64_t blocks = (n_rows + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_apply_gather<T, P><<<(unsigned)blocks, 256, 0, st>>>(c, fc, spans, (const T*)scratch, (T*)y);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                            const void* scratch, void* y, cudaStream_t st) {
+  if (c.dim != 3) return cudaErrorInvalidValue;
+  switch (c.p) {
+    case 1: return run_gather<T, 1>(c, fc, spans, scratch, y, st);
+    case 2: return run_gather<T, 2>(c, fc, spans, scratch, y, st);
+    case 3: return run_gather<T, 3>(c, fc, spans, scratch, y, st);
+    case 4: return run_gather<T, 4>(c, fc, spans, scratch, y, st);
+    case 5: return run_gather<T, 5>(c, fc, spans, scratch, y, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_csr_pattern(const CsrPatch& c, const FnCouple* fc, int64_t* row_ptr,
+                               int32_t* col_idx, cudaStream_t st) {
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  if (n_rows == 0) return cudaSuccess;
+  const int64_t blocks = (n_rows + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_csr_pattern<<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, st>>>(c, fc, row_ptr, col_idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                            const void* A, void* values, bool fp64, cudaStream_t st) {
+  return fp64 ? dispatch_assemble<double>(c, fc, spans, A, values, st)
+              : dispatch_assemble<float>(c, fc, spans, A, values, st);
+}
+
+cudaError_t launch_apply_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
+                                const void* scratch, void* y, bool fp64, cudaStream_t st) {
+  return fp64 ? dispatch_gather<double>(c, fc, spans, scratch, y, st)
+              : dispatch_gather<float>(c, fc, spans, scratch, y, st);
+}
+
+}  // namespace iga

@@ -118,6 +118,39 @@ class IgaPlan:
             raise capi.IgaError(rc, "iga_integrate_backward")
         return grad, J
 
+    @property
+    def n_csr_nnz(self) -> int:
+        return self.info.n_csr_nnz
+
+    def csr_pattern(self, stream=None):
+        """(row_ptr int64 [n_dofs + 1], col_idx int32 [nnz]) of the assembled matrix."""
+        row_ptr = torch.empty(self.n_dofs + 1, dtype=torch.int64, device="cuda")
+        col_idx = torch.empty(self.n_csr_nnz, dtype=torch.int32, device="cuda")
+        rc = capi.iga_csr_pattern(self.handle, _ptr(row_ptr), _ptr(col_idx), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_csr_pattern")
+        return row_ptr, col_idx
+
+    def assemble(self, A_elem, values=None, stream=None):
+        """CSR values of the global matrix assembled from per-element matrices
+        (a K or M output of integrate)."""
+        if values is None:
+            values = torch.empty(self.n_csr_nnz, dtype=self.out_dtype, device=A_elem.device)
+        rc = capi.iga_assemble(self.handle, _ptr(A_elem), _ptr(values), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_assemble")
+        return values
+
+    def apply(self, x, kappa=None, rho=None, jac=None, alpha=1.0, beta=0.0, y=None, stream=None):
+        """y = alpha K(kappa) x + beta M(rho) x, matrix-free."""
+        if y is None:
+            y = torch.empty_like(x)
+        rc = capi.iga_apply(self.handle, _ptr(kappa), _ptr(rho), _ptr(jac), _ptr(x), alpha, beta,
+                            _ptr(y), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_apply")
+        return y
+
     def profile_read(self):
         """(ms, launches) of the element-matrix kernels since the last read."""
         return capi.iga_profile_read(self.handle)

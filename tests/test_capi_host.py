@@ -94,6 +94,9 @@ def test_argument_errors(capi):
     assert L.iga_integrate(None, None, None, None, None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_integrate_backward(None, None, None, None, None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_basis_tables(None, None, None) == capi.IGA_ERR_ARG
+    assert L.iga_csr_pattern(None, None, None, None) == capi.IGA_ERR_ARG
+    assert L.iga_assemble(None, None, None, None) == capi.IGA_ERR_ARG
+    assert L.iga_apply(None, None, None, None, None, 1.0, 0.0, None, None) == capi.IGA_ERR_ARG
     assert L.iga_destroy(None) == capi.IGA_OK
 
 
