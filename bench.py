@@ -395,6 +395,32 @@ def _time_steps(fn, steps, stream, flush):
     return statistics.median(ts)
 
 
+def _graph_us_per_step(fn, dev, reps=50):
+    """Device time per step of fn captured in a CUDA graph and replayed reps
+    times back to back (the launch-latency form of a small workload)."""
+    import torch
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    g.replay()
+    torch.cuda.synchronize(dev)
+    st = torch.cuda.current_stream(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        g.replay()
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) * 1e3 / reps
+
+
 # error levels against the FP64 oracle (per-element relative Frobenius): the
 # tolerances the GPU tests enforce and the worst errors they measured
 FORM_ERR = {
@@ -455,7 +481,12 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
         K2, M2, D2 = pl.empty_outputs(device=dev)
         ms = _time_steps(lambda: pl.integrate(K=K2, M=M2, dof=D2, stream=stream), 20, stream, flush)
         small[f"{meth}_fp64_us_per_step"] = round(ms * 1e3, 2)
+        small[f"{meth}_fp64_graph_us_per_step"] = round(
+            _graph_us_per_step(lambda: pl.integrate(K=K2, M=M2, dof=D2), dev), 2)
         pl.close()
+    small["note"] = ("us_per_step: each call through the Python binding, host launch overhead "
+                     "included; graph_us_per_step: the same three launches (tables, dof map, "
+                     "element kernel) captured once in a CUDA graph and replayed back to back")
     forms["2d_p2_16"] = small
     # 64-patch mixed batch, FP32 mass + stiffness: one persistent graph vs per-patch launches
     specs = wl.batch_specs()

@@ -192,8 +192,9 @@ int iga_csr_pattern(iga_plan_t plan, int64_t* row_ptr, int32_t* col_idx, void* c
  * dof(e, a) = i and dof(e, b) = j.  A_elem is any per-element [E][N][N]
  * array laid out like K_out/M_out of iga_integrate ([n_mat_entries], device);
  * values is [n_csr_nnz], device.  Both are double for IGA_FP64/IGA_FP64_DF
- * plans and float otherwise; sums are formed in FP64 and rounded once.  No
- * atomics: the result does not depend on scheduling. */
+ * plans and float otherwise; each entry is summed in that precision in
+ * ascending element order.  No atomics: the result does not depend on
+ * scheduling. */
 int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_stream);
 
 /* Matrix-free operator application (3D, every patch):

