@@ -18,10 +18,22 @@
 // into bf16 hi + lo, mma.sync.m16n8k16.bf16, FP32 accumulation.  Each element
 // matrix is assembled in shared memory and written with coalesced 16-byte
 // stores when it fits, else scattered to HBM directly.
+//
+// For p <= 3 stage 3 runs on the 5th-generation tensor cores instead
+// (tcgen05.mma, accumulators in tensor memory): stage 2 writes every row
+// (a', b') -- the symmetric half computed once and written to both (a', b')
+// and (b', a') with the x patterns 10 and 01 exchanged -- in the K-major
+// core-matrix layout of umma.cuh; one thread issues the MMAs (3xTF32, or
+// BF16 x (hi + lo) for the BF16 form) into TMEM and commits them to an
+// mbarrier; after a bounded wait every warp reads its 32 TMEM lanes (one row
+// (a', b') per thread, its n^2 columns (a1, b1)) and stores the row's entries
+// K[a1 + n a'][b1 + n b'] straight to HBM: consecutive threads hold
+// consecutive b', so the stores are coalesced and need no staging.
 // MODE: 0 = stiffness and mass, 1 = stiffness only, 2 = mass only.
 #include <cuda_bf16.h>
 
 #include "iga_internal.h"
+#include "umma.cuh"
 
 namespace iga {
 namespace {
@@ -73,9 +85,54 @@ struct SF3F {
   static constexpr size_t f_pairs = al4((size_t)NSp);
   static constexpr bool STAGE =
       4 * (f_fixed + (f_alias > f_out ? f_alias : f_out) + f_pairs) <= 200 * 1024;
-  static constexpr size_t f_region = al4((STAGE && f_out > f_alias) ? f_out : f_alias);
-  static constexpr size_t smem = 4 * (f_fixed + f_region + f_pairs);
+  static constexpr size_t f_region_mma = al4((STAGE && f_out > f_alias) ? f_out : f_alias);
+  static constexpr size_t smem_mma = 4 * (f_fixed + f_region_mma + f_pairs);
+  // ---- stage 3 on tcgen05 (p <= 3) ----
+  static constexpr bool UM = P <= 3;
+  static constexpr int EB = BF ? 2 : 4;                 // bytes per operand element
+  static constexpr int MU = rup(n2 * n2, 128);          // A rows: all (a', b'), whole tiles
+  static constexpr int MTU = MU / 128;                  // 128-row MMA tiles
+  static constexpr int NU = rup(n2, 16);                // B rows (a1, b1) = MMA N
+  static constexpr int NAU = BF ? 1 : 2;                // A arrays: BF16 one, FP32 hi + lo
+  static constexpr size_t uAK = DK ? (size_t)MU * KA * EB : 0, uAM = DM ? (size_t)MU * KAM * EB : 0;
+  static constexpr size_t uBK = DK ? (size_t)NU * KA * EB : 0, uBM = DM ? (size_t)NU * KAM * EB : 0;
+  static constexpr size_t u_ops = NAU * (uAK + uAM) + 2 * (uBK + uBM);   // bytes
+  static constexpr size_t f_uops = (u_ops + 127) / 128 * 32;             // floats, 128-B multiple
+  static constexpr int TC_NEED = (DK ? MTU * NU : 0) + (DM ? MTU * NU : 0);
+  static constexpr int TCOLS = TC_NEED <= 32 ? 32 : TC_NEED <= 64 ? 64 : TC_NEED <= 128 ? 128
+                               : TC_NEED <= 256 ? 256 : 512;
+  static constexpr size_t f_base = f_px + f_py + f_pz;
+  static constexpr size_t f_region = UM ? al4(f_alias) : f_region_mma;
+  // UM: [px py pz][operands][alias region][mbarrier (2 floats) + TMEM slot]
+  static constexpr size_t smem = UM ? 4 * (f_base + f_uops + f_region + 4) + 128 : smem_mma;
 };
+
+template <int EB, int KDIM>
+__device__ __forceinline__ int uoff(int r, int k) {
+  // byte offset of element (r, k) of a K-major operand with KDIM elements per row
+  return (r >> 3) * (KDIM * EB * 8) + ((k * EB) >> 4) * 128 + (r & 7) * 16 + ((k * EB) & 15);
+}
+
+__device__ __forceinline__ float tf32_trunc(float v) {
+  return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+}
+
+// Store v at element (r, k) of an A or B operand: FP32 as hi (the word
+// itself; the tensor core reads its top 19 bits) and lo = v - hi; BF16 as one
+// rounded value (A) or hi + lo (B, when lo != nullptr).
+template <bool BF, int KDIM>
+__device__ __forceinline__ void uput(unsigned char* hi, unsigned char* lo, int r, int k, float v) {
+  if (BF) {
+    const int o = uoff<2, KDIM>(r, k);
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    *(__nv_bfloat16*)(hi + o) = h;
+    if (lo) *(__nv_bfloat16*)(lo + o) = __float2bfloat16_rn(v - __bfloat162float(h));
+  } else {
+    const int o = uoff<4, KDIM>(r, k);
+    *(float*)(hi + o) = v;
+    if (lo) *(float*)(lo + o) = v - tf32_trunc(v);
+  }
+}
 
 __device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -260,9 +317,133 @@ __device__ __forceinline__ void copy_out(const float* __restrict__ s, float* __r
 // Once per CTA, before its first element: the table of symmetric pairs
 // (a',b'), and zeros in the GEMM operands (their padding rows and columns are
 // never written by the element stages).
+// Stage 3 of one matrix on tcgen05 (called by one thread): for every 128-row
+// tile of A, D = A B^T over the K steps of 32 bytes, accumulated in TMEM
+// columns d0 + t NU.  FP32: 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi); BF16:
+// A (B_hi + B_lo).
+template <class C, int KD>
+__device__ __forceinline__ void sf3_issue_um(uint32_t d0, const unsigned char* Ah,
+                                             const unsigned char* Al, const unsigned char* Bh,
+                                             const unsigned char* Bl) {
+  constexpr int EB = C::EB;
+  constexpr uint32_t SBO = KD * EB * 8, LBO = 128;
+  constexpr uint32_t IDESC = umma_idesc(EB == 2 ? 1u : 2u, 128, C::NU);
+  constexpr int KS = KD * EB / 32;
+  const uint32_t ah = smem_u32(Ah), bh = smem_u32(Bh), bl = smem_u32(Bl);
+  const uint32_t al = Al ? smem_u32(Al) : 0u;
+#pragma unroll 1
+  for (int t = 0; t < C::MTU; ++t) {
+    const uint32_t d = d0 + (uint32_t)(t * C::NU);
+    const uint32_t ta = (uint32_t)t * 16u * SBO;   // 128 rows = 16 groups of 8
+#pragma unroll
+    for (int s = 0; s < KS; ++s) {
+      const uint64_t dAh = umma_desc(ah + ta + 256u * s, LBO, SBO);
+      const uint64_t dBh = umma_desc(bh + 256u * s, LBO, SBO);
+      const uint64_t dBl = umma_desc(bl + 256u * s, LBO, SBO);
+      if (EB == 2) {
+        umma_f16(d, dAh, dBh, IDESC, s > 0 ? 1u : 0u);
+        umma_f16(d, dAh, dBl, IDESC, 1u);
+      } else {
+        const uint64_t dAl = umma_desc(al + ta + 256u * s, LBO, SBO);
+        umma_tf32(d, dAh, dBh, IDESC, s > 0 ? 1u : 0u);
+        umma_tf32(d, dAh, dBl, IDESC, 1u);
+        umma_tf32(d, dAl, dBh, IDESC, 1u);
+      }
+    }
+  }
+}
+
+// Entries K[a1 + n a'][b1 + n b'] = v[a1 n + b1] of one TMEM row (a', b'):
+// n contiguous floats per a1, vectorised when the element matrix is aligned.
+template <int n, int N>
+__device__ __forceinline__ void sf3_store_row_um(float* g, int ap, int bp, const float* v) {
+  float* row = g + (int64_t)(n * ap) * N + n * bp;
+  if constexpr (n == 4) {
+    if ((((uintptr_t)g) & 15u) == 0) {
+#pragma unroll
+      for (int a1 = 0; a1 < 4; ++a1)
+        *(float4*)(row + a1 * N) = make_float4(v[4 * a1], v[4 * a1 + 1], v[4 * a1 + 2], v[4 * a1 + 3]);
+      return;
+    }
+  } else if constexpr (n == 2) {
+    if ((((uintptr_t)g) & 7u) == 0) {
+#pragma unroll
+      for (int a1 = 0; a1 < 2; ++a1) *(float2*)(row + a1 * N) = make_float2(v[2 * a1], v[2 * a1 + 1]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+    for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
+}
+
+// Shared-memory carve-up of the tcgen05 form.
+template <class C>
+struct UPtrs {
+  unsigned char *AKh, *AKl, *AMh, *AMl, *BKh, *BKl, *BMh, *BMl;
+  float* region;
+  uint64_t* mbar;
+  uint32_t* tslot;
+  __device__ __forceinline__ explicit UPtrs(float* smf) {
+    // operands start on a 128-byte boundary (the size reserves the slack)
+    uintptr_t o = (uintptr_t)(smf + C::f_base);
+    o = (o + 127) & ~(uintptr_t)127;
+    unsigned char* ops = (unsigned char*)o;
+    AKh = ops;
+    AKl = C::NAU == 2 ? AKh + C::uAK : nullptr;
+    AMh = ops + C::NAU * C::uAK;
+    AMl = C::NAU == 2 ? AMh + C::uAM : nullptr;
+    BKh = ops + C::NAU * (C::uAK + C::uAM);
+    BKl = BKh + C::uBK;
+    BMh = BKh + 2 * C::uBK;
+    BMl = BMh + C::uBM;
+    region = (float*)(ops + C::f_uops * 4);
+    mbar = (uint64_t*)(region + C::f_region);
+    tslot = (uint32_t*)(mbar + 1);
+  }
+};
+
+// tcgen05 form, once per CTA: zero the operands (padding rows and K columns
+// are never written by the element stages), allocate the CTA's TMEM columns
+// (warp 0) and initialise the MMA-completion mbarrier.
+template <int P, int QG, bool GEN, int MODE, bool BF>
+__device__ __forceinline__ void sf3_f32_cta_setup_um(float* smf) {
+  using C = SF3F<P, QG, GEN, MODE, BF>;
+  UPtrs<C> U(smf);
+  uint32_t* ops = (uint32_t*)U.AKh;
+  for (int i = threadIdx.x; i < (int)(C::f_uops); i += C::NT) ops[i] = 0u;
+  if (threadIdx.x < 32) {
+    tmem_alloc(smem_u32(U.tslot), C::TCOLS);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(U.mbar), 1);
+    fence_mbar_init();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+
+// tcgen05 form, once per CTA after its last element: free the TMEM columns.
+template <int P, int QG, bool GEN, int MODE, bool BF>
+__device__ __forceinline__ void sf3_f32_cta_teardown_um(float* smf) {
+  using C = SF3F<P, QG, GEN, MODE, BF>;
+  UPtrs<C> U(smf);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (threadIdx.x < 32) tmem_dealloc(*U.tslot, C::TCOLS);
+}
+
 template <int P, int QG, bool GEN, int MODE, bool BF>
 __device__ __forceinline__ void sf3_f32_cta_setup(float* smf) {
   using C = SF3F<P, QG, GEN, MODE, BF>;
+  if constexpr (C::UM) {
+    sf3_f32_cta_setup_um<P, QG, GEN, MODE, BF>(smf);
+    return;
+  }
   constexpr int Np = C::Np, NSp = C::NSp, NT = C::NT;
   float* AK = smf + C::f_px + C::f_py + C::f_pz;
   float* region = AK + C::f_A4 + C::f_B4;
@@ -278,12 +459,16 @@ __device__ __forceinline__ void sf3_f32_cta_setup(float* smf) {
 
 // One element, all stages.  Called by the per-patch kernel (e = blockIdx.x)
 // and by the persistent queue kernel.
+// Returns false only if the tcgen05 form gave up waiting for its MMAs (the
+// error word then holds IGA_ERR_TIMEOUT and the caller stops).  `phase` is the
+// parity of the MMA-completion mbarrier (one phase per element).
 template <int P, int QG, bool GEN, int MODE, bool BF>
-__device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, float* smf) {
+__device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, float* smf,
+                                                uint32_t& phase) {
   using C = SF3F<P, QG, GEN, MODE, BF>;
   constexpr int n = C::n, q = C::q, Q = C::Q, n2 = C::n2, N = C::N, NS1 = C::NS1,
                 Np = C::Np, NSp = C::NSp, NT = C::NT, REC = C::REC, RW = C::RW;
-  constexpr bool DK = C::DK, DM = C::DM;
+  constexpr bool DK = C::DK, DM = C::DM, UM = C::UM;
   float* px = smf;                                   // [n2][4][q]
   float* py = px + C::f_px;                          // [n2][4][q]
   float* pz = py + C::f_py;                          // [n2][3][q]
@@ -291,7 +476,8 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   float* AM = AK + (DK ? (size_t)C::MPs * C::LDA : 0);  // [MPs][LDAM]  mass GEMM operand
   uint32_t* BK = (uint32_t*)(AK + C::f_A4);   // [2][NPAD][LDB]
   uint32_t* BM = BK + (DK ? (size_t)2 * C::NPAD * C::LDB : 0);  // [2][NPAD][LDBM]
-  float* region = (float*)BK + C::f_B4;
+  const UPtrs<C> U(smf);                             // tcgen05 form
+  float* region = UM ? U.region : (float*)BK + C::f_B4;
   float* T1 = region;                                // [7][n2][q][q]
   float* coef = T1 + C::f_T1;                        // [7][Q]
   double* geo = (double*)(coef + C::f_coef);
@@ -390,8 +576,25 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
   // ---- B operands: x patterns split into hi + lo (TF32 bits or bf16 pairs) ------
   // B[(a1,b1)][X q + k1] = P^X_x[a1][b1][k1] in the record order 11, 00, 10, 01
   // (the same X order as the A columns); mass: B[(a1,b1)][k1] = P^00_x
+  if constexpr (UM) {
+    // B[(a1,b1)][X q + k1] in the core-matrix layout, hi + lo
+    if (DK) {
+      for (int i = tid; i < C::NU * C::KA; i += NT) {
+        const int nn = i / C::KA, k = i % C::KA;
+        const float v = (nn < n2 && k < C::NXK * q) ? px[nn * RW + k] : 0.f;
+        uput<BF, C::KA>(U.BKh, U.BKl, nn, k, v);
+      }
+    }
+    if (DM) {
+      for (int i = tid; i < C::NU * C::KAM; i += NT) {
+        const int nn = i / C::KAM, k = i % C::KAM;
+        const float v = (nn < n2 && k < q) ? px[nn * RW + q + k] : 0.f;
+        uput<BF, C::KAM>(U.BMh, U.BMl, nn, k, v);
+      }
+    }
+  }
 #pragma unroll 1
-  for (int mat = 0; mat < 2; ++mat) {
+  for (int mat = 0; mat < (UM ? 0 : 2); ++mat) {
     if ((mat == 0 && !DK) || (mat == 1 && !DM)) continue;
     uint32_t* Bm = mat == 0 ? BK : BM;
     const int ld = mat == 0 ? C::LDB : C::LDBM;
@@ -527,11 +730,30 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
           }
           if (DM) cm = fmaf(y[k2], tm[k2], cm);
         }
-        if (DK) {
-          AK[pp * C::LDA + 0 * q + k1] = c11;
-          AK[pp * C::LDA + 1 * q + k1] = c00a + c00b;
+        if constexpr (UM) {
+          // rows (a', b') and (b', a'): the patterns 11, 00 and the mass are
+          // symmetric under the exchange
+          const int bp = b2 + n * b3;
+          const int m1 = ap * n2 + bp, m2 = bp * n2 + ap;
+          if (DK) {
+            uput<BF, C::KA>(U.AKh, U.AKl, m1, 0 * q + k1, c11);
+            uput<BF, C::KA>(U.AKh, U.AKl, m1, 1 * q + k1, c00a + c00b);
+            if (m2 != m1) {
+              uput<BF, C::KA>(U.AKh, U.AKl, m2, 0 * q + k1, c11);
+              uput<BF, C::KA>(U.AKh, U.AKl, m2, 1 * q + k1, c00a + c00b);
+            }
+          }
+          if (DM) {
+            uput<BF, C::KAM>(U.AMh, U.AMl, m1, k1, cm);
+            if (m2 != m1) uput<BF, C::KAM>(U.AMh, U.AMl, m2, k1, cm);
+          }
+        } else {
+          if (DK) {
+            AK[pp * C::LDA + 0 * q + k1] = c11;
+            AK[pp * C::LDA + 1 * q + k1] = c00a + c00b;
+          }
+          if (DM) AM[pp * C::LDAM + k1] = cm;
         }
-        if (DM) AM[pp * C::LDAM + k1] = cm;
       }
     }
     // (b) C10[a'][b'] for all (a', b'): row pp(a',b') column 2q+k1 when a' <= b'
@@ -565,13 +787,57 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
           }
           const float val = acc0 + acc1;
           const int bp = b2 + n * b3;
-          if (ap <= bp) AK[upper_index<Np>(ap, bp) * C::LDA + 2 * q + k1] = val;
-          if (bp <= ap) AK[upper_index<Np>(bp, ap) * C::LDA + 3 * q + k1] = val;
+          if constexpr (UM) {
+            // C10 of row (a', b') is C01 of row (b', a')
+            uput<BF, C::KA>(U.AKh, U.AKl, ap * n2 + bp, 2 * q + k1, val);
+            uput<BF, C::KA>(U.AKh, U.AKl, bp * n2 + ap, 3 * q + k1, val);
+          } else {
+            if (ap <= bp) AK[upper_index<Np>(ap, bp) * C::LDA + 2 * q + k1] = val;
+            if (bp <= ap) AK[upper_index<Np>(bp, ap) * C::LDA + 3 * q + k1] = val;
+          }
         }
       }
     }
   }
   __syncthreads();
+
+  if constexpr (UM) {
+    // ---- stage 3 on tcgen05: MMAs into TMEM, then TMEM rows straight to HBM -----
+    fence_proxy_async_smem();  // the operands written above are read by the tensor core
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *U.tslot;
+    constexpr uint32_t colM = DK ? C::MTU * C::NU : 0;
+    if (tid == 0) {
+      if (DK) sf3_issue_um<C, C::KA>(tmem, U.AKh, U.AKl, U.BKh, U.BKl);
+      if (DM) sf3_issue_um<C, C::KAM>(tmem + colM, U.AMh, U.AMl, U.BMh, U.BMl);
+      umma_commit(smem_u32(U.mbar));
+    }
+    const bool done = mbar_wait_bounded(smem_u32(U.mbar), phase, 1000000000ull);
+    phase ^= 1u;
+    if (!__syncthreads_and(done)) {
+      if (tid == 0) atomicCAS(A.err, 0, (int)IGA_ERR_TIMEOUT);
+      return false;
+    }
+    fence_after_sync();
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll 1
+    for (int mat = 0; mat < 2; ++mat) {
+      if ((mat == 0 && !DK) || (mat == 1 && !DM)) continue;
+      float* g = (float*)(mat == 0 ? A.K_out : A.M_out) + e * (int64_t)N * N;
+      const uint32_t col0 = mat == 0 ? 0u : colM;
+#pragma unroll 1
+      for (int t = warp >> 2; t < C::MTU; t += NT / 128) {
+        float v[16];
+        tmem_ld16(tmem + col0 + (uint32_t)(t * C::NU) + ((uint32_t)(32 * (warp & 3)) << 16), v);
+        const int m = t * 128 + 32 * (warp & 3) + lane;
+        if (m < n2 * n2) sf3_store_row_um<n, N>(g, m / n2, m % n2, v);
+      }
+    }
+    fence_before_sync();
+    return true;
+  }
 
   // ---- stage 3 on the tensor cores, one matrix at a time ---------------------------
 #pragma unroll 1
@@ -590,14 +856,17 @@ __device__ __forceinline__ void sf3_f32_element(const ElemArgs& A, int64_t e, fl
       __syncthreads();
     }
   }
+  return true;
 }
 
 template <int P, int QG, bool GEN, int MODE, bool BF>
 __global__ void __launch_bounds__(256) k_sf3_f32(const ElemArgs A) {
   extern __shared__ __align__(16) float smf[];
   sf3_f32_cta_setup<P, QG, GEN, MODE, BF>(smf);
+  uint32_t phase = 0;
   for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x)
-    sf3_f32_element<P, QG, GEN, MODE, BF>(A, e, smf);
+    if (!sf3_f32_element<P, QG, GEN, MODE, BF>(A, e, smf, phase)) break;
+  if constexpr (SF3F<P, QG, GEN, MODE, BF>::UM) sf3_f32_cta_teardown_um<P, QG, GEN, MODE, BF>(smf);
 }
 
 // Persistent form: every CTA pops work items (patch, first element, count)
@@ -611,6 +880,7 @@ __global__ void __launch_bounds__(256) k_sf3_f32_queue(const QueueArgs B) {
   __shared__ int s_item;
   const unsigned long long t0 = global_timer_ns();
   sf3_f32_cta_setup<P, QG, GEN, MODE, BF>(smf);
+  uint32_t phase = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       int it = -1;
@@ -648,9 +918,37 @@ __global__ void __launch_bounds__(256) k_sf3_f32_queue(const QueueArgs B) {
     A.K_out = B.K_out ? (void*)((float*)B.K_out + pd.mat_offset) : nullptr;
     A.M_out = B.M_out ? (void*)((float*)B.M_out + pd.mat_offset) : nullptr;
     A.err = B.err;
-    for (int64_t e = w.e0; e < w.e0 + w.count; ++e)
-      sf3_f32_element<P, QG, GEN, MODE, BF>(A, e, smf);
+    bool ok = true;
+    for (int64_t e = w.e0; e < w.e0 + w.count && ok; ++e)
+      ok = sf3_f32_element<P, QG, GEN, MODE, BF>(A, e, smf, phase);
+    if (!ok) break;
   }
+  if constexpr (SF3F<P, QG, GEN, MODE, BF>::UM) sf3_f32_cta_teardown_um<P, QG, GEN, MODE, BF>(smf);
+}
+
+// Resident CTAs per SM of a kernel using TMEM.  The runtime's occupancy query
+// answers 1 for such kernels (it cannot see how many TMEM columns a CTA
+// takes), so the count comes from the kernel's registers and shared memory,
+// the SM's limits, and the 512 TMEM columns of an SM.
+cudaError_t resident_ctas_tmem(const void* kernel, int nt, size_t smem, int tcols, int* out) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  int dev = 0, smem_sm = 0, res_blk = 0, regs_sm = 0, thr_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&res_blk, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  if (e != cudaSuccess) return e;
+  const size_t per_block = (smem + fa.sharedSizeBytes + res_blk + 127) / 128 * 128;
+  int n = (int)(smem_sm / per_block);
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = regs_sm / (regs_warp * (nt / 32));
+  if (by_regs < n) n = by_regs;
+  if (thr_sm / nt < n) n = thr_sm / nt;
+  if (512 / tcols < n) n = 512 / tcols;
+  *out = n > 0 ? n : 1;
+  return cudaSuccess;
 }
 
 template <int P, int QG, bool GEN, int MODE, bool BF>
@@ -674,7 +972,10 @@ cudaError_t run(const ElemArgs& a, cudaStream_t st) {
       int dev = 0, sms = 0, per_sm = 0;
       if (e == cudaSuccess) e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem);
+      if (e == cudaSuccess) {
+        if (C::UM) e = resident_ctas_tmem((const void*)k, C::NT, C::smem, C::TCOLS, &per_sm);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem);
+      }
       if (e != cudaSuccess) return e;
       capacity = sms * (per_sm > 0 ? per_sm : 1);
     }
@@ -698,7 +999,10 @@ cudaError_t run_queue(const QueueArgs& b, int grid, cudaStream_t st, int* max_gr
       int dev = 0, sms = 0, per_sm = 0;
       e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem);
+      if (e == cudaSuccess) {
+        if (C::UM) e = resident_ctas_tmem((const void*)k, C::NT, C::smem, C::TCOLS, &per_sm);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem);
+      }
       if (e != cudaSuccess) return e;
       *max_grid = sms * (per_sm > 0 ? per_sm : 1);
       return cudaSuccess;
