@@ -58,11 +58,22 @@ struct SF3F {
   // pattern records, floats: x [a1][b1][4][q] (11, 00, 10, 01); y [a2][b2][4][q]
   // (00, 11, 10, 01); z [a3][b3][3][q] (00, 11, 01)
   static constexpr int RW = 4 * q;
-  static constexpr size_t f_px = (size_t)n2 * RW, f_py = (size_t)n2 * RW, f_pz = al4((size_t)n2 * 3 * q);
+  // z-pattern records and stage-1 rows are padded to an odd number of words
+  // when their natural length is even, so that threads indexing consecutive
+  // (a3, b3) hit different shared-memory banks
+  static constexpr int RZ = (3 * q) % 2 == 0 ? 3 * q + 1 : 3 * q;       // z record stride
+  static constexpr int TS = (q * q) % 2 == 0 ? q * q + 1 : q * q;       // stage-1 row stride
+  static constexpr size_t f_px = (size_t)n2 * RW, f_py = (size_t)n2 * RW, f_pz = al4((size_t)n2 * RZ);
   // coefficients [7][Q]: 0 D00, 1 D11, 2 D01, 3 DM, 4 D22, 5 D02, 6 D12 (identity: 0 = W kappa, 3 = W rho)
-  static constexpr size_t f_coef = al4((size_t)7 * Q);
+  // stage-1 terms and coefficients held: all seven with a general Jacobian;
+  // with identity geometry only D00 (= D11 = D22), the mass weight and the
+  // z-derivative term (slots 0, 1, 2 for terms 0, 3, 4)
+  static constexpr int NTERM = GEN ? 7 : 3, NCOEF = GEN ? 7 : 2;
+  static constexpr int ts(int t) { return GEN ? t : (t == 0 ? 0 : (t == 3 ? 1 : 2)); }
+  static constexpr int cs(int t) { return GEN ? t : (t == 0 ? 0 : 1); }
+  static constexpr size_t f_coef = al4((size_t)NCOEF * Q);
   // stage-1 buffers T[7][a3][b3][k1][k2] (same indices as the coefficients)
-  static constexpr size_t f_T1 = al4((size_t)7 * n2 * q * q);
+  static constexpr size_t f_T1 = al4((size_t)NTERM * n2 * TS);
   // stage-3 GEMM: A rows = symmetric pairs (padded to 16), depth padded to the k-step
   static constexpr int NXK = GEN ? 4 : 2;
   static constexpr int KSTEP = BF ? 16 : 8;
@@ -111,6 +122,29 @@ template <int EB, int KDIM>
 __device__ __forceinline__ int uoff(int r, int k) {
   // byte offset of element (r, k) of a K-major operand with KDIM elements per row
   return (r >> 3) * (KDIM * EB * 8) + ((k * EB) >> 4) * 128 + (r & 7) * 16 + ((k * EB) & 15);
+}
+
+// Physical operand row of (a', b') in the tcgen05 form.  For n^2 = 16 the
+// low three bits of the row are rotated by a' within each 16-row block, so
+// that the threads of a warp writing rows (a', b') for consecutive a' -- and
+// the mirrored rows (b', a') -- land on different shared-memory banks.  A
+// permutation of A's rows only permutes the TMEM rows of the product; the
+// epilogue inverts it (urow_inv).
+template <int n2>
+__device__ __forceinline__ int urow(int x, int y) {
+  if constexpr (n2 == 16) return 16 * x + ((y & 8) | ((x + y) & 7));
+  else return x * n2 + y;
+}
+template <int n2>
+__device__ __forceinline__ void urow_inv(int r, int& x, int& y) {
+  if constexpr (n2 == 16) {
+    x = r >> 4;
+    const int lo = r & 15;
+    y = (lo & 8) | ((lo - x) & 7);
+  } else {
+    x = r / n2;
+    y = r % n2;
+  }
 }
 
 __device__ __forceinline__ float tf32_trunc(float v) {
@@ -459,6 +493,76 @@ __device__ __forceinline__ void sf3_f32_cta_setup(float* smf) {
 
 // One element, all stages.  Called by the per-patch kernel (e = blockIdx.x)
 // and by the persistent queue kernel.
+// Issue the cp.async copies of element e's inputs: its three 1D basis
+// records, kappa, rho and (curved geometry) the Jacobians.
+template <class C, bool GEN>
+__device__ __forceinline__ void sf3_f32_stage_inputs(const ElemArgs& A, int64_t e, double* rec,
+                                                     double* kap, double* rho, double* jac) {
+  constexpr int REC = C::REC, Q = C::Q, NT = C::NT;
+  const int tid = threadIdx.x;
+  const int e1 = (int)(e % A.K1);
+  const int e2 = (int)((e / A.K1) % A.K2);
+  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  for (int i = tid; i < 3 * REC; i += NT) {
+    const int d = i / REC, j = i - d * REC;
+    const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
+    const double* tb = d == 0 ? A.tab[0] : (d == 1 ? A.tab[1] : A.tab[2]);
+    cp_async8(rec + i, tb + (int64_t)ek * REC + j);
+  }
+  for (int k = tid; k < Q; k += NT) {
+    if (A.kappa) cp_async8(kap + k, A.kappa + e * Q + k);
+    else kap[k] = 1.0;
+    if (A.rho) cp_async8(rho + k, A.rho + e * Q + k);
+    else rho[k] = 1.0;
+  }
+  if (GEN) {
+    const double* G = A.jac + e * Q * 9;
+    for (int i = tid; i < 9 * Q; i += NT) cp_async8(jac + i, G + i);
+  }
+}
+
+// Coefficients of quadrature point k: cofactors and determinant of the
+// Jacobian in FP64, the rest in FP32.  General geometry:
+//   D = (w kappa / |det G|) c^T c  (c = cofactor matrix, G^{-T} = c / det G),
+// the six distinct entries in slots 0 D00, 1 D11, 2 D01, 4 D22, 5 D02, 6 D12,
+// and slot 3 the mass weight w |det G| rho; identity geometry: w kappa, w rho.
+// Kept out of line: inlined, its FP64 temporaries raise the register count of
+// the whole element kernel (64 instead of 40 at p = 3), which costs resident CTAs.
+template <class C, bool GEN>
+__device__ __noinline__ void sf3_f32_coef(int k, const float* recf, const double* kap,
+                                             const double* rho, const double* jac, float* coef) {
+  constexpr int q = C::q, n = C::n, Q = C::Q, REC = C::REC;
+  const int k1 = k % q, k2 = (k / q) % q, k3 = k / (q * q);
+  const float* w0 = recf + 2 * q * n;
+  const float W = w0[k1] * (w0 + REC)[k2] * (w0 + 2 * REC)[k3];
+  const float kp = (float)kap[k], rh = (float)rho[k];
+  if (GEN) {
+    const double* G = jac + 9 * k;
+    const double g00 = G[0], g01 = G[1], g02 = G[2], g10 = G[3], g11 = G[4], g12 = G[5],
+                 g20 = G[6], g21 = G[7], g22 = G[8];
+    const double d00 = g11 * g22 - g12 * g21, d01 = g12 * g20 - g10 * g22,
+                 d02 = g10 * g21 - g11 * g20;
+    const double det = g00 * d00 + g01 * d01 + g02 * d02;
+    const float c00 = (float)d00, c01 = (float)d01, c02 = (float)d02;
+    const float c10 = (float)(g02 * g21 - g01 * g22), c11 = (float)(g00 * g22 - g02 * g20),
+                c12 = (float)(g01 * g20 - g00 * g21);
+    const float c20 = (float)(g01 * g12 - g02 * g11), c21 = (float)(g02 * g10 - g00 * g12),
+                c22 = (float)(g00 * g11 - g01 * g10);
+    const float adet = (float)fabs(det);
+    const float s = W * kp / adet;
+    coef[C::cs(0) * Q + k] = s * (c00 * c00 + c10 * c10 + c20 * c20);
+    coef[C::cs(1) * Q + k] = s * (c01 * c01 + c11 * c11 + c21 * c21);
+    coef[C::cs(2) * Q + k] = s * (c00 * c01 + c10 * c11 + c20 * c21);
+    coef[C::cs(3) * Q + k] = W * adet * rh;
+    coef[C::cs(4) * Q + k] = s * (c02 * c02 + c12 * c12 + c22 * c22);
+    coef[C::cs(5) * Q + k] = s * (c00 * c02 + c10 * c12 + c20 * c22);
+    coef[C::cs(6) * Q + k] = s * (c01 * c02 + c11 * c12 + c21 * c22);
+  } else {
+    coef[C::cs(0) * Q + k] = W * kp;
+    coef[C::cs(3) * Q + k] = W * rh;
+  }
+}
+
 // Returns false only if the tcgen05 form gave up waiting for its MMAs (the
 // error word then holds IGA_ERR_TIMEOUT and the caller stops).  `phase` is the
 // parity of the MMA-completion mbarrier (one phase per element).
@@ -495,35 +599,23 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
   const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
   __syncthreads();  // shared memory of the previous element is no longer read
 
-  // ---- coalesced staging of this element's inputs; zero the GEMM operands -------
+  // ---- coalesced staging of this element's inputs -------------------------------
   // every copy of this thread is issued before any completes (cp.async)
-  for (int i = tid; i < 3 * REC; i += NT) {
-    const int d = i / REC, j = i - d * REC;
-    const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
-    const double* tb = d == 0 ? A.tab[0] : (d == 1 ? A.tab[1] : A.tab[2]);
-    cp_async8(rec + i, tb + (int64_t)ek * REC + j);
-  }
-  for (int k = tid; k < Q; k += NT) {
-    if (A.kappa) cp_async8(kap + k, A.kappa + e * Q + k);
-    else kap[k] = 1.0;
-    if (A.rho) cp_async8(rho + k, A.rho + e * Q + k);
-    else rho[k] = 1.0;
-  }
-  if (GEN) {
-    const double* G = A.jac + e * Q * 9;
-    for (int i = tid; i < 9 * Q; i += NT) cp_async8(jac + i, G + i);
-  }
+  sf3_f32_stage_inputs<C, GEN>(A, e, rec, kap, rho, jac);
   cp_async_wait_all();
-  __syncthreads();
+  // each thread converts the records it copied itself (visible to it after the
+  // wait), so one barrier serves both
   for (int i = tid; i < 3 * REC; i += NT) recf[i] = (float)rec[i];
   __syncthreads();
 
-  // ---- 1D factor pattern records in FP32 ---------------------------------------
-  for (int i = tid; i < n2 * q; i += NT) {
+  // ---- quadrature-point coefficients (taken from the last threads down) and ------
+  // ---- the 1D factor pattern records in FP32 (from the first threads up) --------
+  for (int k = NT - 1 - tid; k < Q; k += NT) sf3_f32_coef<C, GEN>(k, recf, kap, rho, jac, coef);
+  for (int it = tid; it < 3 * n2 * q; it += NT) {
+    const int d = it / (n2 * q), i = it % (n2 * q);
     const int a = i / (n * q), b = (i / q) % n, k = i % q;
     const int ab = a * n + b;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    {
       const float* v = recf + d * REC;
       const float* dv = v + q * n;
       const float va = v[k * n + a], vb = v[k * n + b], da = dv[k * n + a], db = dv[k * n + b];
@@ -534,41 +626,9 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
         float* r = py + ab * RW;
         r[0 * q + k] = va * vb; r[1 * q + k] = da * db; r[2 * q + k] = da * vb; r[3 * q + k] = va * db;
       } else {
-        float* r = pz + ab * 3 * q;
+        float* r = pz + ab * C::RZ;
         r[0 * q + k] = va * vb; r[1 * q + k] = da * db; r[2 * q + k] = va * db;
       }
-    }
-  }
-  // ---- coefficients: cofactors and determinant in FP64, the rest in FP32 ------
-  for (int k = tid; k < Q; k += NT) {
-    const int k1 = k % q, k2 = (k / q) % q, k3 = k / (q * q);
-    const float* w0 = recf + 2 * q * n;
-    const float W = w0[k1] * (w0 + REC)[k2] * (w0 + 2 * REC)[k3];
-    const float kp = (float)kap[k], rh = (float)rho[k];
-    if (GEN) {
-      const double* G = jac + 9 * k;
-      const double g00 = G[0], g01 = G[1], g02 = G[2], g10 = G[3], g11 = G[4], g12 = G[5],
-                   g20 = G[6], g21 = G[7], g22 = G[8];
-      const double d00 = g11 * g22 - g12 * g21, d01 = g12 * g20 - g10 * g22,
-                   d02 = g10 * g21 - g11 * g20;
-      const double det = g00 * d00 + g01 * d01 + g02 * d02;
-      const float c00 = (float)d00, c01 = (float)d01, c02 = (float)d02;
-      const float c10 = (float)(g02 * g21 - g01 * g22), c11 = (float)(g00 * g22 - g02 * g20),
-                  c12 = (float)(g01 * g20 - g00 * g21);
-      const float c20 = (float)(g01 * g12 - g02 * g11), c21 = (float)(g02 * g10 - g00 * g12),
-                  c22 = (float)(g00 * g11 - g01 * g10);
-      const float adet = (float)fabs(det);
-      const float s = W * kp / adet;
-      coef[0 * Q + k] = s * (c00 * c00 + c10 * c10 + c20 * c20);
-      coef[1 * Q + k] = s * (c01 * c01 + c11 * c11 + c21 * c21);
-      coef[2 * Q + k] = s * (c00 * c01 + c10 * c11 + c20 * c21);
-      coef[3 * Q + k] = W * adet * rh;
-      coef[4 * Q + k] = s * (c02 * c02 + c12 * c12 + c22 * c22);
-      coef[5 * Q + k] = s * (c00 * c02 + c10 * c12 + c20 * c22);
-      coef[6 * Q + k] = s * (c01 * c02 + c11 * c12 + c21 * c22);
-    } else {
-      coef[0 * Q + k] = W * kp;
-      coef[3 * Q + k] = W * rh;
     }
   }
   __syncthreads();
@@ -639,11 +699,11 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
 #pragma unroll
     for (int k3 = 0; k3 < q; ++k3) {
       const int o = kk + q * q * k3;
-      d0[k3] = coef[0 * Q + o];
-      d3[k3] = coef[3 * Q + o];
+      d0[k3] = coef[C::cs(0) * Q + o];
+      d3[k3] = coef[C::cs(3) * Q + o];
       if (GEN) {
-        d1[k3] = coef[1 * Q + o]; d2[k3] = coef[2 * Q + o]; d4[k3] = coef[4 * Q + o];
-        d5[k3] = coef[5 * Q + o]; d6[k3] = coef[6 * Q + o];
+        d1[k3] = coef[C::cs(1) * Q + o]; d2[k3] = coef[C::cs(2) * Q + o]; d4[k3] = coef[C::cs(4) * Q + o];
+        d5[k3] = coef[C::cs(5) * Q + o]; d6[k3] = coef[C::cs(6) * Q + o];
       }
     }
     const int b3e = (part + 1) * CH < n ? (part + 1) * CH : n;
@@ -651,7 +711,7 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
     for (int bo = 0; bo < CH; ++bo) {
       const int b3 = part * CH + bo;
       if (b3 >= b3e) break;
-      const float* z = Pz + (a3 * n + b3) * 3 * q;
+      const float* z = Pz + (a3 * n + b3) * C::RZ;
       float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f, t6 = 0.f;
 #pragma unroll
       for (int k3 = 0; k3 < q; ++k3) {
@@ -668,20 +728,20 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
         }
         if (DM) t3 = fmaf(z00, d3[k3], t3);
       }
-      const int o = (a3 * n + b3) * q * q + kk;
-      constexpr int S = n2 * q * q;
+      const int o = (a3 * n + b3) * C::TS + kk;
+      constexpr int S = n2 * C::TS;
       if (DK) {
-        T1[0 * S + o] = t0; T1[4 * S + o] = t4;
-        if (GEN) { T1[1 * S + o] = t1; T1[2 * S + o] = t2; T1[5 * S + o] = t5; T1[6 * S + o] = t6; }
+        T1[C::ts(0) * S + o] = t0; T1[C::ts(4) * S + o] = t4;
+        if (GEN) { T1[C::ts(1) * S + o] = t1; T1[C::ts(2) * S + o] = t2; T1[C::ts(5) * S + o] = t5; T1[C::ts(6) * S + o] = t6; }
       }
-      if (DM) T1[3 * S + o] = t3;
+      if (DM) T1[C::ts(3) * S + o] = t3;
     }
   }
   __syncthreads();
 
   // ---- stage 2: the GEMM operand rows (a',b'), a' <= b' --------------------------
   {
-    constexpr int S = n2 * q * q;
+    constexpr int S = n2 * C::TS;
     constexpr int T11 = GEN ? 1 : 0;
     // (a) C11, C00, CM: item = (a3 <= b3, k1, a2)
     for (int it = tid; it < NS1 * q * n; it += NT) {
@@ -690,17 +750,17 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
       while (rr >= n - a3) { rr -= n - a3; ++a3; }
       const int b3 = a3 + rr;
       // T layout [t][a3][b3][k1 + q k2]
-      const int ab3 = (a3 * n + b3) * q * q + k1, ba3 = (b3 * n + a3) * q * q + k1;
+      const int ab3 = (a3 * n + b3) * C::TS + k1, ba3 = (b3 * n + a3) * C::TS + k1;
       float t00[q], t11[q], t22[q], tab[q], tba[q], tm[q];
 #pragma unroll
       for (int k2 = 0; k2 < q; ++k2) {
         if (DK) {
-          t00[k2] = T1[0 * S + ab3 + q * k2];
-          t11[k2] = T1[T11 * S + ab3 + q * k2];
-          t22[k2] = T1[4 * S + ab3 + q * k2];
-          if (GEN) { tab[k2] = T1[6 * S + ab3 + q * k2]; tba[k2] = T1[6 * S + ba3 + q * k2]; }
+          t00[k2] = T1[C::ts(0) * S + ab3 + q * k2];
+          t11[k2] = T1[C::ts(T11) * S + ab3 + q * k2];
+          t22[k2] = T1[C::ts(4) * S + ab3 + q * k2];
+          if (GEN) { tab[k2] = T1[C::ts(6) * S + ab3 + q * k2]; tba[k2] = T1[C::ts(6) * S + ba3 + q * k2]; }
         }
-        if (DM) tm[k2] = T1[3 * S + ab3 + q * k2];
+        if (DM) tm[k2] = T1[C::ts(3) * S + ab3 + q * k2];
       }
       const int ap = a2 + n * a3;
       const int b2s = (a3 == b3 ? a2 : 0);
@@ -734,7 +794,7 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
           // rows (a', b') and (b', a'): the patterns 11, 00 and the mass are
           // symmetric under the exchange
           const int bp = b2 + n * b3;
-          const int m1 = ap * n2 + bp, m2 = bp * n2 + ap;
+          const int m1 = urow<n2>(ap, bp), m2 = urow<n2>(bp, ap);
           if (DK) {
             uput<BF, C::KA>(U.AKh, U.AKl, m1, 0 * q + k1, c11);
             uput<BF, C::KA>(U.AKh, U.AKl, m1, 1 * q + k1, c00a + c00b);
@@ -762,12 +822,12 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
       for (int it = tid; it < n2 * q * n; it += NT) {
         const int a2 = it % n, r = it / n, k1 = r % q, ab = r / q;
         const int a3 = ab / n, b3 = ab % n;
-        const int o = (a3 * n + b3) * q * q + k1;
+        const int o = (a3 * n + b3) * C::TS + k1;
         float t01[q], t02[q];
 #pragma unroll
         for (int k2 = 0; k2 < q; ++k2) {
-          t01[k2] = T1[2 * S + o + q * k2];
-          t02[k2] = T1[5 * S + o + q * k2];
+          t01[k2] = T1[C::ts(2) * S + o + q * k2];
+          t02[k2] = T1[C::ts(5) * S + o + q * k2];
         }
         const int ap = a2 + n * a3;
 #pragma unroll
@@ -789,8 +849,8 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
           const int bp = b2 + n * b3;
           if constexpr (UM) {
             // C10 of row (a', b') is C01 of row (b', a')
-            uput<BF, C::KA>(U.AKh, U.AKl, ap * n2 + bp, 2 * q + k1, val);
-            uput<BF, C::KA>(U.AKh, U.AKl, bp * n2 + ap, 3 * q + k1, val);
+            uput<BF, C::KA>(U.AKh, U.AKl, urow<n2>(ap, bp), 2 * q + k1, val);
+            uput<BF, C::KA>(U.AKh, U.AKl, urow<n2>(bp, ap), 3 * q + k1, val);
           } else {
             if (ap <= bp) AK[upper_index<Np>(ap, bp) * C::LDA + 2 * q + k1] = val;
             if (bp <= ap) AK[upper_index<Np>(bp, ap) * C::LDA + 3 * q + k1] = val;
@@ -832,7 +892,11 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
         float v[16];
         tmem_ld16(tmem + col0 + (uint32_t)(t * C::NU) + ((uint32_t)(32 * (warp & 3)) << 16), v);
         const int m = t * 128 + 32 * (warp & 3) + lane;
-        if (m < n2 * n2) sf3_store_row_um<n, N>(g, m / n2, m % n2, v);
+        if (m < n2 * n2) {
+          int ap, bp;
+          urow_inv<n2>(m, ap, bp);
+          sf3_store_row_um<n, N>(g, ap, bp, v);
+        }
       }
     }
     fence_before_sync();
@@ -972,6 +1036,10 @@ cudaError_t run(const ElemArgs& a, cudaStream_t st) {
       int dev = 0, sms = 0, per_sm = 0;
       if (e == cudaSuccess) e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      // the tcgen05 form sizes its grid from the full shared-memory carveout
+      if (e == cudaSuccess && C::UM)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
       if (e == cudaSuccess) {
         if (C::UM) e = resident_ctas_tmem((const void*)k, C::NT, C::smem, C::TCOLS, &per_sm);
         else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::NT, C::smem);
@@ -994,6 +1062,9 @@ cudaError_t run_queue(const QueueArgs& b, int grid, cudaStream_t st, int* max_gr
   } else {
     auto k = k_sf3_f32_queue<P, QG, GEN, MODE, BF>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (e == cudaSuccess && C::UM)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (max_grid) {
       int dev = 0, sms = 0, per_sm = 0;
