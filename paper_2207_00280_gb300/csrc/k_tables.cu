@@ -3,27 +3,32 @@
 
 namespace iga {
 
-// One thread per (patch, direction, element) record.  For every Gauss point
-// of the element the p+1 non-zero B-splines B_{s-p+r;p}(xi), r = 0..p, are
-// built by the triangular form of the Cox--de Boor recursion (Sec. 2.3,
-// eq. cox2: each degree combines two neighbours of the previous degree, the
-// degree-0 start being the indicator of span s, eq. cox1).  Only the
-// non-vanishing functions are carried, so no 0/0 term ever arises.  The
-// derivative uses the degree p-1 row:
+// One thread per (patch, direction, element) record and Gauss point j.  At
+// the point the p+1 non-zero B-splines B_{s-p+r;p}(xi), r = 0..p, are built by
+// the triangular form of the Cox--de Boor recursion (Sec. 2.3, eq. cox2: each
+// degree combines two neighbours of the previous degree, the degree-0 start
+// being the indicator of span s, eq. cox1).  Only the non-vanishing functions
+// are carried, so no 0/0 term ever arises.  The derivative uses the degree
+// p-1 row:
 //   B'_{i;p} = p B_{i;p-1}/(t_{i+p}-t_i) - p B_{i+1;p-1}/(t_{i+p+1}-t_{i+1}).
 // The record also stores the Gauss weight scaled by half the span length.
+// The FP64 pipe of GB300 retires about two lanes per SM per clock, so each
+// thread's serial chain is kept short (one point) and the threads are spread
+// over many SMs (small blocks).
 __global__ void k_basis_tables(const TableJob* __restrict__ jobs, int n_jobs,
                                const double* __restrict__ knots,
                                const double* __restrict__ gauss, double* __restrict__ tables) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = g / kMaxGauss, j = g % kMaxGauss;
   if (r >= n_jobs) return;
   const TableJob J = jobs[r];
+  if (j >= J.q) return;
   const double* t = knots + J.knot_off;
   const int p = J.p, q = J.q, n = p + 1, s = J.span;
   const double a = t[s], b = t[s + 1];
   const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
   double* out = tables + J.out_off;
-  for (int j = 0; j < q; ++j) {
+  {
     const double xi = mid + half * gauss[J.gauss_off + j];
     double N[kMaxDegree2D + 1], Nm1[kMaxDegree2D + 1];
     double left[kMaxDegree2D + 1], right[kMaxDegree2D + 1];
@@ -58,45 +63,46 @@ __global__ void k_basis_tables(const TableJob* __restrict__ jobs, int n_jobs,
 cudaError_t launch_basis_tables(const TableJob* jobs, int n_jobs, const double* knots,
                                 const double* gauss, double* tables, cudaStream_t st) {
   if (n_jobs <= 0) return cudaSuccess;
-  const int bs = 128;
-  k_basis_tables<<<(n_jobs + bs - 1) / bs, bs, 0, st>>>(jobs, n_jobs, knots, gauss, tables);
+  const int bs = 32;
+  const int64_t threads = (int64_t)n_jobs * kMaxGauss;
+  k_basis_tables<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(jobs, n_jobs, knots, gauss,
+                                                                     tables);
   return cudaGetLastError();
 }
 
 // Global dof of every local function of every element (support set of the
 // Remark in Sec. 3.1): dof = dof_offset + sum_k (s_k - p + a_k) stride_k.
-// One thread per (element, local function); consecutive threads write
-// consecutive entries.
+// One block per element (grid-stride), one thread per local function:
+// consecutive threads write consecutive entries.  The planner keeps every
+// index below 2^31, so the arithmetic is 32-bit (64-bit division is slow).
 __global__ void k_dofmap(const PatchDev* __restrict__ pdp, const int* __restrict__ spans,
-                         int32_t* __restrict__ dof, int64_t total) {
+                         int32_t* __restrict__ dof, int n_elem) {
   const PatchDev pd = *pdp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = i / pd.N;
-    const int a = (int)(i - e * pd.N);
-    const int e1 = (int)(e % pd.K[0]);
-    const int64_t r = e / pd.K[0];
-    const int e2 = (int)(r % pd.K[1]);
-    const int e3 = (int)(r / pd.K[1]);
-    const int a1 = a % pd.n;
-    const int a2 = (a / pd.n) % pd.n;
-    const int a3 = a / (pd.n * pd.n);
-    int64_t g = spans[pd.span_offset[0] + e1] - pd.p + a1;
-    g += (int64_t)(spans[pd.span_offset[1] + e2] - pd.p + a2) * pd.nf[0];
-    if (pd.dim == 3)
-      g += (int64_t)(spans[pd.span_offset[2] + e3] - pd.p + a3) * pd.nf[0] * pd.nf[1];
-    dof[i] = (int32_t)(pd.dof_offset + g);
+  const int a = threadIdx.x;
+  if (a >= pd.N) return;
+  const int a1 = a % pd.n;
+  const int a2 = (a / pd.n) % pd.n;
+  const int a3 = a / (pd.n * pd.n);
+  const int base = (int)pd.dof_offset;
+  for (int e = blockIdx.x; e < n_elem; e += gridDim.x) {
+    const int e1 = e % pd.K[0];
+    const int r = e / pd.K[0];
+    const int e2 = r % pd.K[1];
+    const int e3 = r / pd.K[1];
+    int g = spans[pd.span_offset[0] + e1] - pd.p + a1;
+    g += (spans[pd.span_offset[1] + e2] - pd.p + a2) * pd.nf[0];
+    if (pd.dim == 3) g += (spans[pd.span_offset[2] + e3] - pd.p + a3) * pd.nf[0] * pd.nf[1];
+    dof[(int64_t)e * pd.N + a] = base + g;
   }
 }
 
 cudaError_t launch_dofmap(const PatchDev* pdp, const PatchDev& ph, const int* spans,
                           int32_t* dof_out, cudaStream_t st) {
-  const int64_t total = (int64_t)ph.K[0] * ph.K[1] * ph.K[2] * ph.N;
-  if (total == 0) return cudaSuccess;
-  const int bs = 256;
-  int64_t blocks = (total + bs - 1) / bs;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  k_dofmap<<<(unsigned)blocks, bs, 0, st>>>(pdp, spans, dof_out, total);
+  const int64_t E = (int64_t)ph.K[0] * ph.K[1] * ph.K[2];
+  if (E == 0) return cudaSuccess;
+  const int bs = (ph.N + 31) / 32 * 32;
+  const int64_t blocks = E < 152 * 64 ? E : 152 * 64;
+  k_dofmap<<<(unsigned)blocks, bs, 0, st>>>(pdp, spans, dof_out, (int)E);
   return cudaGetLastError();
 }
 
