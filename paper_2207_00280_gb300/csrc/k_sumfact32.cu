@@ -19,16 +19,19 @@
 // matrix is assembled in shared memory and written with coalesced 16-byte
 // stores when it fits, else scattered to HBM directly.
 //
-// For p <= 3 stage 3 runs on the 5th-generation tensor cores instead
-// (tcgen05.mma, accumulators in tensor memory): stage 2 writes every row
-// (a', b') -- the symmetric half computed once and written to both (a', b')
-// and (b', a') with the x patterns 10 and 01 exchanged -- in the K-major
-// core-matrix layout of umma.cuh; one thread issues the MMAs (3xTF32, or
-// BF16 x (hi + lo) for the BF16 form) into TMEM and commits them to an
-// mbarrier; after a bounded wait every warp reads its 32 TMEM lanes (one row
-// (a', b') per thread, its n^2 columns (a1, b1)) and stores the row's entries
-// K[a1 + n a'][b1 + n b'] straight to HBM: consecutive threads hold
-// consecutive b', so the stores are coalesced and need no staging.
+// For p <= 3 (and p = 4 in BF16) stage 3 runs on the 5th-generation tensor
+// cores instead (tcgen05.mma, accumulators in tensor memory).  p <= 3: stage
+// 2 writes every row (a', b') -- the symmetric half computed once and written
+// to both (a', b') and (b', a') with the x patterns 10 and 01 exchanged -- in
+// the K-major core-matrix layout of umma.cuh; one thread issues the MMAs
+// (3xTF32, or BF16 x (hi + lo) for the BF16 form) into TMEM and commits them
+// to an mbarrier; after a bounded wait every warp reads its 32 TMEM lanes (one
+// row (a', b') per thread, its n^2 columns (a1, b1)) and stores the row's
+// entries K[a1 + n a'][b1 + n b'] straight to HBM: consecutive threads hold
+// consecutive b', so the stores are coalesced and need no staging.  p = 4:
+// the rows a' <= b' only; the epilogue writes each entry and its mirror into a
+// staged copy of the element matrix (over the operands, dead by then) and
+// copies it to HBM with aligned 16-byte stores.
 // MODE: 0 = stiffness and mass, 1 = stiffness only, 2 = mass only.
 #include <cuda_bf16.h>
 
@@ -98,10 +101,16 @@ struct SF3F {
       4 * (f_fixed + (f_alias > f_out ? f_alias : f_out) + f_pairs) <= 200 * 1024;
   static constexpr size_t f_region_mma = al4((STAGE && f_out > f_alias) ? f_out : f_alias);
   static constexpr size_t smem_mma = 4 * (f_fixed + f_region_mma + f_pairs);
-  // ---- stage 3 on tcgen05 (p <= 3) ----
-  static constexpr bool UM = P <= 3;
+  // ---- stage 3 on tcgen05: p <= 3, and p = 4 in BF16 ----
+  // (FP32 at p = 4 needs hi and lo operands of 74 KB: two CTAs per SM, where
+  // the mma.sync form below is faster)
+  static constexpr bool UM = P <= 3 || (P == 4 && BF);
+  // p <= 3: A holds every row (a', b') and the epilogue stores rows straight to
+  // HBM; p = 4: A holds the rows a' <= b' and the epilogue stages the element
+  // matrix (both triangles) in shared memory over the dead operands
+  static constexpr bool FULLR = P <= 3;
   static constexpr int EB = BF ? 2 : 4;                 // bytes per operand element
-  static constexpr int MU = rup(n2 * n2, 128);          // A rows: all (a', b'), whole tiles
+  static constexpr int MU = rup(FULLR ? n2 * n2 : NSp, 128);   // A rows, whole tiles
   static constexpr int MTU = MU / 128;                  // 128-row MMA tiles
   static constexpr int NU = rup(n2, 16);                // B rows (a1, b1) = MMA N
   static constexpr int NAU = BF ? 1 : 2;                // A arrays: BF16 one, FP32 hi + lo
@@ -113,9 +122,18 @@ struct SF3F {
   static constexpr int TCOLS = TC_NEED <= 32 ? 32 : TC_NEED <= 64 ? 64 : TC_NEED <= 128 ? 128
                                : TC_NEED <= 256 ? 256 : 512;
   static constexpr size_t f_base = f_px + f_py + f_pz;
-  static constexpr size_t f_region = UM ? al4(f_alias) : f_region_mma;
-  // UM: [px py pz][operands][alias region][mbarrier (2 floats) + TMEM slot]
-  static constexpr size_t smem = UM ? 4 * (f_base + f_uops + f_region + 4) + 128 : smem_mma;
+  // tcgen05 region: the geometry staging and the FP32 records are dead once
+  // the coefficients are formed, before stage 1 writes T1, so they share its
+  // space; then the coefficients
+  static constexpr size_t f_geo_u = 2 * d_geo + f_recf;
+  static constexpr size_t f_T1u = al4(f_T1 > f_geo_u ? f_T1 : f_geo_u);
+  static constexpr size_t f_region_u = al4(f_T1u + f_coef);
+  // p = 4: the staged element matrix covers the operands and the region
+  static constexpr size_t f_span_u = (FULLR || f_uops + f_region_u >= f_out + 4)
+                                         ? f_uops + f_region_u : al4(f_out + 4);
+  static constexpr size_t f_region = UM ? f_region_u : f_region_mma;
+  // UM: [px py pz][operands][region (or the staged matrix)][mbarrier + TMEM slot]
+  static constexpr size_t smem = UM ? 4 * (f_base + f_span_u + 4) + 128 : smem_mma;
 };
 
 template <int EB, int KDIM>
@@ -433,7 +451,7 @@ struct UPtrs {
     BMh = BKh + 2 * C::uBK;
     BMl = BMh + C::uBM;
     region = (float*)(ops + C::f_uops * 4);
-    mbar = (uint64_t*)(region + C::f_region);
+    mbar = (uint64_t*)((float*)ops + C::f_span_u);
     tslot = (uint32_t*)(mbar + 1);
   }
 };
@@ -582,9 +600,10 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
   uint32_t* BM = BK + (DK ? (size_t)2 * C::NPAD * C::LDB : 0);  // [2][NPAD][LDBM]
   const UPtrs<C> U(smf);                             // tcgen05 form
   float* region = UM ? U.region : (float*)BK + C::f_B4;
-  float* T1 = region;                                // [7][n2][q][q]
-  float* coef = T1 + C::f_T1;                        // [7][Q]
-  double* geo = (double*)(coef + C::f_coef);
+  float* T1 = region;                                // [NTERM][n2][TS]
+  float* coef = T1 + (UM ? C::f_T1u : C::f_T1);      // [NCOEF][Q]
+  // tcgen05 form: the staging lives in T1's space (dead before stage 1)
+  double* geo = UM ? (double*)T1 : (double*)(coef + C::f_coef);
   double* rec = geo;                                 // [3][REC]
   double* kap = rec + 3 * REC;                       // [Q]
   double* rho = kap + Q;                             // [Q]
@@ -790,7 +809,21 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
           }
           if (DM) cm = fmaf(y[k2], tm[k2], cm);
         }
-        if constexpr (UM) {
+        if constexpr (UM && !C::FULLR) {
+          // rows a' <= b' only; the K columns past the data are rewritten with
+          // zeros (the staged matrix of the previous element covered them)
+          if (DK) {
+            uput<BF, C::KA>(U.AKh, U.AKl, pp, 0 * q + k1, c11);
+            uput<BF, C::KA>(U.AKh, U.AKl, pp, 1 * q + k1, c00a + c00b);
+            if (k1 == 0)
+              for (int kz = C::NXK * q; kz < C::KA; ++kz) uput<BF, C::KA>(U.AKh, U.AKl, pp, kz, 0.f);
+          }
+          if (DM) {
+            uput<BF, C::KAM>(U.AMh, U.AMl, pp, k1, cm);
+            if (k1 == 0)
+              for (int kz = q; kz < C::KAM; ++kz) uput<BF, C::KAM>(U.AMh, U.AMl, pp, kz, 0.f);
+          }
+        } else if constexpr (UM) {
           // rows (a', b') and (b', a'): the patterns 11, 00 and the mass are
           // symmetric under the exchange
           const int bp = b2 + n * b3;
@@ -847,7 +880,10 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
           }
           const float val = acc0 + acc1;
           const int bp = b2 + n * b3;
-          if constexpr (UM) {
+          if constexpr (UM && !C::FULLR) {
+            if (ap <= bp) uput<BF, C::KA>(U.AKh, U.AKl, upper_index<Np>(ap, bp), 2 * q + k1, val);
+            if (bp <= ap) uput<BF, C::KA>(U.AKh, U.AKl, upper_index<Np>(bp, ap), 3 * q + k1, val);
+          } else if constexpr (UM) {
             // C10 of row (a', b') is C01 of row (b', a')
             uput<BF, C::KA>(U.AKh, U.AKl, urow<n2>(ap, bp), 2 * q + k1, val);
             uput<BF, C::KA>(U.AKh, U.AKl, urow<n2>(bp, ap), 3 * q + k1, val);
@@ -887,16 +923,47 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
       if ((mat == 0 && !DK) || (mat == 1 && !DM)) continue;
       float* g = (float*)(mat == 0 ? A.K_out : A.M_out) + e * (int64_t)N * N;
       const uint32_t col0 = mat == 0 ? 0u : colM;
+      if constexpr (C::FULLR) {
 #pragma unroll 1
-      for (int t = warp >> 2; t < C::MTU; t += NT / 128) {
-        float v[16];
-        tmem_ld16(tmem + col0 + (uint32_t)(t * C::NU) + ((uint32_t)(32 * (warp & 3)) << 16), v);
-        const int m = t * 128 + 32 * (warp & 3) + lane;
-        if (m < n2 * n2) {
-          int ap, bp;
-          urow_inv<n2>(m, ap, bp);
-          sf3_store_row_um<n, N>(g, ap, bp, v);
+        for (int t = warp >> 2; t < C::MTU; t += NT / 128) {
+          float v[16];
+          tmem_ld16(tmem + col0 + (uint32_t)(t * C::NU) + ((uint32_t)(32 * (warp & 3)) << 16), v);
+          const int m = t * 128 + 32 * (warp & 3) + lane;
+          if (m < n2 * n2) {
+            int ap, bp;
+            urow_inv<n2>(m, ap, bp);
+            sf3_store_row_um<n, N>(g, ap, bp, v);
+          }
         }
+      } else {
+        // rows a' <= b': entry (a1 + n a', b1 + n b') and its mirror into the
+        // staged matrix (over the operands, all read by now), then one
+        // coalesced copy to HBM
+        float* stage = (float*)U.AKh + stage_offset(g);
+#pragma unroll 1
+        for (int t = warp >> 2; t < C::MTU; t += NT / 128) {
+          float v[C::NU];
+          const uint32_t ta = tmem + col0 + (uint32_t)(t * C::NU) + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll
+          for (int c = 0; c < C::NU; c += 16) tmem_ld16(ta + c, v + c);
+          const int m = t * 128 + 32 * (warp & 3) + lane;
+          if (m < NSp) {
+            int ap = 0, r = m;
+            while (r >= Np - ap) { r -= Np - ap; ++ap; }
+            const int bp = ap + r;
+#pragma unroll
+            for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+              for (int b1 = 0; b1 < n; ++b1) {
+                const float x = v[a1 * n + b1];
+                stage[(a1 + n * ap) * N + n * bp + b1] = x;
+                if (ap != bp) stage[(b1 + n * bp) * N + n * ap + a1] = x;
+              }
+          }
+        }
+        __syncthreads();
+        copy_out<N * N, NT>(stage, g);
+        __syncthreads();
       }
     }
     fence_before_sync();
