@@ -82,6 +82,12 @@ def lib():
             L.ora_assemble.restype = ctypes.c_int
             L.ora_apply.argtypes = [pp, dp, dp, dp, dp, dp, dp]
             L.ora_apply.restype = ctypes.c_int
+            L.ora_wq_points.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
+            L.ora_wq_points.restype = ctypes.c_int
+            L.ora_wq_weights.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
+            L.ora_wq_weights.restype = ctypes.c_int
+            L.ora_wq_mass.argtypes = [pp, dp, dp, dp, dp]
+            L.ora_wq_mass.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -127,6 +133,27 @@ def basis_1d(t, p: int, s: int, q: int):
     val = np.zeros((q, p + 1)); der = np.zeros((q, p + 1))
     lib().ora_basis_1d(_ptr(t), p, s, q, _ptr(xi), _ptr(w), _ptr(val), _ptr(der))
     return xi, w, val, der
+
+
+def wq_points(t, p: int) -> np.ndarray:
+    """Global weighted-quadrature points of one direction (see iga_oracle.h)."""
+    t = _f64(t)
+    cap = 4 * len(t) + 8
+    x = np.zeros(cap)
+    n = lib().ora_wq_points(_ptr(t), len(t), p, _ptr(x), cap)
+    if n < 1:
+        raise ValueError("oracle rejected its arguments")
+    return x[:n].copy()
+
+
+def wq_weights(t, p: int, x) -> np.ndarray:
+    """W[n_functions][n_points]: least-norm weighted-quadrature weights."""
+    t = _f64(t)
+    x = _f64(x)
+    W = np.zeros((len(t) - p - 1, len(x)))
+    if lib().ora_wq_weights(_ptr(t), len(t), p, _ptr(x), len(x), _ptr(W)) != 0:
+        raise ValueError("oracle: singular weighted-quadrature system")
+    return W
 
 
 class Patch:
@@ -250,3 +277,15 @@ class Patch:
         if rc != 0:
             raise ValueError("oracle rejected its arguments")
         return yK, yM
+
+    def wq_mass(self, row_ptr, col_idx, c=None):
+        """CSR values of the weighted-quadrature mass matrix; c at the tensor grid
+        of wq_points (x fastest) or None (= 1)."""
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        c = _f64(c)
+        vals = np.zeros(len(col_idx))
+        if lib().ora_wq_mass(ctypes.byref(self._s), _ptr(c), _ptr(row_ptr), _ptr(col_idx),
+                             _ptr(vals)) != 0:
+            raise ValueError("oracle: weighted quadrature failed")
+        return vals

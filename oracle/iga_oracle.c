@@ -687,3 +687,182 @@ int ora_apply(const ora_patch* pt, const double* kappa, const double* rho, const
   free_layout(&L);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Weighted quadrature for the mass matrix (Sec. 1.2 names it; the rule is   */
+/* defined in iga_oracle.h).                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* B_{i;p}(x) with the right end of the domain included: an open knot vector
+ * makes the last function 1 there and every other one 0 (the half-open
+ * recursion alone would give 0 for all). */
+static double wq_bspline(const double* t, int m, int i, int p, double x) {
+  if (x >= t[m - 1]) return (i == m - p - 2) ? 1.0 : 0.0;
+  return ora_bspline(t, i, p, x);
+}
+
+int ora_wq_points(const double* t, int m, int p, double* x, int cap) {
+  if (!t || !x || m < 2 * p + 2 || p < 1) return -1;
+  int* sp = (int*)malloc(sizeof(int) * (size_t)m);
+  const int K = ora_spans(t, m, p, sp);
+  int n = 0;
+  for (int e = 0; e < K; ++e) {
+    const double a = t[sp[e]], b = t[sp[e] + 1];
+    if (n >= cap) { free(sp); return -1; }
+    x[n++] = a;
+    if (e < p || e >= K - p) {
+      for (int r = 1; r <= p; ++r) {
+        if (n >= cap) { free(sp); return -1; }
+        x[n++] = a + (b - a) * (double)r / (double)(p + 1);
+      }
+    } else {
+      if (n >= cap) { free(sp); return -1; }
+      x[n++] = 0.5 * (a + b);
+    }
+  }
+  if (n >= cap) { free(sp); return -1; }
+  x[n++] = t[sp[K - 1] + 1];
+  free(sp);
+  return n;
+}
+
+/* Solve the dense system G y = r (n x n, row-major, overwritten) by Gaussian
+ * elimination with partial pivoting.  Returns 0, or -1 if a pivot vanishes. */
+static int wq_solve(double* G, double* r, int n) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(G[i * n + k]) > fabs(G[piv * n + k])) piv = i;
+    if (!(fabs(G[piv * n + k]) > 0.0)) return -1;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) { double tmp = G[k * n + j]; G[k * n + j] = G[piv * n + j]; G[piv * n + j] = tmp; }
+      double tmp = r[k]; r[k] = r[piv]; r[piv] = tmp;
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const double f = G[i * n + k] / G[k * n + k];
+      for (int j = k; j < n; ++j) G[i * n + j] -= f * G[k * n + j];
+      r[i] -= f * r[k];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double s = r[k];
+    for (int j = k + 1; j < n; ++j) s -= G[k * n + j] * r[j];
+    r[k] = s / G[k * n + k];
+  }
+  return 0;
+}
+
+int ora_wq_weights(const double* t, int m, int p, const double* x, int np, double* W) {
+  if (!t || !x || !W || np < 1) return -1;
+  const int nf = m - p - 1;
+  double gx[64], gw[64];
+  if (ora_gauss_legendre(p + 1, gx, gw)) return -1;
+  int* sp = (int*)malloc(sizeof(int) * (size_t)m);
+  const int K = ora_spans(t, m, p, sp);
+  const int cap = 2 * p + 1;
+  double* A = (double*)malloc(sizeof(double) * (size_t)cap * np);
+  double* G = (double*)malloc(sizeof(double) * (size_t)cap * cap);
+  double* r = (double*)malloc(sizeof(double) * (size_t)cap);
+  int js[64];
+  int rc = 0;
+  for (int i = 0; i < nf * np; ++i) W[i] = 0.0;
+  for (int i = 0; i < nf && rc == 0; ++i) {
+    const double lo = t[i], hi = t[i + p + 1];
+    /* points in the closed support */
+    int qlo = 0;
+    while (qlo < np && x[qlo] < lo) ++qlo;
+    int qhi = qlo;
+    while (qhi < np && x[qhi] <= hi) ++qhi;
+    const int nq = qhi - qlo;
+    /* test-trial pairs with a support overlap of positive length */
+    int nj = 0;
+    for (int j = 0; j < nf; ++j) {
+      const double olo = t[i] > t[j] ? t[i] : t[j];
+      const double ohi = t[i + p + 1] < t[j + p + 1] ? t[i + p + 1] : t[j + p + 1];
+      if (ohi > olo && nj < 64) js[nj++] = j;
+    }
+    if (nj > cap || nq < nj) { rc = -1; break; }
+    for (int a = 0; a < nj; ++a) {
+      for (int q = 0; q < nq; ++q) A[a * nq + q] = wq_bspline(t, m, js[a], p, x[qlo + q]);
+      /* exact int B_i B_j: Gauss with p + 1 points on every element */
+      double s = 0.0;
+      for (int e = 0; e < K; ++e) {
+        const double ea = t[sp[e]], eb = t[sp[e] + 1];
+        if (eb <= lo || ea >= hi) continue;
+        for (int g = 0; g < p + 1; ++g) {
+          const double xi = 0.5 * (ea + eb) + 0.5 * (eb - ea) * gx[g];
+          s += 0.5 * (eb - ea) * gw[g] * ora_bspline(t, i, p, xi) * ora_bspline(t, js[a], p, xi);
+        }
+      }
+      r[a] = s;
+    }
+    for (int a = 0; a < nj; ++a)
+      for (int b = 0; b < nj; ++b) {
+        double s = 0.0;
+        for (int q = 0; q < nq; ++q) s += A[a * nq + q] * A[b * nq + q];
+        G[a * nj + b] = s;
+      }
+    if (wq_solve(G, r, nj)) { rc = -1; break; }
+    for (int q = 0; q < nq; ++q) {
+      double s = 0.0;
+      for (int a = 0; a < nj; ++a) s += A[a * nq + q] * r[a];
+      W[(size_t)i * np + qlo + q] = s;
+    }
+  }
+  free(sp); free(A); free(G); free(r);
+  return rc;
+}
+
+int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
+                const int32_t* col_idx, double* values) {
+  layout L;
+  if (!row_ptr || !col_idx || !values || make_layout(pt, &L)) { free_layout(&L); return -1; }
+  const int d = L.d, p = L.p;
+  double* x[3] = {NULL, NULL, NULL};
+  double* W[3] = {NULL, NULL, NULL};
+  double* Bv[3] = {NULL, NULL, NULL};
+  int np[3] = {1, 1, 1}, nf[3] = {1, 1, 1};
+  int rc = 0;
+  for (int k = 0; k < d && rc == 0; ++k) {
+    const int m = pt->m[k];
+    nf[k] = m - p - 1;
+    const int cap = 4 * m + 8;
+    x[k] = (double*)malloc(sizeof(double) * (size_t)cap);
+    np[k] = ora_wq_points(pt->t[k], m, p, x[k], cap);
+    if (np[k] < 1) { rc = -1; break; }
+    W[k] = (double*)malloc(sizeof(double) * (size_t)nf[k] * np[k]);
+    Bv[k] = (double*)malloc(sizeof(double) * (size_t)nf[k] * np[k]);
+    if (ora_wq_weights(pt->t[k], m, p, x[k], np[k], W[k])) { rc = -1; break; }
+    for (int j = 0; j < nf[k]; ++j)
+      for (int q = 0; q < np[k]; ++q) Bv[k][(size_t)j * np[k] + q] = wq_bspline(pt->t[k], m, j, p, x[k][q]);
+  }
+  if (rc == 0) {
+    const int64_t nd = (int64_t)nf[0] * nf[1] * nf[2];
+    for (int64_t i = 0; i < nd; ++i) {
+      const int i1 = (int)(i % nf[0]), i2 = (int)((i / nf[0]) % nf[1]), i3 = (int)(i / ((int64_t)nf[0] * nf[1]));
+      for (int64_t z = row_ptr[i]; z < row_ptr[i + 1]; ++z) {
+        const int64_t j = col_idx[z];
+        const int j1 = (int)(j % nf[0]), j2 = (int)((j / nf[0]) % nf[1]), j3 = (int)(j / ((int64_t)nf[0] * nf[1]));
+        double s = 0.0;
+        for (int q3 = 0; q3 < np[2]; ++q3) {
+          const double f3 = (d == 3) ? W[2][(size_t)i3 * np[2] + q3] * Bv[2][(size_t)j3 * np[2] + q3] : 1.0;
+          if (f3 == 0.0) continue;
+          for (int q2 = 0; q2 < np[1]; ++q2) {
+            const double f2 = W[1][(size_t)i2 * np[1] + q2] * Bv[1][(size_t)j2 * np[1] + q2];
+            if (f2 == 0.0) continue;
+            for (int q1 = 0; q1 < np[0]; ++q1) {
+              const double f1 = W[0][(size_t)i1 * np[0] + q1] * Bv[0][(size_t)j1 * np[0] + q1];
+              if (f1 == 0.0) continue;
+              const double cq = c ? c[q1 + (int64_t)np[0] * (q2 + (int64_t)np[1] * q3)] : 1.0;
+              s += f1 * f2 * f3 * cq;
+            }
+          }
+        }
+        values[z] = s;
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) { free(x[k]); free(W[k]); free(Bv[k]); }
+  free_layout(&L);
+  return rc;
+}

@@ -121,6 +121,38 @@ int ora_assemble(const ora_patch* pt, const int64_t* row_ptr, const int32_t* col
 int ora_apply(const ora_patch* pt, const double* kappa, const double* rho, const double* G,
               const double* x, double* yK, double* yM);
 
+/* Weighted quadrature for the mass matrix (named in Sec. 1.2 as a further
+ * reduction of the integration cost; not defined in the paper -- the reading
+ * below is written from the method's defining property).  For each test
+ * function B_i, a rule sum_q w_{i,q} f(x_q) over global points x_q in the
+ * closed support of B_i that integrates B_i f exactly for every spline f of
+ * the space, i.e. sum_q w_{i,q} B_j(x_q) = int B_i B_j for all j; among such
+ * rules the one of least Euclidean norm.
+ * ora_wq_points: the global points of one direction, ascending: each
+ * element's left end and midpoint, plus the right end of the last element; in
+ * the first p and the last p elements instead the left end and p interior
+ * points at fractions r/(p+1), r = 1..p.  Writes at most cap points to x,
+ * returns their number (or -1). */
+int ora_wq_points(const double* t, int m, int p, double* x, int cap);
+
+/* The weights of one direction: W[nf][np] (row i = test function i, zero
+ * outside the closed support), from the point set of ora_wq_points.  The
+ * exact integrals int B_i B_j come from Gauss--Legendre with p+1 points per
+ * element; the least-norm solution is W_i = A^T (A A^T)^{-1} r_i with
+ * A[j][q] = B_j(x_q) restricted to the support, solved by Gaussian elimination
+ * with partial pivoting.  Returns 0, or -1 (bad arguments or a singular
+ * system). */
+int ora_wq_weights(const double* t, int m, int p, const double* x, int np, double* W);
+
+/* Global mass matrix by weighted quadrature, on the CSR pattern of
+ * ora_csr_pattern: values[z] of entry (i, j) = sum over the points x_q of the
+ * tensor grid (q = q1 + n1 (q2 + n2 q3)) of W1[i1][q1] W2[i2][q2] W3[i3][q3]
+ * c[q] B_j1(x_q1) B_j2(x_q2) B_j3(x_q3) (2D: two factors).  c holds the
+ * coefficient (for the mass: rho |det G|) at every grid point, or NULL = 1.
+ * Returns 0, or -1. */
+int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
+                const int32_t* col_idx, double* values);
+
 #ifdef __cplusplus
 }
 #endif

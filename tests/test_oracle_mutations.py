@@ -39,6 +39,16 @@ MUTANTS = {
     # operator application gathers the test function's dof instead of the trial's
     "apply_gather": ("if (Ke) sK += Ke[(size_t)a * N + b] * x[dof[b]];",
                      "if (Ke) sK += Ke[(size_t)a * N + b] * x[dof[a]];", "test_oracle_assembly.py"),
+    # weighted quadrature: the right end of the domain evaluated as 0
+    "wq_right_end": ("  if (x >= t[m - 1]) return (i == m - p - 2) ? 1.0 : 0.0;",
+                     "  if (x >= t[m - 1]) return 0.0;", "test_oracle_wq.py"),
+    # weighted quadrature: Gauss weights without the half-length factor
+    "wq_gram_weight": ("s += 0.5 * (eb - ea) * gw[g] * ora_bspline(t, i, p, xi)",
+                       "s += gw[g] * ora_bspline(t, i, p, xi)", "test_oracle_wq.py"),
+    # weighted quadrature: test and trial weights exchanged in direction 2
+    "wq_transposed": ("const double f2 = W[1][(size_t)i2 * np[1] + q2] * Bv[1][(size_t)j2 * np[1] + q2];",
+                      "const double f2 = W[1][(size_t)j2 * np[1] + q2] * Bv[1][(size_t)i2 * np[1] + q2];",
+                      "test_oracle_wq.py"),
     # sparsity pattern misses the first function of every element
     "pattern_drop": ("for (int b = 0; b < N; ++b)\n        if (mark[dof[b]] != i)",
                      "for (int b = 1; b < N; ++b)\n        if (mark[dof[b]] != i)", "test_oracle_assembly.py"),
