@@ -527,7 +527,57 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
     forms["adjoint_3d_p3_40"] = adj
     forms["apply_3d_p3_40"] = measure_apply(A, ka, stream, flush, dev)
     forms["assembly_3d_p3_32"] = measure_assembly(W, kappa, stream, flush, dev)
+    forms["wq_mass_3d_p3_32"] = measure_wq(W, stream, flush, dev)
     return forms
+
+
+def wq_flops(knots, p, xs):
+    """Algorithmic flops of the weighted-quadrature mass, row by row: for row
+    i with n_k support points and w_k coupled functions per direction,
+    2 (w3 n1 n2 n3 + w2 w3 n1 n2 + w1 w2 w3 n1)."""
+    import numpy as np
+    per_dir = []
+    for t, x in zip(knots, xs):
+        nf = len(t) - p - 1
+        n = np.array([np.count_nonzero((x >= t[i]) & (x <= t[i + p + 1])) for i in range(nf)])
+        lo = np.array([max(0, i - p) for i in range(nf)])
+        hi = np.array([min(nf - 1, i + p) for i in range(nf)])
+        per_dir.append((n.astype(float), (hi - lo + 1).astype(float)))
+    (n1, w1), (n2, w2), (n3, w3) = per_dir
+    N1, N2, N3 = np.meshgrid(n1, n2, n3, indexing="ij")
+    W1, W2, W3 = np.meshgrid(w1, w2, w3, indexing="ij")
+    return float(2 * (W3 * N1 * N2 * N3 + W2 * W3 * N1 * N2 + W1 * W2 * W3 * N1).sum())
+
+
+def measure_wq(W, stream, flush, dev):
+    """Weighted-quadrature mass (FP64, lognormal coefficient on the point grid)
+    on the 32^3 p=3 mesh, next to the Gauss form of the same matrix: element
+    mass matrices by sum factorization plus their CSR assembly."""
+    import torch
+    from paper_2207_00280_gb300 import workloads as wl
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+    sp = W.spec
+    peaks = measured_peaks()[0]
+    pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="sumfact", precision="fp64", mass=True,
+                 stiffness=False, blocking=False)
+    c = torch.as_tensor(wl.lognormal(pl.wq_grid_size(0), 93), device=dev)
+    vals = torch.empty(pl.n_csr_nnz, dtype=torch.float64, device=dev)
+    ms = _time_steps(lambda: pl.wq_mass(c=c, values=vals, stream=stream), 10, stream, flush)
+    fl = wq_flops(sp.knots, sp.p, pl.wq_points(0))
+    peak = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    out = {"rows": pl.n_dofs, "nnz": pl.n_csr_nnz, "ms_per_matrix": round(ms, 4),
+           "rows_per_s": round(pl.n_dofs / (ms * 1e-3), 1), "flop_per_matrix": fl,
+           "fp64_frac": round(fl / (ms * 1e-3) / peak, 4)}
+    # the Gauss route to the same global matrix
+    _, M, _ = pl.empty_outputs(device=dev, dof=False)
+    rho = torch.as_tensor(wl.lognormal(pl.n_qp, 94), device=dev)
+
+    def gauss():
+        pl.integrate(rho=rho, M=M, stream=stream)
+        pl.assemble(M, values=vals, stream=stream)
+    out["gauss_sumfact_plus_assembly_ms"] = round(_time_steps(gauss, 10, stream, flush), 4)
+    pl.close()
+    return out
 
 
 def apply_flops_per_element(p, q):

@@ -215,6 +215,28 @@ int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_s
 int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const double* jac,
               const void* x, double alpha, double beta, void* y, void* cuda_stream);
 
+/* Weighted quadrature for the mass matrix (3D, p <= 5; the variant Sec. 1.2
+ * names as a further reduction of the integration cost, which the paper does
+ * not define).  Each direction has one global point list: every element's
+ * left end and midpoint, p+1 points in the p boundary elements at each end,
+ * and the right end of the domain.  Test function B_i integrates with the
+ * least-norm weights w_{i,q} on the points of its closed support that make
+ * sum_q w_{i,q} B_j(x_q) = int B_i B_j exact for every spline B_j; the global
+ * matrix is formed row by row,
+ *   M_ij = sum_q w1_{i1,q1} w2_{i2,q2} w3_{i3,q3} c(x_q) B_j(x_q),
+ * so no element matrix exists.  With c = 1 it is the exact Gram matrix.
+ * iga_wq_points: number (n_out) and, if x_out != NULL (host, n_out
+ * doubles), the parametric coordinates of the points of direction `dir` of
+ * patch `patch`; dir = -1 gives the patch's grid size (x_out NULL), patch = -1
+ * (with dir = -1) the total over patches.  The first call of either entry
+ * builds the plan's tables (host least-norm solves, device upload).
+ * iga_wq_mass: FP64 plans only.  c: device, the coefficient (rho |det G| for
+ * a mass) at every grid point, patches concatenated, each [n3][n2][n1] with x
+ * fastest; NULL = 1.  values: device [n_csr_nnz] doubles on the pattern of
+ * iga_csr_pattern, overwritten. */
+int iga_wq_points(iga_plan_t plan, int patch, int dir, double* x_out, int64_t* n_out);
+int iga_wq_mass(iga_plan_t plan, const double* c, double* values, void* cuda_stream);
+
 /* With opts.profile = 1: synchronize on the last recorded event and return
  * the summed device time (ms) of the element-matrix kernel launches since the
  * previous call, timed by CUDA events recorded on the caller's stream

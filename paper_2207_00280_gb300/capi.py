@@ -40,7 +40,7 @@ IGA_SCHED_PERSISTENT_GRAPH = 3
 
 # Every exported symbol of include/iga.h (checked by tests/test_capi_symbols.py).
 EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_basis_tables",
-            "iga_csr_pattern", "iga_assemble", "iga_apply",
+            "iga_csr_pattern", "iga_assemble", "iga_apply", "iga_wq_points", "iga_wq_mass",
             "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str")
 
 
@@ -105,6 +105,10 @@ def lib() -> ctypes.CDLL:
             L.iga_assemble.restype = i32
             L.iga_apply.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
             L.iga_apply.restype = i32
+            L.iga_wq_points.argtypes = [vp, i32, i32, vp, ctypes.POINTER(ctypes.c_int64)]
+            L.iga_wq_points.restype = i32
+            L.iga_wq_mass.argtypes = [vp, vp, vp, vp]
+            L.iga_wq_mass.restype = i32
             L.iga_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
             L.iga_profile_read.restype = i32
@@ -157,6 +161,14 @@ def iga_assemble(plan, A_elem, values, stream) -> int:
 
 def iga_apply(plan, kappa, rho, jac, x, alpha, beta, y, stream) -> int:
     return lib().iga_apply(plan, kappa, rho, jac, x, float(alpha), float(beta), y, stream)
+
+
+def iga_wq_points(plan, patch, dir_, x_out, n_out) -> int:
+    return lib().iga_wq_points(plan, int(patch), int(dir_), x_out, n_out)
+
+
+def iga_wq_mass(plan, c, values, stream) -> int:
+    return lib().iga_wq_mass(plan, c, values, stream)
 
 
 def iga_profile_read(plan):

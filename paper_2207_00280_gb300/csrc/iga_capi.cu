@@ -50,6 +50,19 @@ struct iga_plan_s {
   // operator application: per-element results [N][E] per patch, allocated by
   // the first iga_apply call
   void* d_apply_scratch = nullptr;
+  // weighted quadrature: per patch and direction, built by the first call
+  struct WqDir {
+    std::vector<double> x;      // global points
+    int qmax = 0;
+    int* d_qlo = nullptr;
+    int* d_qn = nullptr;
+    double* d_V = nullptr;
+  };
+  std::vector<WqDir> wq;        // [patch * 3 + k]
+  std::vector<int64_t> wq_coef_off;  // [n_patches + 1] prefix of the grid sizes
+  std::vector<double> knots_host;    // all knot vectors, as uploaded
+  std::vector<FnCouple> fc_host;     // all coupling records, as uploaded
+  int wq_status = -1;           // -1 not built, else the build's iga_status
   iga_plan_info info{};
 };
 
@@ -154,6 +167,140 @@ std::vector<FnCouple> couple_1d(const std::vector<int>& spans, int p, int nf) {
   return out;
 }
 
+// Values of the p+1 B-splines non-zero on span s at x (triangular Cox--de Boor
+// of Sec. 2.3, the polynomial piece of span s, so x at the span's right end
+// gives the left limit): N[r] = B_{s-p+r;p}(x).
+void host_basis(const double* t, int p, int s, double x, double* N) {
+  double left[kMaxDegree2D + 1], right[kMaxDegree2D + 1];
+  N[0] = 1.0;
+  for (int d = 1; d <= p; ++d) {
+    left[d] = x - t[s + 1 - d];
+    right[d] = t[s + d] - x;
+    double saved = 0.0;
+    for (int r = 0; r < d; ++r) {
+      const double tmp = N[r] / (right[r + 1] + left[d - r]);
+      N[r] = saved + right[r + 1] * tmp;
+      saved = left[d - r] * tmp;
+    }
+    N[d] = saved;
+  }
+}
+
+// B_{j;p}(x) for x in [t_p, t_end]: the span holding x (the last non-empty span
+// for the right end), then the triangular values.
+double host_bspline(const double* t, const std::vector<int>& spans, int p, int j, double x) {
+  size_t e = std::upper_bound(spans.begin(), spans.end(), 0, [&](int, int s) { return x < t[s]; }) -
+             spans.begin();
+  e = e == 0 ? 0 : e - 1;
+  const int s = spans[e];
+  if (j < s - p || j > s) return 0.0;
+  double N[kMaxDegree2D + 1];
+  host_basis(t, p, s, x, N);
+  return N[j - (s - p)];
+}
+
+// One direction of the weighted quadrature of the mass matrix: the global
+// points (each element's left end and midpoint, p+1 points in the p boundary
+// elements at each end, the right end), and for each test function i the
+// least-norm weights on the points of its closed support that integrate
+// B_i B_j exactly for every coupled j (G y = r with G = A A^T by Cholesky,
+// w = A^T y; A[j][q] = B_j(x_q), r_j = int B_i B_j by Gauss--Legendre with
+// p+1 points per element).  Output: V[(i W + jj) qmax + qq] = w_q B_j(x_q).
+int wq_build_direction(const double* t, int p, const std::vector<int>& spans,
+                       const std::vector<FnCouple>& fc, std::vector<double>* x_out,
+                       std::vector<int>* qlo_out, std::vector<int>* qn_out,
+                       std::vector<double>* V_out, int* qmax_out) {
+  const int K = (int)spans.size(), nf = (int)fc.size(), W = 2 * p + 1;
+  std::vector<double>& x = *x_out;
+  x.clear();
+  for (int e = 0; e < K; ++e) {
+    const double a = t[spans[e]], b = t[spans[e] + 1];
+    x.push_back(a);
+    if (e < p || e >= K - p) {
+      for (int r = 1; r <= p; ++r) x.push_back(a + (b - a) * r / (double)(p + 1));
+    } else {
+      x.push_back(0.5 * (a + b));
+    }
+  }
+  x.push_back(t[spans[K - 1] + 1]);
+  std::vector<double> gx(p + 1), gw(p + 1);
+  gauss_legendre_newton(p + 1, gx.data(), gw.data());
+  std::vector<int>& qlo = *qlo_out;
+  std::vector<int>& qn = *qn_out;
+  qlo.assign(nf, 0);
+  qn.assign(nf, 0);
+  int qmax = 0;
+  for (int i = 0; i < nf; ++i) {
+    const double lo = t[i], hi = t[i + p + 1];
+    const int a = (int)(std::lower_bound(x.begin(), x.end(), lo) - x.begin());
+    const int b = (int)(std::upper_bound(x.begin(), x.end(), hi) - x.begin());
+    qlo[i] = a;
+    qn[i] = b - a;
+    qmax = std::max(qmax, b - a);
+  }
+  std::vector<double>& V = *V_out;
+  V.assign((size_t)nf * W * qmax, 0.0);
+  for (int i = 0; i < nf; ++i) {
+    const int nj = fc[i].fhi - fc[i].flo + 1, nq = qn[i];
+    if (nj > W || nq < nj) return IGA_ERR_UNSUPPORTED;
+    std::vector<double> A((size_t)nj * nq), r(nj, 0.0), G((size_t)nj * nj, 0.0);
+    for (int jj = 0; jj < nj; ++jj)
+      for (int qq = 0; qq < nq; ++qq)
+        A[(size_t)jj * nq + qq] = host_bspline(t, spans, p, fc[i].flo + jj, x[qlo[i] + qq]);
+    for (int e = fc[i].elo; e <= fc[i].ehi; ++e) {
+      const int s = spans[e];
+      const double ea = t[s], eb = t[s + 1];
+      double N[kMaxDegree2D + 1];
+      for (int g = 0; g <= p; ++g) {
+        const double xi = 0.5 * (ea + eb) + 0.5 * (eb - ea) * gx[g];
+        host_basis(t, p, s, xi, N);
+        const double bi = N[i - (s - p)], wg = 0.5 * (eb - ea) * gw[g];
+        for (int jj = 0; jj < nj; ++jj) {
+          const int j = fc[i].flo + jj;
+          if (j >= s - p && j <= s) r[jj] += wg * bi * N[j - (s - p)];
+        }
+      }
+    }
+    for (int u = 0; u < nj; ++u)
+      for (int v = 0; v <= u; ++v) {
+        double acc = 0.0;
+        for (int qq = 0; qq < nq; ++qq) acc += A[(size_t)u * nq + qq] * A[(size_t)v * nq + qq];
+        G[(size_t)u * nj + v] = acc;
+      }
+    // Cholesky G = L L^T (lower triangle in place), then L L^T y = r
+    for (int u = 0; u < nj; ++u) {
+      for (int v = 0; v <= u; ++v) {
+        double acc = G[(size_t)u * nj + v];
+        for (int k = 0; k < v; ++k) acc -= G[(size_t)u * nj + k] * G[(size_t)v * nj + k];
+        if (u == v) {
+          if (!(acc > 0.0)) return IGA_ERR_UNSUPPORTED;
+          G[(size_t)u * nj + u] = std::sqrt(acc);
+        } else {
+          G[(size_t)u * nj + v] = acc / G[(size_t)v * nj + v];
+        }
+      }
+    }
+    for (int u = 0; u < nj; ++u) {
+      double acc = r[u];
+      for (int k = 0; k < u; ++k) acc -= G[(size_t)u * nj + k] * r[k];
+      r[u] = acc / G[(size_t)u * nj + u];
+    }
+    for (int u = nj - 1; u >= 0; --u) {
+      double acc = r[u];
+      for (int k = u + 1; k < nj; ++k) acc -= G[(size_t)k * nj + u] * r[k];
+      r[u] = acc / G[(size_t)u * nj + u];
+    }
+    for (int qq = 0; qq < nq; ++qq) {
+      double w = 0.0;
+      for (int jj = 0; jj < nj; ++jj) w += A[(size_t)jj * nq + qq] * r[jj];
+      for (int jj = 0; jj < nj; ++jj)
+        V[((size_t)i * W + jj) * qmax + qq] = w * A[(size_t)jj * nq + qq];
+    }
+  }
+  *qmax_out = qmax;
+  return IGA_OK;
+}
+
 bool method_supported(const iga_plan_opts& o, int dim, int p, int q) {
   if (o.precision == IGA_FP64) {
     if (o.method == IGA_SUMFACT) return sumfact_f64_supported(dim, p, q);
@@ -191,6 +338,11 @@ void free_plan_memory(iga_plan_s* P) {
   cudaFree(P->d_partial);
   cudaFree(P->d_fc);
   cudaFree(P->d_apply_scratch);
+  for (auto& w : P->wq) {
+    cudaFree(w.d_qlo);
+    cudaFree(w.d_qn);
+    cudaFree(w.d_V);
+  }
 }
 
 int map_cuda(cudaError_t e) {
@@ -349,6 +501,8 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   if (ce == cudaSuccess) ce = upload(&P->d_gauss, gauss_all.data(), gauss_all.size());
   if (ce == cudaSuccess) ce = upload(&P->d_jobs, jobs.data(), jobs.size());
   if (ce == cudaSuccess) ce = upload(&P->d_fc, fc_all.data(), fc_all.size());
+  P->knots_host = knots_all;
+  P->fc_host = fc_all;
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_tables, sizeof(double) * (size_t)tab_off);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&P->d_err, sizeof(int));
   if (ce == cudaSuccess) ce = cudaMemset(P->d_err, 0, sizeof(int));
@@ -641,6 +795,95 @@ extern "C" int iga_apply(iga_plan_t P, const double* kappa, const double* rho, c
     e = launch_apply(a, pd.p, pd.q, fp64, st);
     if (e == cudaSuccess)
       e = launch_apply_gather(P->csr[ip], P->d_fc, P->d_spans, a.scratch, y, fp64, st);
+  }
+  return finish(P, st, e);
+}
+
+namespace {
+// Build the weighted-quadrature tables of every patch (host) and upload them.
+int wq_ensure(iga_plan_s* P) {
+  if (P->wq_status >= 0) return P->wq_status;
+  int rc = IGA_OK;
+  P->wq.assign((size_t)P->n_patches * 3, iga_plan_s::WqDir{});
+  P->wq_coef_off.assign(1, 0);
+  for (int ip = 0; ip < P->n_patches && rc == IGA_OK; ++ip) {
+    const PatchDev& pd = P->ph[ip];
+    if (pd.dim != 3 || pd.p > 5) { rc = IGA_ERR_UNSUPPORTED; break; }
+    int64_t grid = 1;
+    for (int k = 0; k < 3 && rc == IGA_OK; ++k) {
+      iga_plan_s::WqDir& w = P->wq[(size_t)ip * 3 + k];
+      const CsrPatch& c = P->csr[ip];
+      // the coupling records of this direction (the planner's host copy)
+      std::vector<FnCouple> all(P->fc_host.begin() + c.fn_offset[k],
+                                P->fc_host.begin() + c.fn_offset[k] + pd.nf[k]);
+      std::vector<int> qlo, qn;
+      std::vector<double> V;
+      const double* t = P->knots_host.data() + pd.knot_offset[k];
+      rc = wq_build_direction(t, pd.p, P->spans_h[(size_t)ip * P->dim + k], all, &w.x, &qlo, &qn, &V,
+                              &w.qmax);
+      if (rc != IGA_OK) break;
+      cudaError_t e = upload(&w.d_qlo, qlo.data(), qlo.size());
+      if (e == cudaSuccess) e = upload(&w.d_qn, qn.data(), qn.size());
+      if (e == cudaSuccess) e = upload(&w.d_V, V.data(), V.size());
+      if (e != cudaSuccess) { cudaGetLastError(); rc = map_cuda(e); }
+      grid *= (int64_t)w.x.size();
+    }
+    P->wq_coef_off.push_back(P->wq_coef_off.back() + grid);
+  }
+  P->wq_status = rc;
+  return rc;
+}
+}  // namespace
+
+extern "C" int iga_wq_points(iga_plan_t P, int patch, int dir, double* x_out, int64_t* n_out) {
+  if (!P || !n_out || patch < -1 || patch >= P->n_patches || dir < -1 || dir > 2) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  const int rc = wq_ensure(P);
+  if (rc != IGA_OK) return rc;
+  if (patch == -1) {
+    if (dir != -1 || x_out) return IGA_ERR_ARG;
+    *n_out = P->wq_coef_off.back();
+    return IGA_OK;
+  }
+  if (dir == -1) {
+    if (x_out) return IGA_ERR_ARG;
+    *n_out = P->wq_coef_off[patch + 1] - P->wq_coef_off[patch];
+    return IGA_OK;
+  }
+  const std::vector<double>& x = P->wq[(size_t)patch * 3 + dir].x;
+  *n_out = (int64_t)x.size();
+  if (x_out) std::memcpy(x_out, x.data(), sizeof(double) * x.size());
+  return IGA_OK;
+}
+
+extern "C" int iga_wq_mass(iga_plan_t P, const double* c, double* values, void* cuda_stream) {
+  NvtxRange range("iga_wq_mass");
+  if (!P || !values) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  if (P->opts.precision != IGA_FP64 && P->opts.precision != IGA_FP64_DF) return IGA_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  const int rc = wq_ensure(P);
+  if (rc != IGA_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSuccess;
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip) {
+    WqPatchArgs a{};
+    a.c = P->csr[ip];
+    a.fc = P->d_fc;
+    for (int k = 0; k < 3; ++k) {
+      const iga_plan_s::WqDir& w = P->wq[(size_t)ip * 3 + k];
+      a.d[k].qlo = w.d_qlo;
+      a.d[k].qn = w.d_qn;
+      a.d[k].V = w.d_V;
+      a.d[k].np = (int)w.x.size();
+      a.d[k].qmax = w.qmax;
+    }
+    a.coef = c ? c + P->wq_coef_off[ip] : nullptr;
+    a.values = values;
+    e = launch_wq_mass(a, P->ph[ip].p, st);
   }
   return finish(P, st, e);
 }

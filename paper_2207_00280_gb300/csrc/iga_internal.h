@@ -185,4 +185,25 @@ cudaError_t launch_apply_gather(const CsrPatch& c, const FnCouple* fc, const int
                                 const void* scratch, void* y, bool fp64, cudaStream_t st);
 bool apply_supported(int dim, int p, int q);
 
+// ---- weighted quadrature (mass matrix, 3D, FP64) -------------------------------
+// One direction of one patch: the rule of test function i covers the points
+// qlo[i] .. qlo[i] + qn[i] - 1 of the direction's global point list, and
+// V[(i * W + jj) * QMAX + qq] = w_{i, qlo + qq} B_{flo(i) + jj}(x_{qlo + qq})
+// (W = 2p + 1 columns, zero-padded).
+struct WqDirDev {
+  const int* qlo;
+  const int* qn;
+  const double* V;
+  int np;      // points of the direction
+  int qmax;    // padding of the point index in V
+};
+struct WqPatchArgs {
+  CsrPatch c;            // rows, coupling ranges, CSR offsets
+  const FnCouple* fc;
+  WqDirDev d[3];
+  const double* coef;    // patch block of the coefficient grid [np3][np2][np1], or null = 1
+  double* values;        // global CSR values
+};
+cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, cudaStream_t st);
+
 }  // namespace iga

@@ -200,6 +200,102 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Global mass matrix by weighted quadrature (3D, FP64): one CTA per row i.
+// With V_k the per-direction tables of test function i_k (rule weights times
+// trial values at the rule's points) and c the coefficient on the points of
+// the support box, the row is contracted one direction at a time (the sum
+// factorization of Sec. 3.2 applied to the rule of the row):
+//   T1[j3][q1][q2] = sum_q3 V3[j3][q3] c[q1, q2, q3]
+//   T2[j2][j3][q1] = sum_q2 V2[j2][q2] T1[j3][q1][q2]
+//   M[j1][j2][j3]  = sum_q1 V1[j1][q1] T2[j2][j3][q1]
+// and written to the row's CSR entries (j3, j2, j1 ascending).
+template <int P>
+__global__ void __launch_bounds__(128) k_wq_mass(const WqPatchArgs A) {
+  constexpr int W = 2 * P + 1, NT = 128;
+  extern __shared__ double wsm[];
+  const CsrPatch& c = A.c;
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  for (int64_t row = blockIdx.x; row < n_rows; row += gridDim.x) {
+    int ii[3];
+    const RowGeom g = row_geom(c, A.fc, row, ii);
+    int qlo[3], qn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      qlo[k] = A.d[k].qlo[ii[k]];
+      qn[k] = A.d[k].qn[ii[k]];
+    }
+    const int n1 = qn[0], n2 = qn[1], n3 = qn[2];
+    const int w1 = g.w[0], w2 = g.w[1], w3 = g.w[2];
+    double* V1 = wsm;                    // [w1][n1]
+    double* V2 = V1 + W * n1;            // [w2][n2]
+    double* V3 = V2 + W * n2;            // [w3][n3]
+    double* T1 = V3 + W * n3;            // [w3][n1][n2]
+    double* T2 = T1 + (size_t)W * n1 * n2;   // [w2][w3][n1]
+    __syncthreads();                     // the previous row's buffers are no longer read
+    for (int k = 0; k < 3; ++k) {
+      const int wk = g.w[k], nk = qn[k];
+      const double* src = A.d[k].V + (size_t)ii[k] * W * A.d[k].qmax;
+      double* dst = k == 0 ? V1 : (k == 1 ? V2 : V3);
+      for (int t = threadIdx.x; t < wk * nk; t += NT) dst[t] = src[(t / nk) * A.d[k].qmax + t % nk];
+    }
+    __syncthreads();
+    // q3: one coefficient load per point, all w3 sums of the point in registers
+    const int64_t np1 = A.d[0].np, np2 = A.d[1].np;
+    for (int it = threadIdx.x; it < n1 * n2; it += NT) {
+      const int q1 = it % n1, q2 = it / n1;
+      double acc[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int q3 = 0; q3 < n3; ++q3) {
+        const double cq = A.coef ? A.coef[(qlo[0] + q1) + np1 * ((qlo[1] + q2) + np2 * (qlo[2] + q3))] : 1.0;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w3) acc[j] = fma(V3[j * n3 + q3], cq, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j < w3) T1[((size_t)j * n1 + q1) * n2 + q2] = acc[j];
+    }
+    __syncthreads();
+    // q2
+    for (int it = threadIdx.x; it < n1 * w3; it += NT) {
+      const int q1 = it % n1, j3 = it / n1;
+      const double* t1 = T1 + ((size_t)j3 * n1 + q1) * n2;
+      double acc[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int q2 = 0; q2 < n2; ++q2) {
+        const double tv = t1[q2];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w2) acc[j] = fma(V2[j * n2 + q2], tv, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j < w2) T2[((size_t)j * w3 + j3) * n1 + q1] = acc[j];
+    }
+    __syncthreads();
+    // q1, then the row's entries
+    for (int it = threadIdx.x; it < w2 * w3; it += NT) {
+      const int j2 = it % w2, j3 = it / w2;
+      const double* t2 = T2 + ((size_t)j2 * w3 + j3) * n1;
+      double acc[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int q1 = 0; q1 < n1; ++q1) {
+        const double tv = t2[q1];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w1) acc[j] = fma(V1[j * n1 + q1], tv, acc[j]);
+      }
+      double* out = A.values + g.start + ((int64_t)j3 * w2 + j2) * w1;
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j < w1) out[j] = acc[j];
+    }
+  }
+}
+
 template <typename T, int P, int DIM>
 cudaError_t run_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans, const void* A,
                          void* values, cudaStream_t st) {
@@ -267,7 +363,34 @@ cudaError_t dispatch_gather(const CsrPatch& c, const FnCouple* fc, const int* sp
   }
 }
 
+template <int P>
+cudaError_t run_wq(const WqPatchArgs& a, cudaStream_t st) {
+  constexpr int W = 2 * P + 1;
+  const int64_t n_rows = (int64_t)a.c.nf[0] * a.c.nf[1] * a.c.nf[2];
+  if (n_rows == 0) return cudaSuccess;
+  const size_t q1 = a.d[0].qmax, q2 = a.d[1].qmax, q3 = a.d[2].qmax;
+  const size_t smem = sizeof(double) * (W * (q1 + q2 + q3) + W * q1 * q2 + (size_t)W * W * q1);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto k = k_wq_mass<P>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = n_rows < 152 * 64 ? n_rows : 152 * 64;
+  k<<<(unsigned)blocks, 128, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, cudaStream_t st) {
+  switch (p) {
+    case 1: return run_wq<1>(a, st);
+    case 2: return run_wq<2>(a, st);
+    case 3: return run_wq<3>(a, st);
+    case 4: return run_wq<4>(a, st);
+    case 5: return run_wq<5>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_csr_pattern(const CsrPatch& c, const FnCouple* fc, int64_t* row_ptr,
                                int32_t* col_idx, cudaStream_t st) {

@@ -151,6 +151,38 @@ class IgaPlan:
             raise capi.IgaError(rc, "iga_apply")
         return y
 
+    def wq_points(self, patch: int = 0):
+        """Parametric coordinates of the weighted-quadrature points, one array per direction."""
+        out = []
+        for d in range(self.patches[patch].dim):
+            n = ctypes.c_int64()
+            rc = capi.iga_wq_points(self.handle, patch, d, None, ctypes.byref(n))
+            if rc != capi.IGA_OK:
+                raise capi.IgaError(rc, "iga_wq_points")
+            x = np.zeros(n.value)
+            rc = capi.iga_wq_points(self.handle, patch, d, x.ctypes.data_as(ctypes.c_void_p),
+                                    ctypes.byref(n))
+            if rc != capi.IGA_OK:
+                raise capi.IgaError(rc, "iga_wq_points")
+            out.append(x)
+        return out
+
+    def wq_grid_size(self, patch: int = -1) -> int:
+        n = ctypes.c_int64()
+        rc = capi.iga_wq_points(self.handle, patch, -1, None, ctypes.byref(n))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_wq_points")
+        return n.value
+
+    def wq_mass(self, c=None, values=None, stream=None):
+        """CSR values of the weighted-quadrature mass matrix (c on the point grid or None = 1)."""
+        if values is None:
+            values = torch.empty(self.n_csr_nnz, dtype=torch.float64, device="cuda")
+        rc = capi.iga_wq_mass(self.handle, _ptr(c), _ptr(values), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_wq_mass")
+        return values
+
     def profile_read(self):
         """(ms, launches) of the element-matrix kernels since the last read."""
         return capi.iga_profile_read(self.handle)

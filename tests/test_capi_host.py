@@ -97,6 +97,9 @@ def test_argument_errors(capi):
     assert L.iga_csr_pattern(None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_assemble(None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_apply(None, None, None, None, None, 1.0, 0.0, None, None) == capi.IGA_ERR_ARG
+    n = ctypes.c_int64()
+    assert L.iga_wq_points(None, 0, 0, None, ctypes.byref(n)) == capi.IGA_ERR_ARG
+    assert L.iga_wq_mass(None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_destroy(None) == capi.IGA_OK
 
 
