@@ -3,70 +3,77 @@
 
 namespace iga {
 
-// One thread per (patch, direction, element) record and Gauss point j.  At
-// the point the p+1 non-zero B-splines B_{s-p+r;p}(xi), r = 0..p, are built by
-// the triangular form of the Cox--de Boor recursion (Sec. 2.3, eq. cox2: each
+// One 32-thread block per (patch, direction, element) record.  At each Gauss
+// point the p+1 non-zero B-splines B_{s-p+r;p}(xi), r = 0..p, are built by the
+// triangular form of the Cox--de Boor recursion (Sec. 2.3, eq. cox2: each
 // degree combines two neighbours of the previous degree, the degree-0 start
 // being the indicator of span s, eq. cox1).  Only the non-vanishing functions
 // are carried, so no 0/0 term ever arises.  The derivative uses the degree
 // p-1 row:
 //   B'_{i;p} = p B_{i;p-1}/(t_{i+p}-t_i) - p B_{i+1;p-1}/(t_{i+p+1}-t_{i+1}).
 // The record also stores the Gauss weight scaled by half the span length.
-// The FP64 pipe of GB300 retires about two lanes per SM per clock, so each
-// thread's serial chain is kept short (one point) and the threads are spread
-// over many SMs (small blocks).
-__global__ void k_basis_tables(const TableJob* __restrict__ jobs, int n_jobs,
-                               const double* __restrict__ knots,
-                               const double* __restrict__ gauss, double* __restrict__ tables) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = g / kMaxGauss, j = g % kMaxGauss;
-  if (r >= n_jobs) return;
-  const TableJob J = jobs[r];
-  if (j >= J.q) return;
+// Every division of the recursion (and of the derivative) is by a knot
+// difference t_{s+k+1} - t_{s+1-d+k} (degree d, 0 <= k < d) that depends on
+// the span only and is at least the span length: the block first forms these
+// reciprocals, one per thread, then each thread evaluates one Gauss point with
+// multiplications only.  GB300's FP64 pipe retires about two lanes per SM per
+// clock, so the serial chain of a thread is what bounds this kernel.
+__global__ void __launch_bounds__(32)
+    k_basis_tables(const TableJob* __restrict__ jobs, const double* __restrict__ knots,
+                   const double* __restrict__ gauss, double* __restrict__ tables) {
+  __shared__ double rden[kMaxDegree2D * (kMaxDegree2D + 1) / 2];   // [d(d-1)/2 + k]
+  const TableJob J = jobs[blockIdx.x];
   const double* t = knots + J.knot_off;
   const int p = J.p, q = J.q, n = p + 1, s = J.span;
+  for (int i = threadIdx.x; i < p * (p + 1) / 2; i += 32) {
+    int d = 1, k = i;
+    while (k >= d) { k -= d; ++d; }
+    rden[i] = 1.0 / (t[s + k + 1] - t[s + 1 - d + k]);
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= q) return;
   const double a = t[s], b = t[s + 1];
   const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
   double* out = tables + J.out_off;
-  {
-    const double xi = mid + half * gauss[J.gauss_off + j];
-    double N[kMaxDegree2D + 1], Nm1[kMaxDegree2D + 1];
-    double left[kMaxDegree2D + 1], right[kMaxDegree2D + 1];
-    N[0] = 1.0;
-    Nm1[0] = 1.0;
-    for (int d = 1; d <= p; ++d) {
-      if (d == p) {
-        for (int k = 0; k < d; ++k) Nm1[k] = N[k];
-      }
-      left[d] = xi - t[s + 1 - d];
-      right[d] = t[s + d] - xi;
-      double saved = 0.0;
-      for (int k = 0; k < d; ++k) {
-        const double tmp = N[k] / (right[k + 1] + left[d - k]);
-        N[k] = saved + right[k + 1] * tmp;
-        saved = left[d - k] * tmp;
-      }
-      N[d] = saved;
+  const double xi = mid + half * gauss[J.gauss_off + j];
+  double N[kMaxDegree2D + 1], Nm1[kMaxDegree2D + 1];
+  double left[kMaxDegree2D + 1], right[kMaxDegree2D + 1];
+  N[0] = 1.0;
+  Nm1[0] = 1.0;
+  for (int d = 1; d <= p; ++d) {
+    if (d == p) {
+      for (int k = 0; k < d; ++k) Nm1[k] = N[k];
     }
-    for (int rr = 0; rr < n; ++rr) {
-      double dv = 0.0;
-      // B_{s-p+rr; p-1} is Nm1[rr-1] (rr >= 1), B_{s-p+rr+1; p-1} is Nm1[rr] (rr <= p-1)
-      if (rr >= 1) dv += Nm1[rr - 1] / (t[s + rr] - t[s - p + rr]);
-      if (rr <= p - 1) dv -= Nm1[rr] / (t[s + rr + 1] - t[s - p + rr + 1]);
-      out[j * n + rr] = N[rr];
-      out[q * n + j * n + rr] = p * dv;
+    left[d] = xi - t[s + 1 - d];
+    right[d] = t[s + d] - xi;
+    const double* rd = rden + d * (d - 1) / 2;
+    double saved = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double tmp = N[k] * rd[k];
+      N[k] = saved + right[k + 1] * tmp;
+      saved = left[d - k] * tmp;
     }
-    out[2 * q * n + j] = half * gauss[J.gauss_off + q + j];
+    N[d] = saved;
   }
+  // derivative denominators are the degree-p differences: t_{s+rr} - t_{s-p+rr}
+  // is entry k = rr - 1 and t_{s+rr+1} - t_{s-p+rr+1} entry k = rr of degree p
+  const double* rp = rden + p * (p - 1) / 2;
+  for (int rr = 0; rr < n; ++rr) {
+    double dv = 0.0;
+    // B_{s-p+rr; p-1} is Nm1[rr-1] (rr >= 1), B_{s-p+rr+1; p-1} is Nm1[rr] (rr <= p-1)
+    if (rr >= 1) dv += Nm1[rr - 1] * rp[rr - 1];
+    if (rr <= p - 1) dv -= Nm1[rr] * rp[rr];
+    out[j * n + rr] = N[rr];
+    out[q * n + j * n + rr] = p * dv;
+  }
+  out[2 * q * n + j] = half * gauss[J.gauss_off + q + j];
 }
 
 cudaError_t launch_basis_tables(const TableJob* jobs, int n_jobs, const double* knots,
                                 const double* gauss, double* tables, cudaStream_t st) {
   if (n_jobs <= 0) return cudaSuccess;
-  const int bs = 32;
-  const int64_t threads = (int64_t)n_jobs * kMaxGauss;
-  k_basis_tables<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(jobs, n_jobs, knots, gauss,
-                                                                     tables);
+  k_basis_tables<<<(unsigned)n_jobs, 32, 0, st>>>(jobs, knots, gauss, tables);
   return cudaGetLastError();
 }
 

@@ -174,5 +174,8 @@ WORKLOADS = {
     # reduced sizes of the same workloads, for profiler captures (inputs + outputs > L2)
     "3d_p3_16": Workload("3d_p3_16", PatchSpec(3, 3, 16, 4), SEED_KAPPA_P3),
     "3d_p3_20": Workload("3d_p3_20", PatchSpec(3, 3, 20, 4), SEED_KAPPA_P3),
+    # the largest degree class of the 64-patch batch, alone
+    "3d_p5_16": Workload("3d_p5_16", PatchSpec(3, 5, 16, 6), SEED_BATCH_KAPPA),
+    "3d_p4_16": Workload("3d_p4_16", PatchSpec(3, 4, 16, 5), SEED_BATCH_KAPPA),
     "3d_p4_24_curved": Workload("3d_p4_24_curved", PatchSpec(3, 4, 24, 5), SEED_KAPPA_P4, curved=True),
 }
