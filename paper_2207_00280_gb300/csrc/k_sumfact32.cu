@@ -97,9 +97,19 @@ struct SF3F {
   static constexpr size_t f_A4 = al4(f_A), f_B4 = al4(f_B);
   static constexpr size_t f_fixed = f_px + f_py + f_pz + f_A4 + f_B4;
   static constexpr size_t f_pairs = al4((size_t)NSp);
-  static constexpr bool STAGE =
-      4 * (f_fixed + (f_alias > f_out ? f_alias : f_out) + f_pairs) <= 200 * 1024;
-  static constexpr size_t f_region_mma = al4((STAGE && f_out > f_alias) ? f_out : f_alias);
+  // the staged element matrix: whole, or in NSPLIT blocks of RB rows when the
+  // whole one does not fit beside the operands (the stage-3 GEMM then runs
+  // once per block and keeps the entries of the block's rows)
+  static constexpr int rows_of(int s) { return (N + s - 1) / s; }
+  static constexpr size_t f_outb_of(int s) { return al4((size_t)rows_of(s) * N + 4); }
+  static constexpr bool fits(int s) {
+    return 4 * (f_fixed + (f_alias > f_outb_of(s) ? f_alias : f_outb_of(s)) + f_pairs) <= 216 * 1024;
+  }
+  static constexpr int NSPLIT = fits(1) ? 1 : fits(2) ? 2 : fits(3) ? 3 : fits(4) ? 4 : 0;
+  static constexpr bool STAGE = NSPLIT > 0;
+  static constexpr int RB = STAGE ? rows_of(NSPLIT) : N;
+  static constexpr size_t f_outb = f_outb_of(STAGE ? NSPLIT : 1);
+  static constexpr size_t f_region_mma = al4((STAGE && f_outb > f_alias) ? f_outb : f_alias);
   static constexpr size_t smem_mma = 4 * (f_fixed + f_region_mma + f_pairs);
   // ---- stage 3 on tcgen05: p <= 3, and p = 4 in BF16 ----
   // (FP32 at p = 4 needs hi and lo operands of 74 KB: two CTAs per SM, where
@@ -234,9 +244,11 @@ __device__ __forceinline__ int upper_index(int ap, int bp) {
 // words).  Warp w takes the 16-row tiles w, w+8, ...; fragments follow the
 // m16n8k8 (TF32) / m16n8k16 (BF16) register layouts: row g = lane/4, column
 // pair 2*(lane%4).
+// Only the entries whose row lies in [r0, r1) are written, at (row - r0) N + col
+// of dst (the staged row block, or the element matrix itself when r0 = 0).
 template <class C, int LDA_, int LDB_, int KS>
 __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, const int* pairs,
-                                         float* dst_stage, float* dst_global) {
+                                         float* dst_stage, float* dst_global, int r0, int r1) {
   constexpr int n = C::n, N = C::N, NSp = C::NSp, NTN = C::NPAD / 8, MT = C::MPs / 16;
   constexpr bool BF = C::KSTEP == 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -262,7 +274,7 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
     }
   // column offsets of this lane's two columns in every N tile: direct (a1 N + b1)
   // and mirrored (b1 N + a1); -1 marks padding columns
-  int cd[NTN][2], cm[NTN][2];
+  int cd[NTN][2], cm[NTN][2], ca[NTN][2], cb[NTN][2];
 #pragma unroll
   for (int nt = 0; nt < NTN; ++nt)
 #pragma unroll
@@ -271,8 +283,11 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
       const int a1 = nn / n, b1 = nn % n;
       cd[nt][h] = nn < n * n ? a1 * N + b1 : -1;
       cm[nt][h] = b1 * N + a1;
+      ca[nt][h] = a1;   // row offset of the direct entry
+      cb[nt][h] = b1;   // row offset of the mirrored entry
     }
   float* dst = C::STAGE ? dst_stage : dst_global;
+  const int off0 = r0 * N;
   for (int mt = warp; mt < MT; mt += C::NT / 32) {
     uint32_t ah[KS][4], al[KS][4];
 #pragma unroll
@@ -297,8 +312,9 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
         }
       }
     }
-    // row bases of this lane's two rows: direct n (a' N + b'), mirrored n (b' N + a')
-    int rd[2], rm[2];
+    // row bases of this lane's two rows: direct n (a' N + b'), mirrored n (b' N + a');
+    // the entry rows are n a' + a1 (direct) and n b' + b1 (mirrored)
+    int rd[2], rm[2], ra[2], rb[2];
     bool rv[2], off[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -308,6 +324,8 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
       const int ap = pr >> 16, bp = pr & 0xffff;
       rd[h] = n * (ap * N + bp);
       rm[h] = n * (bp * N + ap);
+      ra[h] = n * ap;
+      rb[h] = n * bp;
       off[h] = ap != bp;
     }
     float c[NTN][4];
@@ -336,8 +354,14 @@ __device__ __forceinline__ void gemm_sym(const float* Am, const uint32_t* Bm, co
       for (int h = 0; h < 4; ++h) {
         const int r = h >> 1, cc = h & 1;
         if (rv[r] && cd[nt][cc] >= 0) {
-          dst[rd[r] + cd[nt][cc]] = c[nt][h];
-          if (off[r]) dst[rm[r] + cm[nt][cc]] = c[nt][h];
+          if constexpr (C::NSPLIT > 1) {
+            const int rowd = ra[r] + ca[nt][cc], rowm = rb[r] + cb[nt][cc];
+            if (rowd >= r0 && rowd < r1) dst[rd[r] + cd[nt][cc] - off0] = c[nt][h];
+            if (off[r] && rowm >= r0 && rowm < r1) dst[rm[r] + cm[nt][cc] - off0] = c[nt][h];
+          } else {
+            dst[rd[r] + cd[nt][cc]] = c[nt][h];
+            if (off[r]) dst[rm[r] + cm[nt][cc]] = c[nt][h];
+          }
         }
       }
     }
@@ -364,6 +388,19 @@ __device__ __forceinline__ void copy_out(const float* __restrict__ s, float* __r
   const float4* s4 = (const float4*)(s + h);
   for (int i = threadIdx.x; i < nv; i += NT) g4[i] = s4[i];
   for (int i = h + 4 * nv + threadIdx.x; i < NN; i += NT) g[i] = s[i];
+}
+
+// copy_out with a run-time count (a row block of the staged matrix).
+template <int NT>
+__device__ __forceinline__ void copy_out_n(const float* __restrict__ s, float* __restrict__ g, int nn) {
+  const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
+  const int h = head < nn ? head : nn;
+  for (int i = threadIdx.x; i < h; i += NT) g[i] = s[i];
+  const int nv = (nn - h) / 4;
+  float4* g4 = (float4*)(g + h);
+  const float4* s4 = (const float4*)(s + h);
+  for (int i = threadIdx.x; i < nv; i += NT) g4[i] = s4[i];
+  for (int i = h + 4 * nv + threadIdx.x; i < nn; i += NT) g[i] = s[i];
 }
 
 // Once per CTA, before its first element: the table of symmetric pairs
@@ -978,13 +1015,18 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
     float* dst = (float*)(isK ? A.K_out : A.M_out);
     if (!dst) continue;
     float* g = dst + e * (int64_t)N * N;
-    float* stage = outs + stage_offset(g);
-    if (isK) gemm_sym<C, C::LDA, C::LDB, C::KA / C::KSTEP>(AK, BK, pairs, stage, g);
-    else gemm_sym<C, C::LDAM, C::LDBM, C::KAM / C::KSTEP>(AM, BM, pairs, stage, g);
-    if (C::STAGE) {
-      __syncthreads();
-      copy_out<N * N, NT>(stage, g);
-      __syncthreads();
+#pragma unroll 1
+    for (int blk = 0; blk < (C::STAGE ? C::NSPLIT : 1); ++blk) {
+      const int r0 = blk * C::RB, r1 = (r0 + C::RB < N) ? r0 + C::RB : N;
+      float* gb = g + (int64_t)r0 * N;
+      float* stage = outs + stage_offset(gb);
+      if (isK) gemm_sym<C, C::LDA, C::LDB, C::KA / C::KSTEP>(AK, BK, pairs, stage, g, r0, r1);
+      else gemm_sym<C, C::LDAM, C::LDBM, C::KAM / C::KSTEP>(AM, BM, pairs, stage, g, r0, r1);
+      if (C::STAGE) {
+        __syncthreads();
+        copy_out_n<NT>(stage, gb, (r1 - r0) * N);
+        __syncthreads();
+      }
     }
   }
   return true;
