@@ -88,6 +88,8 @@ def lib():
             L.ora_wq_weights.restype = ctypes.c_int
             L.ora_wq_mass.argtypes = [pp, dp, dp, dp, dp]
             L.ora_wq_mass.restype = ctypes.c_int
+            L.ora_integrate_grad.argtypes = [pp, dp, ctypes.c_int64, dp, dp, dp, dp, dp]
+            L.ora_integrate_grad.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -289,3 +291,18 @@ class Patch:
                              _ptr(vals)) != 0:
             raise ValueError("oracle: weighted quadrature failed")
         return vals
+
+    def integrate_grad(self, GK=None, GM=None, G=None, elems=None):
+        """(dL/dkappa [n_sel][Q], dL/drho [n_sel][Q]) from upstream gradients of the
+        element matrices GK, GM [n_sel][N][N] (either may be None)."""
+        el = self._elems(elems)
+        G = self._check_qp(G, self.dim * self.dim)
+        GK = _f64(GK)
+        GM = _f64(GM)
+        gk = np.zeros((len(el), self.Q)) if GK is not None else None
+        gr = np.zeros((len(el), self.Q)) if GM is not None else None
+        rc = lib().ora_integrate_grad(ctypes.byref(self._s), _ptr(el), len(el), _ptr(G), _ptr(GK),
+                                      _ptr(GM), _ptr(gk), _ptr(gr))
+        if rc != 0:
+            raise ValueError("oracle rejected its arguments")
+        return gk, gr

@@ -866,3 +866,66 @@ int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
   free_layout(&L);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Backward of the element matrices with respect to kappa and rho.           */
+/* ------------------------------------------------------------------------ */
+int ora_integrate_grad(const ora_patch* pt, const int64_t* elems, int64_t n_sel, const double* G,
+                       const double* GK, const double* GM, double* gk, double* gr) {
+  layout L;
+  if ((!GK && !GM) || (GK && !gk) || (GM && !gr) || make_layout(pt, &L)) { free_layout(&L); return -1; }
+  const int d = L.d, n = L.n, N = L.N, Q = L.Q;
+  const int64_t E = n_elements(&L);
+  elem1d* B = (elem1d*)malloc(sizeof(elem1d));
+  double* W = (double*)malloc(sizeof(double) * Q);
+  double* Ginv = (double*)malloc(sizeof(double) * Q * 9);
+  double* phi = (double*)malloc(sizeof(double) * (size_t)N);
+  double* grad = (double*)malloc(sizeof(double) * (size_t)N * 3);
+  int rc = 0;
+  for (int64_t s = 0; s < n_sel && rc == 0; ++s) {
+    const int64_t e = elems[s];
+    if (e < 0 || e >= E) { rc = -1; break; }
+    int ek[3];
+    split_elem(&L, e, ek);
+    element_1d(pt, &L, ek, B);
+    element_geometry(&L, e, B, G, W, Ginv);
+    for (int k = 0; k < Q; ++k) {
+      int kk[3];
+      split_qp(&L, k, kk);
+      const double* Gi = Ginv + (size_t)k * d * d;
+      for (int a = 0; a < N; ++a) {
+        int aa[3];
+        split_local(&L, a, aa);
+        double v = 1.0, gref[3];
+        for (int j = 0; j < d; ++j) v *= B->val[j][kk[j] * n + aa[j]];
+        for (int i = 0; i < d; ++i) {
+          double g = 1.0;
+          for (int j = 0; j < d; ++j)
+            g *= (i == j) ? B->der[j][kk[j] * n + aa[j]] : B->val[j][kk[j] * n + aa[j]];
+          gref[i] = g;
+        }
+        phi[a] = v;
+        for (int i = 0; i < d; ++i) {
+          double s2 = 0.0;
+          for (int j = 0; j < d; ++j) s2 += Gi[j * d + i] * gref[j];
+          grad[(size_t)a * 3 + i] = s2;
+        }
+      }
+      double sk = 0.0, sm = 0.0;
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+          if (GK) {
+            double dot = 0.0;
+            for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + i];
+            sk += GK[((size_t)s * N + a) * N + b] * dot;
+          }
+          if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[b];
+        }
+      if (GK) gk[(size_t)s * Q + k] = W[k] * sk;
+      if (GM) gr[(size_t)s * Q + k] = W[k] * sm;
+    }
+  }
+  free(B); free(W); free(Ginv); free(phi); free(grad);
+  free_layout(&L);
+  return rc;
+}

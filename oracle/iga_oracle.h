@@ -153,6 +153,17 @@ int ora_wq_weights(const double* t, int m, int p, const double* x, int np, doubl
 int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
                 const int32_t* col_idx, double* values);
 
+/* Backward of the element matrices with respect to the coefficients (not in
+ * the paper; the element integrals of eq. 10 and of the stiffness are linear
+ * in kappa and rho): given upstream gradients GK[n_sel][N][N] = dL/dK_e and
+ * GM[n_sel][N][N] = dL/dM_e (either may be NULL),
+ *   gk[s][q] = dL/dkappa_q = w_q |det G_q| sum_ab GK_ab (G^{-T} grad phi_a).(G^{-T} grad phi_b)
+ *   gr[s][q] = dL/drho_q   = w_q |det G_q| sum_ab GM_ab phi_a phi_b
+ * at every quadrature point of every selected element, by the plain double
+ * sum.  Returns 0, or -1. */
+int ora_integrate_grad(const ora_patch* pt, const int64_t* elems, int64_t n_sel, const double* G,
+                       const double* GK, const double* GM, double* gk, double* gr);
+
 #ifdef __cplusplus
 }
 #endif

@@ -240,3 +240,64 @@ def test_apply_bilinear_matches_adjoint(oracle_mod, p, K):
     yK, _ = P.apply(v, kappa=kappa, G=G, mass=False)
     _, J = P.adjoint(u, v, kappa=kappa, G=G)
     assert float(np.dot(u, yK)) == pytest.approx(J, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Backward of the element matrices with respect to kappa and rho
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,p,K", [(2, 2, 3), (3, 2, 2), (3, 3, 2)])
+def test_integrate_grad_linearity(oracle_mod, dim, p, K):
+    """K and M are linear in kappa and rho, so for any upstream GK, GM:
+    sum_q kappa_q dL/dkappa_q = <GK, K(kappa)> and sum_q rho_q dL/drho_q =
+    <GM, M(rho)>, with K, M from the classical element matrices (another
+    oracle path)."""
+    t = wl.open_uniform_knots(K, p)
+    P = oracle_mod.Patch([t] * dim, p, p + 1)
+    kappa = wl.lognormal(P.E * P.Q, 71)
+    rho = wl.lognormal(P.E * P.Q, 72)
+    G = wl.curved_map_jacobian(P.knots, P.q) if dim == 3 else None
+    GK = wl.normal(P.E * P.N * P.N, 73).reshape(P.E, P.N, P.N)
+    GM = wl.normal(P.E * P.N * P.N, 74).reshape(P.E, P.N, P.N)
+    gk, gr = P.integrate_grad(GK=GK, GM=GM, G=G)
+    Ke, Me = P.classical(kappa=kappa, rho=rho, G=G)
+    lhs_k = float((kappa.reshape(P.E, P.Q) * gk).sum())
+    lhs_m = float((rho.reshape(P.E, P.Q) * gr).sum())
+    assert lhs_k == pytest.approx(float((GK * Ke).sum()), rel=1e-12)
+    assert lhs_m == pytest.approx(float((GM * Me).sum()), rel=1e-12)
+
+
+def test_integrate_grad_outer_product_is_adjoint(oracle_mod):
+    """GK_e = u_e v_e^T (the gathered global vectors) gives dL/dkappa of
+    L = u^T K(kappa) v, which the adjoint computes by interpolation at the
+    quadrature points (another oracle path)."""
+    p, K = 2, 3
+    t = wl.open_uniform_knots(K, p)
+    P = oracle_mod.Patch([t] * 3, p, p + 1)
+    G = wl.curved_map_jacobian(P.knots, P.q)
+    u, v = wl.normal(P.n_dofs, 75), wl.normal(P.n_dofs, 76)
+    dof = P.dofmap()
+    GK = u[dof][:, :, None] * v[dof][:, None, :]
+    gk, _ = P.integrate_grad(GK=GK, G=G)
+    g, _ = P.adjoint(u, v, G=G)
+    assert np.abs(gk - g).max() <= 1e-12 * np.abs(g).max()
+
+
+def test_integrate_grad_central_differences(oracle_mod):
+    """d<GK, K(kappa)>/dkappa_q by central differences on sampled points."""
+    p, K = 2, 2
+    t = wl.open_uniform_knots(K, p)
+    P = oracle_mod.Patch([t] * 3, p, p + 1)
+    kappa = wl.lognormal(P.E * P.Q, 77)
+    GK = wl.normal(P.E * P.N * P.N, 78).reshape(P.E, P.N, P.N)
+    gk, _ = P.integrate_grad(GK=GK)
+    rng = np.random.default_rng(79)
+    for idx in rng.choice(P.E * P.Q, size=6, replace=False):
+        h = 1e-6 * kappa[idx]
+        kp, km = kappa.copy(), kappa.copy()
+        kp[idx] += h
+        km[idx] -= h
+        Kp, _ = P.classical(kappa=kp, mass=False)
+        Km, _ = P.classical(kappa=km, mass=False)
+        fd = float((GK * (Kp - Km)).sum()) / (2 * h)
+        assert fd == pytest.approx(gk.reshape(-1)[idx], rel=1e-6, abs=1e-10)

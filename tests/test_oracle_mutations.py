@@ -49,6 +49,10 @@ MUTANTS = {
     "wq_transposed": ("const double f2 = W[1][(size_t)i2 * np[1] + q2] * Bv[1][(size_t)j2 * np[1] + q2];",
                       "const double f2 = W[1][(size_t)j2 * np[1] + q2] * Bv[1][(size_t)i2 * np[1] + q2];",
                       "test_oracle_wq.py"),
+    # element-matrix backward: the upstream gradient read transposed for the mass
+    "grad_mass_product": ("if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[b];",
+                          "if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[a];",
+                          "test_oracle_assembly.py"),
     # sparsity pattern misses the first function of every element
     "pattern_drop": ("for (int b = 0; b < N; ++b)\n        if (mark[dof[b]] != i)",
                      "for (int b = 1; b < N; ++b)\n        if (mark[dof[b]] != i)", "test_oracle_assembly.py"),
