@@ -10,6 +10,12 @@ IgaApply: y = alpha K(kappa) x + beta M(rho) x.  Both operators are symmetric,
 so dL/dx = alpha K g_y + beta M g_y (one more iga_apply), and since y is linear
 in kappa, dL/dkappa_q = alpha * (dJ/dkappa_q of J = g_y^T K(kappa) x), the
 adjoint kernel with u = g_y, v = x.  rho is not differentiated.
+
+IgaIntegrate: (K_e, M_e) = element matrices of every element (iga_integrate).
+Both are linear in the coefficients, so the backward maps the upstream
+gradients dL/dK_e and dL/dM_e to dL/dkappa and dL/drho at every quadrature
+point with one call of the reverse sum-factorization kernel
+(iga_integrate_grad); nothing is saved between the two passes.
 """
 from __future__ import annotations
 
@@ -81,3 +87,38 @@ class IgaApply(torch.autograd.Function):
 def iga_apply(kappa, x, plan, alpha=1.0, beta=0.0, rho=None, jac=None):
     """y = alpha K(kappa) x + beta M(rho) x, differentiable with respect to kappa and x."""
     return IgaApply.apply(kappa, x, plan, alpha, beta, rho, jac)
+
+
+class IgaIntegrate(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, kappa, rho, plan, jac=None):
+        for name, c in (("kappa", kappa), ("rho", rho)):
+            if c is not None and c.dtype != torch.float64:
+                raise TypeError(f"{name} must be float64 (one value per quadrature point)")
+        K, M, _ = plan.empty_outputs(device="cuda", dof=False)
+        plan.integrate(kappa=kappa.contiguous() if kappa is not None else None,
+                       rho=rho.contiguous() if rho is not None else None, jac=jac, K=K, M=M)
+        ctx.plan, ctx.jac = plan, jac
+        ctx.has = (kappa is not None, rho is not None)
+        return K, M
+
+    @staticmethod
+    def backward(ctx, gK, gM):
+        plan = ctx.plan
+        want_k = ctx.needs_input_grad[0] and gK is not None
+        want_r = ctx.needs_input_grad[1] and gM is not None
+        gk = gr = None
+        if want_k or want_r:
+            dt = plan.out_dtype
+            GK = gK.contiguous().to(dt) if want_k else None
+            GM = gM.contiguous().to(dt) if want_r else None
+            g1, g2 = plan.integrate_grad(GK=GK, GM=GM, jac=ctx.jac)
+            gk = g1.to(torch.float64) if want_k else None
+            gr = g2.to(torch.float64) if want_r else None
+        return gk, gr, None, None
+
+
+def iga_integrate(plan, kappa=None, rho=None, jac=None):
+    """(K, M) element matrices (None where the plan skips one), differentiable
+    with respect to kappa and rho."""
+    return IgaIntegrate.apply(kappa, rho, plan, jac)

@@ -39,7 +39,8 @@ IGA_SCHED_PERSISTENT = 2
 IGA_SCHED_PERSISTENT_GRAPH = 3
 
 # Every exported symbol of include/iga.h (checked by tests/test_capi_symbols.py).
-EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_basis_tables",
+EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_integrate_grad",
+            "iga_basis_tables",
             "iga_csr_pattern", "iga_assemble", "iga_apply", "iga_wq_points", "iga_wq_mass",
             "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str")
 
@@ -97,6 +98,8 @@ def lib() -> ctypes.CDLL:
             L.iga_integrate.restype = i32
             L.iga_integrate_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.iga_integrate_backward.restype = i32
+            L.iga_integrate_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.iga_integrate_grad.restype = i32
             L.iga_basis_tables.argtypes = [vp, vp, vp]
             L.iga_basis_tables.restype = i32
             L.iga_csr_pattern.argtypes = [vp, vp, vp, vp]
@@ -145,6 +148,10 @@ def iga_integrate(plan, kappa, rho, jac, K_out, M_out, dof_out, stream) -> int:
 
 def iga_integrate_backward(plan, kappa, jac, u, v, grad_kappa, J_out, stream) -> int:
     return lib().iga_integrate_backward(plan, kappa, jac, u, v, grad_kappa, J_out, stream)
+
+
+def iga_integrate_grad(plan, jac, GK, GM, grad_kappa, grad_rho, stream) -> int:
+    return lib().iga_integrate_grad(plan, jac, GK, GM, grad_kappa, grad_rho, stream)
 
 
 def iga_basis_tables(plan, out, stream) -> int:

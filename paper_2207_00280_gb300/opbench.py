@@ -5,8 +5,9 @@ one JSON line.  Used for profiling single kernels, e.g.
   python -m paper_2207_00280_gb300.opbench --op assemble --workload 3d_p3_16 --precision fp32
 
 Operations: integrate (element matrices), assemble (CSR values of the stiffness
-from its element matrices, integrated once before timing), apply (y = K x + M x)
-and adjoint (J and dJ/dkappa).
+from its element matrices, integrated once before timing), apply (y = K x + M x),
+adjoint (J and dJ/dkappa) and grad (dL/dkappa, and dL/drho where the workload
+has a mass, from random upstream gradients of the element matrices).
 """
 from __future__ import annotations
 
@@ -25,7 +26,7 @@ L2_FLUSH_BYTES = 2 * 129 * 1024 * 1024
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="integrate", choices=["integrate", "assemble", "apply", "adjoint"])
+    ap.add_argument("--op", default="integrate", choices=["integrate", "assemble", "apply", "adjoint", "grad"])
     ap.add_argument("--workload", default="3d_p3_16")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_df", "fp32", "bf16"])
     ap.add_argument("--method", default="sumfact", choices=["sumfact", "classical"])
@@ -62,6 +63,17 @@ def main(argv=None):
 
         def step():
             plan.apply(x, kappa=kappa, jac=jac, alpha=1.0, beta=1.0, y=y, stream=stream)
+    elif args.op == "grad":
+        del D
+        gen = torch.Generator(device=dev).manual_seed(wl.SEED_ADJ_U)
+        GK = torch.randn(K.numel(), dtype=dt, device=dev, generator=gen)
+        GM = torch.randn(M.numel(), dtype=dt, device=dev, generator=gen) if M is not None else None
+        del K, M
+        gk = torch.empty(plan.n_qp, dtype=dt, device=dev)
+        gr = torch.empty(plan.n_qp, dtype=dt, device=dev) if GM is not None else None
+
+        def step():
+            plan.integrate_grad(GK=GK, GM=GM, jac=jac, grad_kappa=gk, grad_rho=gr, stream=stream)
     else:
         del K, M, D
         u = torch.as_tensor(wl.normal(plan.n_dofs, wl.SEED_ADJ_U), device=dev, dtype=dt)

@@ -118,6 +118,24 @@ class IgaPlan:
             raise capi.IgaError(rc, "iga_integrate_backward")
         return grad, J
 
+    def integrate_grad(self, GK=None, GM=None, jac=None, grad_kappa=None, grad_rho=None,
+                       stream=None):
+        """(dL/dkappa, dL/drho) at every quadrature point from upstream gradients
+        GK = dL/dK and GM = dL/dM (layout and dtype of integrate's K and M)."""
+        ref = GK if GK is not None else GM
+        if ref is None:
+            raise ValueError("integrate_grad needs GK or GM")
+        if GK is not None and grad_kappa is None:
+            grad_kappa = torch.empty(self.n_qp, dtype=ref.dtype, device=ref.device)
+        if GM is not None and grad_rho is None:
+            grad_rho = torch.empty(self.n_qp, dtype=ref.dtype, device=ref.device)
+        rc = capi.iga_integrate_grad(self.handle, _ptr(jac), _ptr(GK), _ptr(GM),
+                                     _ptr(grad_kappa if GK is not None else None),
+                                     _ptr(grad_rho if GM is not None else None), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_integrate_grad")
+        return (grad_kappa if GK is not None else None), (grad_rho if GM is not None else None)
+
     @property
     def n_csr_nnz(self) -> int:
         return self.info.n_csr_nnz
