@@ -198,6 +198,7 @@ struct GradArgs {
   const void* GM;        // [E][N][N] or null (skip grad_rho)
   void* grad_kappa;      // [E][Q]
   void* grad_rho;        // [E][Q]
+  bool two_buffers;      // set by the launcher
 };
 cudaError_t launch_grad(const GradArgs& a, int p, int q, bool fp64, cudaStream_t st);
 bool grad_supported(int dim, int p, int q);

@@ -5,44 +5,301 @@
 //   dL/dkappa_q = w_q |det G_q| sum_ij (G^{-1} G^{-T})_ij H_ij(q),
 //   H_ij(q)     = sum_ab GK_ab d_i phi_a(q) d_j phi_b(q)   (reference derivatives)
 //   dL/drho_q   = w_q |det G_q| sum_ab GM_ab phi_a(q) phi_b(q).
+// The metric G^{-1} G^{-T} and phi_a phi_b are symmetric, so only the
+// symmetric parts of GK and GM matter; with a symmetric upstream matrix H is
+// symmetric too (6 distinct terms i <= j instead of 9, 3 for the identity
+// map) and every diagonal stage below is a symmetric matrix, formed on its
+// upper triangle and mirrored.
+//
 // H is formed by sum factorization run backwards (the transpose of Algorithm
-// 2's stage order): for each Gauss point q1 of x, contract (a1, b1) against
-// the x factors, then (a2, b2) against the y factors at every q2, then (a3,
-// b3) against the z factors at every q3.  A term (i, j) uses the derivative
-// factor in direction i on the test side and in direction j on the trial
-// side; identity geometry needs the three terms i = j, a general Jacobian all
-// nine.  One CTA per element; T = double (FP64) or float (FP32 with FP64
-// cofactors and determinant).
+// 2's stage order).  One CTA per element and one pass per upstream matrix:
+// the element's block is read once from HBM into shared memory (padded rows,
+// cp.async; the mass block streams in during the stiffness pass where both
+// fit) and replaced in place by G + G^T; then for each Gauss point q1 of x,
+//   x: UX_st[a2 a3][b2 b3] = sum_{a1 b1} f^s_x(q1)[a1] S[a][b] f^t_x(q1)[b1], S = G + G^T,
+//      for the factor pairs (s, t) the terms need (in FP64 on the upper
+//      triangle of (a2 a3, b2 b3), the pair (derivative, value) giving both
+//      halves);
+//   y: UY_ij[a3][b3][q2] = sum_{a2 b2} f_y(q2)[a2] f_y(q2)[b2] UX[a2 a3][b2 b3];
+//   z: H_ij[q2][q3]      = sum_{a3 b3} f_z(q3)[a3] f_z(q3)[b3] UY_ij[a3][b3][q2];
+// then the geometry at the q^2 points of the slice.  T = double (FP64) or
+// float (FP32 with FP64 cofactors and determinant).
 #include "iga_internal.h"
 
 namespace iga {
 namespace {
 
+// stiffness terms (i, j), i <= j: the diagonal first
+__host__ __device__ constexpr int term_i(int t) { return t < 3 ? t : (t == 5 ? 1 : 0); }
+__host__ __device__ constexpr int term_j(int t) { return t < 3 ? t : (t == 3 ? 1 : 2); }
+
 template <typename T, int P, int QG, bool GEN>
 struct GRD {
   static constexpr int n = P + 1, q = QG, n2 = n * n, n4 = n2 * n2, N = n2 * n, Q = q * q * q;
-  static constexpr int NT = 128;
+  static constexpr int GS = N + 1;               // padded row stride of the staged block
+  static constexpr size_t dyn_bytes = sizeof(T) * (size_t)N * GS;   // one block
+  // room for both upstream blocks (the mass block loads during the stiffness pass)
+  // (FP32 only: the FP64 kernel is bound by its pipe and wants more CTAs per SM)
+  static constexpr bool TWO = sizeof(T) == 4 && 2 * dyn_bytes <= 80 * 1024;
+  // one CTA per SM when the block is large: give it 8 warps
+  static constexpr int NT = dyn_bytes > 48 * 1024 ? 256 : 128;
   static constexpr int REC = 2 * q * n + q;
-  static constexpr int NTERM = GEN ? 9 : 3;       // stiffness terms (i, j)
-  static constexpr int NXP = GEN ? 4 : 2;         // x factor pairs of the stiffness
-  // term t -> (i, j): GEN t = 3 i + j; identity t -> (t, t)
-  static constexpr int ti(int t) { return GEN ? t / 3 : t; }
-  static constexpr int tj(int t) { return GEN ? t % 3 : t; }
-  // x pair index of (s, t): GEN 0 (1,1) 1 (1,0) 2 (0,1) 3 (0,0); identity 0 (1,1) 1 (0,0)
-  static constexpr int xp(int s, int t) {
-    return GEN ? (s ? (t ? 0 : 1) : (t ? 2 : 3)) : (s ? 0 : 1);
-  }
+  static constexpr int T3 = n * (n + 1) / 2;      // upper triangle of (a3, b3)
+  // x items: the upper triangle of (a2 a3, b2 b3) in FP64 (bound by the FP64
+  // pipe: fewer operations); every pair in FP32 (balanced over the threads)
+  static constexpr bool TRI = sizeof(T) == 8;
+  static constexpr int TX = TRI ? n2 * (n2 + 1) / 2 : n4;
+  static constexpr int ITX = (TX + NT - 1) / NT;  // x items per thread
+  static constexpr int NPX = GEN ? 3 : 2;         // x pairs: (d, d), (v, v), (d, v)
+  static constexpr int NTY = GEN ? 6 : 3;         // stiffness terms
+  // the x blocks of a thread's items stay in registers across q1 when small
+  static constexpr bool HOLD = n2 * ITX * (int)sizeof(T) <= 256;
 };
 
-template <typename T, int P, int QG, bool GEN>
-__global__ void __launch_bounds__(128) k_grad3(const GradArgs A) {
+__device__ __forceinline__ void tri_decode(int t, int m, int& a, int& b) {
+  a = 0;
+  while (t >= m - a) {
+    t -= m - a;
+    ++a;
+  }
+  b = a + t;
+}
+
+// [N][N] block from HBM into rows of stride GS = N + 1 (the transposed
+// accesses of the symmetrization then hit distinct banks) by cp.async of one
+// value per thread and step: coalesced, any alignment, the whole block in
+// flight at once without passing through registers.
+template <typename T, int N, int GS, int NT>
+__device__ __forceinline__ void issue_block(const T* __restrict__ src, T* G) {
+  for (int i = threadIdx.x; i < N * N; i += NT) {
+    const int r = i / N;
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(G + r * GS + i - r * N));
+    if (sizeof(T) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + i) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + i) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int PENDING>
+__device__ __forceinline__ void wait_blocks() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+  __syncthreads();
+}
+
+// One upstream matrix: MASS = GM -> grad_rho, else GK -> grad_kappa.
+template <typename T, int P, int QG, bool GEN, bool MASS>
+__device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __restrict__ out, T* G, const T (*f)[2][QG * (P + 1)],
+                                          const double* rec, T* UX, T* UY, T* HZ) {
   using C = GRD<T, P, QG, GEN>;
   constexpr int n = C::n, q = C::q, n2 = C::n2, n4 = C::n4, N = C::N, Q = C::Q, NT = C::NT,
-                REC = C::REC, NTERM = C::NTERM, NXP = C::NXP;
+                REC = C::REC, T3 = C::T3, TX = C::TX, ITX = C::ITX, GS = C::GS;
+  constexpr bool TRI = C::TRI;
+  constexpr int ND = MASS ? 1 : 3;                  // diagonal terms
+  constexpr int NO = MASS ? 0 : C::NTY - 3;         // off-diagonal terms
+  constexpr bool HOLD = C::HOLD;
+  const int tid = threadIdx.x;
+  // the caller has waited for this pass's block and synchronized;
+  // G + G^T (twice the symmetric part; the 1/2 goes into the weights)
+  for (int idx = tid; idx < N * N; idx += NT) {
+    const int a = idx / N, b = idx - a * N;
+    if (a <= b) {
+      const T s = G[a * GS + b] + G[b * GS + a];
+      G[a * GS + b] = s;
+      G[b * GS + a] = s;
+    }
+  }
+  __syncthreads();
+  int ia[ITX], ib[ITX];
+  T Gr[HOLD ? ITX : 1][HOLD ? n2 : 1];
+#pragma unroll
+  for (int k = 0; k < ITX; ++k) {
+    const int t = tid + k * NT;
+    ia[k] = ib[k] = -1;
+    if (t < TX) {
+      if (TRI) {
+        tri_decode(t, n2, ia[k], ib[k]);
+      } else {
+        ia[k] = t / n2;
+        ib[k] = t - ia[k] * n2;
+      }
+    }
+    if (HOLD && t < TX) {
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+        for (int b1 = 0; b1 < n; ++b1)
+          Gr[HOLD ? k : 0][HOLD ? a1 * n + b1 : 0] = G[(a1 + n * ia[k]) * GS + n * ib[k] + b1];
+    }
+  }
+#pragma unroll 1
+  for (int q1 = 0; q1 < q; ++q1) {
+    const T* fx0 = &f[0][0][q1 * n];
+    const T* fx1 = &f[0][1][q1 * n];
+    // x
+#pragma unroll
+    for (int k = 0; k < ITX; ++k) {
+      if (ia[k] < 0) continue;
+      const int a23 = ia[k], b23 = ib[k];
+      T v0[n], v1[n];
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1) {
+        T s0 = 0, s1 = 0;
+#pragma unroll
+        for (int b1 = 0; b1 < n; ++b1) {
+          const T g = HOLD ? Gr[HOLD ? k : 0][HOLD ? a1 * n + b1 : 0]
+                           : G[(a1 + n * a23) * GS + n * b23 + b1];
+          s0 += g * fx0[b1];
+          if (!MASS) s1 += g * fx1[b1];
+        }
+        v0[a1] = s0;
+        v1[a1] = s1;
+      }
+      T p00 = 0, p11 = 0, p10 = 0, p01 = 0;
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1) {
+        p00 += fx0[a1] * v0[a1];
+        if (!MASS) {
+          p11 += fx1[a1] * v1[a1];
+          if (GEN) {
+            p10 += fx1[a1] * v0[a1];
+            if (TRI) p01 += fx0[a1] * v1[a1];
+          }
+        }
+      }
+      const int u = a23 * n2 + b23, l = b23 * n2 + a23;
+      if (MASS) {
+        UX[u] = p00;
+        if (TRI) UX[l] = p00;
+      } else {
+        UX[u] = p11;
+        UX[n4 + u] = p00;
+        if (GEN) UX[2 * n4 + u] = p10;
+        if (TRI) {
+          UX[l] = p11;
+          UX[n4 + l] = p00;
+          if (GEN) UX[2 * n4 + l] = p01;
+        }
+      }
+    }
+    __syncthreads();
+    // y: diagonal terms on the (a3 <= b3) triangle, then the off-diagonal ones
+    for (int it = tid; it < (ND * T3 + NO * n2) * q; it += NT) {
+      int term, a3, b3, q2;
+      bool mirror;
+      if (it < ND * T3 * q) {
+        term = it / (T3 * q);
+        const int r = it - term * (T3 * q);
+        q2 = r % q;
+        tri_decode(r / q, n, a3, b3);
+        mirror = true;
+      } else {
+        const int r0 = it - ND * T3 * q;
+        term = ND + r0 / (n2 * q);
+        const int r = r0 % (n2 * q);
+        q2 = r % q;
+        a3 = (r / q) / n;
+        b3 = (r / q) % n;
+        mirror = false;
+      }
+      int px, sy, ty;
+      if (MASS) {
+        px = 0;
+        sy = ty = 0;
+      } else {
+        const int i = term_i(term), j = term_j(term);
+        px = (i == 0 && j == 0) ? 0 : (i == 0 ? 2 : 1);
+        sy = i == 1;
+        ty = j == 1;
+      }
+      const T* U = UX + px * n4;
+      const T* fa = &f[1][sy][q2 * n];
+      const T* fb = &f[1][ty][q2 * n];
+      T acc = 0;
+#pragma unroll
+      for (int a2 = 0; a2 < n; ++a2) {
+        T s0 = 0;
+#pragma unroll
+        for (int b2 = 0; b2 < n; ++b2) s0 += fb[b2] * U[(a2 + n * a3) * n2 + b2 + n * b3];
+        acc += fa[a2] * s0;
+      }
+      UY[(term * n2 + a3 * n + b3) * q + q2] = acc;
+      if (mirror) UY[(term * n2 + b3 * n + a3) * q + q2] = acc;
+    }
+    __syncthreads();
+    // z: every (term, q2, q3)
+    for (int it = tid; it < (ND + NO) * q * q; it += NT) {
+      const int term = it / (q * q), r = it - term * (q * q), q2 = r % q, q3 = r / q;
+      int sz = 0, tz = 0;
+      if (!MASS) {
+        sz = term_i(term) == 2;
+        tz = term_j(term) == 2;
+      }
+      const T* fa = &f[2][sz][q3 * n];
+      const T* fb = &f[2][tz][q3 * n];
+      const T* U = UY + term * n2 * q + q2;
+      T acc = 0;
+#pragma unroll
+      for (int a3 = 0; a3 < n; ++a3) {
+        T s0 = 0;
+#pragma unroll
+        for (int b3 = 0; b3 < n; ++b3) s0 += fb[b3] * U[(a3 * n + b3) * q];
+        acc += fa[a3] * s0;
+      }
+      HZ[term * q * q + r] = acc;
+    }
+    __syncthreads();
+    // geometry at the q^2 points of this slice
+    for (int it = tid; it < q * q; it += NT) {
+      const int q2 = it % q, q3 = it / q;
+      const int k = q1 + q * (q2 + q * q3);
+      const double W =
+          0.5 * rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2] * rec[2 * REC + 2 * q * n + q3];
+      T g;
+      if (GEN) {
+        const double* Gq = A.jac + (e * Q + k) * 9;
+        const double g00 = Gq[0], g01 = Gq[1], g02 = Gq[2], g10 = Gq[3], g11 = Gq[4], g12 = Gq[5],
+                     g20 = Gq[6], g21 = Gq[7], g22 = Gq[8];
+        const double c[3][3] = {{g11 * g22 - g12 * g21, g12 * g20 - g10 * g22, g10 * g21 - g11 * g20},
+                                {g02 * g21 - g01 * g22, g00 * g22 - g02 * g20, g01 * g20 - g00 * g21},
+                                {g01 * g12 - g02 * g11, g02 * g10 - g00 * g12, g00 * g11 - g01 * g10}};
+        const double adet = fabs(g00 * c[0][0] + g01 * c[0][1] + g02 * c[0][2]);
+        if (MASS) {
+          g = (T)(W * adet) * HZ[it];
+        } else {
+          // w |det| (G^{-1} G^{-T})_ij = (w / |det|) sum_m c_mi c_mj; off-diagonal terms twice
+          const double wk = W / adet;
+          g = 0;
+#pragma unroll
+          for (int term = 0; term < C::NTY; ++term) {
+            const int i = term_i(term), j = term_j(term);
+            const double d = (term < 3 ? wk : 2.0 * wk) *
+                             (c[0][i] * c[0][j] + c[1][i] * c[1][j] + c[2][i] * c[2][j]);
+            g += (T)d * HZ[term * q * q + it];
+          }
+        }
+      } else if (MASS) {
+        g = (T)W * HZ[it];
+      } else {
+        g = (T)W * (HZ[it] + HZ[q * q + it] + HZ[2 * q * q + it]);
+      }
+      out[e * Q + k] = g;
+    }
+  }
+}
+
+template <typename T, int P, int QG, bool GEN>
+__global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs A) {
+  using C = GRD<T, P, QG, GEN>;
+  constexpr int n = C::n, q = C::q, n2 = C::n2, n4 = C::n4, NT = C::NT, REC = C::REC;
+  extern __shared__ __align__(16) unsigned char grad_dyn[];
   __shared__ double rec[3 * REC];
-  __shared__ T f[3][2][q * n];          // [direction][value, derivative][q][n]
-  __shared__ T UX[NXP + 1][n4];         // x-contracted pairs of GK, then the mass pair of GM
-  __shared__ T UY[NTERM + 1][n2 * q];   // [term][a3 n + b3][q2], the mass last
+  __shared__ T f[3][2][q * n];            // [direction][value, derivative][q][n]
+  __shared__ T UX[C::NPX * n4];
+  __shared__ T UY[C::NTY * n2 * q];
+  __shared__ T HZ[C::NTY * q * q];
+  T* G = reinterpret_cast<T*>(grad_dyn);
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
   const int e1 = (int)(e % A.K1);
@@ -59,145 +316,51 @@ __global__ void __launch_bounds__(128) k_grad3(const GradArgs A) {
     const int d = i / (2 * q * n), j = i % (2 * q * n);
     (&f[0][0][0])[i] = (T)rec[d * REC + j];
   }
-  __syncthreads();
-  const T* GK = (const T*)A.GK;
-  const T* GM = (const T*)A.GM;
-  const bool doK = GK != nullptr, doM = GM != nullptr;
-#pragma unroll 1
-  for (int q1 = 0; q1 < q; ++q1) {
-    // x: every (a2 a3, b2 b3) block of the upstream matrices against the x factors
-    for (int it = tid; it < n4; it += NT) {
-      const int a23 = it / n2, b23 = it % n2;
-      if (doK) {
-        T v[2][n];
-#pragma unroll
-        for (int a1 = 0; a1 < n; ++a1) {
-          const T* row = GK + ((int64_t)e * N + a1 + n * a23) * N + n * b23;
-          T s0 = 0, s1 = 0;
-#pragma unroll
-          for (int b1 = 0; b1 < n; ++b1) {
-            const T g = row[b1];
-            s0 += g * f[0][0][q1 * n + b1];
-            s1 += g * f[0][1][q1 * n + b1];
-          }
-          v[0][a1] = s0;
-          v[1][a1] = s1;
-        }
-#pragma unroll
-        for (int pi = 0; pi < NXP; ++pi) {
-          const int s = GEN ? (pi <= 1) : (pi == 0);
-          const int t = GEN ? (pi == 0 || pi == 2) : (pi == 0);
-          T acc = 0;
-#pragma unroll
-          for (int a1 = 0; a1 < n; ++a1) acc += f[0][s][q1 * n + a1] * v[t][a1];
-          UX[pi][it] = acc;
-        }
-      }
-      if (doM) {
-        T acc = 0;
-#pragma unroll
-        for (int a1 = 0; a1 < n; ++a1) {
-          const T* row = GM + ((int64_t)e * N + a1 + n * a23) * N + n * b23;
-          T s0 = 0;
-#pragma unroll
-          for (int b1 = 0; b1 < n; ++b1) s0 += row[b1] * f[0][0][q1 * n + b1];
-          acc += f[0][0][q1 * n + a1] * s0;
-        }
-        UX[NXP][it] = acc;
-      }
-    }
-    __syncthreads();
-    // y: every (term, a3 b3, q2)
-    for (int it = tid; it < (NTERM + 1) * n2 * q; it += NT) {
-      const int term = it / (n2 * q), r = it % (n2 * q), ab3 = r / q, q2 = r % q;
-      if ((term < NTERM && !doK) || (term == NTERM && !doM)) continue;
-      const int a3 = ab3 / n, b3 = ab3 % n;
-      int px, sy, ty;
-      if (term < NTERM) {
-        const int i = C::ti(term), j = C::tj(term);
-        px = C::xp(i == 0, j == 0);
-        sy = i == 1;
-        ty = j == 1;
-      } else {
-        px = NXP;
-        sy = ty = 0;
-      }
-      T acc = 0;
-#pragma unroll
-      for (int a2 = 0; a2 < n; ++a2) {
-        T s0 = 0;
-#pragma unroll
-        for (int b2 = 0; b2 < n; ++b2) s0 += f[1][ty][q2 * n + b2] * UX[px][(a2 + n * a3) * n2 + b2 + n * b3];
-        acc += f[1][sy][q2 * n + a2] * s0;
-      }
-      UY[term][ab3 * q + q2] = acc;
-    }
-    __syncthreads();
-    // z and the geometry at every (q2, q3) of this q1
-    for (int it = tid; it < q * q; it += NT) {
-      const int q2 = it % q, q3 = it / q;
-      const int k = q1 + q * (q2 + q * q3);
-      T H[NTERM + 1];
-#pragma unroll
-      for (int term = 0; term <= NTERM; ++term) {
-        H[term] = 0;
-        if ((term < NTERM && !doK) || (term == NTERM && !doM)) continue;
-        int sz = 0, tz = 0;
-        if (term < NTERM) {
-          sz = C::ti(term) == 2;
-          tz = C::tj(term) == 2;
-        }
-        T acc = 0;
-#pragma unroll
-        for (int a3 = 0; a3 < n; ++a3) {
-          T s0 = 0;
-#pragma unroll
-          for (int b3 = 0; b3 < n; ++b3) s0 += f[2][tz][q3 * n + b3] * UY[term][(a3 * n + b3) * q + q2];
-          acc += f[2][sz][q3 * n + a3] * s0;
-        }
-        H[term] = acc;
-      }
-      const double W = rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2] * rec[2 * REC + 2 * q * n + q3];
-      double wk = W, wm = W;
-      T D[NTERM];
-      if (GEN) {
-        const double* G = A.jac + (e * Q + k) * 9;
-        const double g00 = G[0], g01 = G[1], g02 = G[2], g10 = G[3], g11 = G[4], g12 = G[5],
-                     g20 = G[6], g21 = G[7], g22 = G[8];
-        const double c[3][3] = {{g11 * g22 - g12 * g21, g12 * g20 - g10 * g22, g10 * g21 - g11 * g20},
-                                {g02 * g21 - g01 * g22, g00 * g22 - g02 * g20, g01 * g20 - g00 * g21},
-                                {g01 * g12 - g02 * g11, g02 * g10 - g00 * g12, g00 * g11 - g01 * g10}};
-        const double det = g00 * c[0][0] + g01 * c[0][1] + g02 * c[0][2];
-        const double adet = fabs(det);
-        // w |det| (G^{-1} G^{-T})_ij = (w / |det|) sum_m c_mi c_mj
-        wk = W / adet;
-        wm = W * adet;
-#pragma unroll
-        for (int term = 0; term < NTERM; ++term) {
-          const int i = C::ti(term), j = C::tj(term);
-          D[term] = (T)(wk * (c[0][i] * c[0][j] + c[1][i] * c[1][j] + c[2][i] * c[2][j]));
-        }
-      } else {
-#pragma unroll
-        for (int term = 0; term < NTERM; ++term) D[term] = (T)W;
-      }
-      if (doK) {
-        T g = 0;
-#pragma unroll
-        for (int term = 0; term < NTERM; ++term) g += D[term] * H[term];
-        ((T*)A.grad_kappa)[e * Q + k] = g;
-      }
-      if (doM) ((T*)A.grad_rho)[e * Q + k] = (T)wm * H[NTERM];
-    }
-    __syncthreads();
+  // both blocks in flight at once when the launch gave two buffers
+  constexpr int64_t NN = (int64_t)C::N * C::N;
+  const bool two = A.GK && A.GM && A.two_buffers;
+  T* G1 = two ? G + C::N * C::GS : G;
+  if (A.GK) issue_block<T, C::N, C::GS, NT>((const T*)A.GK + e * NN, G);
+  if (A.GM && (two || !A.GK)) issue_block<T, C::N, C::GS, NT>((const T*)A.GM + e * NN, G1);
+  if (A.GK) {
+    if (two) wait_blocks<1>();
+    else wait_blocks<0>();
+    grad_pass<T, P, QG, GEN, false>(A, e, (T*)A.grad_kappa, G, f, rec, UX, UY, HZ);
   }
+  if (A.GM) {
+    if (A.GK && !two) {
+      __syncthreads();   // the stiffness pass is done with the buffer
+      issue_block<T, C::N, C::GS, NT>((const T*)A.GM + e * NN, G1);
+    }
+    wait_blocks<0>();
+    grad_pass<T, P, QG, GEN, true>(A, e, (T*)A.grad_rho, G1, f, rec, UX, UY, HZ);
+  }
+}
+
+template <typename T, int P, int QG, bool GEN>
+cudaError_t run1(GradArgs a, cudaStream_t st) {
+  using C = GRD<T, P, QG, GEN>;
+  a.two_buffers = a.GK && a.GM && C::TWO;
+  const size_t dyn = C::dyn_bytes * (a.two_buffers ? 2 : 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_grad3<T, P, QG, GEN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(C::dyn_bytes * (C::TWO ? 2 : 1)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_grad3<T, P, QG, GEN>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_grad3<T, P, QG, GEN><<<(unsigned)a.n_elem, C::NT, dyn, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <typename T, int P, int QG>
 cudaError_t run(const GradArgs& a, cudaStream_t st) {
-  if (a.jac) k_grad3<T, P, QG, true><<<(unsigned)a.n_elem, 128, 0, st>>>(a);
-  else k_grad3<T, P, QG, false><<<(unsigned)a.n_elem, 128, 0, st>>>(a);
-  return cudaGetLastError();
+  return a.jac ? run1<T, P, QG, true>(a, st) : run1<T, P, QG, false>(a, st);
 }
 
 template <typename T>
