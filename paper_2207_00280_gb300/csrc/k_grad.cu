@@ -15,7 +15,7 @@
 // 2's stage order).  One CTA per element and one pass per upstream matrix:
 // the element's block is read once from HBM into shared memory (padded rows,
 // cp.async; the mass block streams in during the stiffness pass where both
-// fit) and replaced in place by G + G^T; then for each Gauss point q1 of x,
+// fit), and S = G + G^T is formed; then for each Gauss point q1 of x,
 //   x: UX_st[a2 a3][b2 b3] = sum_{a1 b1} f^s_x(q1)[a1] S[a][b] f^t_x(q1)[b1], S = G + G^T,
 //      for the factor pairs (s, t) the terms need (in FP64 on the upper
 //      triangle of (a2 a3, b2 b3), the pair (derivative, value) giving both
@@ -91,7 +91,8 @@ __device__ __forceinline__ void wait_blocks() {
 // One upstream matrix: MASS = GM -> grad_rho, else GK -> grad_kappa.
 template <typename T, int P, int QG, bool GEN, bool MASS>
 __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __restrict__ out, T* G, const T (*f)[2][QG * (P + 1)],
-                                          const double* rec, T* UX, T* UY, T* HZ) {
+                                          const double* rec, const unsigned char* tri3, T* UX, T* UY,
+                                          T* HZ) {
   using C = GRD<T, P, QG, GEN>;
   constexpr int n = C::n, q = C::q, n2 = C::n2, n4 = C::n4, N = C::N, Q = C::Q, NT = C::NT,
                 REC = C::REC, T3 = C::T3, TX = C::TX, ITX = C::ITX, GS = C::GS;
@@ -100,17 +101,20 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
   constexpr int NO = MASS ? 0 : C::NTY - 3;         // off-diagonal terms
   constexpr bool HOLD = C::HOLD;
   const int tid = threadIdx.x;
-  // the caller has waited for this pass's block and synchronized;
-  // G + G^T (twice the symmetric part; the 1/2 goes into the weights)
-  for (int idx = tid; idx < N * N; idx += NT) {
-    const int a = idx / N, b = idx - a * N;
-    if (a <= b) {
-      const T s = G[a * GS + b] + G[b * GS + a];
-      G[a * GS + b] = s;
-      G[b * GS + a] = s;
+  // The caller has waited for this pass's block and synchronized.  S = G + G^T
+  // (twice the symmetric part; the 1/2 goes into the weights): formed while
+  // loading the register blocks, else in place.
+  if (!HOLD) {
+    for (int idx = tid; idx < N * N; idx += NT) {
+      const int a = idx / N, b = idx - a * N;
+      if (a <= b) {
+        const T s = G[a * GS + b] + G[b * GS + a];
+        G[a * GS + b] = s;
+        G[b * GS + a] = s;
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   int ia[ITX], ib[ITX];
   T Gr[HOLD ? ITX : 1][HOLD ? n2 : 1];
 #pragma unroll
@@ -130,7 +134,8 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
       for (int a1 = 0; a1 < n; ++a1)
 #pragma unroll
         for (int b1 = 0; b1 < n; ++b1)
-          Gr[HOLD ? k : 0][HOLD ? a1 * n + b1 : 0] = G[(a1 + n * ia[k]) * GS + n * ib[k] + b1];
+          Gr[HOLD ? k : 0][HOLD ? a1 * n + b1 : 0] =
+              G[(a1 + n * ia[k]) * GS + n * ib[k] + b1] + G[(b1 + n * ib[k]) * GS + n * ia[k] + a1];
     }
   }
 #pragma unroll 1
@@ -192,7 +197,9 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
         term = it / (T3 * q);
         const int r = it - term * (T3 * q);
         q2 = r % q;
-        tri_decode(r / q, n, a3, b3);
+        const int ab = tri3[r / q];
+        a3 = ab >> 4;
+        b3 = ab & 15;
         mirror = true;
       } else {
         const int r0 = it - ND * T3 * q;
@@ -299,6 +306,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   __shared__ T UX[C::NPX * n4];
   __shared__ T UY[C::NTY * n2 * q];
   __shared__ T HZ[C::NTY * q * q];
+  __shared__ unsigned char tri3[C::T3];   // (a3 << 4 | b3) of the (a3 <= b3) triangle
   T* G = reinterpret_cast<T*>(grad_dyn);
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
@@ -316,6 +324,11 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
     const int d = i / (2 * q * n), j = i % (2 * q * n);
     (&f[0][0][0])[i] = (T)rec[d * REC + j];
   }
+  if (tid < C::T3) {
+    int a3, b3;
+    tri_decode(tid, n, a3, b3);
+    tri3[tid] = (unsigned char)(a3 << 4 | b3);
+  }
   // both blocks in flight at once when the launch gave two buffers
   constexpr int64_t NN = (int64_t)C::N * C::N;
   const bool two = A.GK && A.GM && A.two_buffers;
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   if (A.GK) {
     if (two) wait_blocks<1>();
     else wait_blocks<0>();
-    grad_pass<T, P, QG, GEN, false>(A, e, (T*)A.grad_kappa, G, f, rec, UX, UY, HZ);
+    grad_pass<T, P, QG, GEN, false>(A, e, (T*)A.grad_kappa, G, f, rec, tri3, UX, UY, HZ);
   }
   if (A.GM) {
     if (A.GK && !two) {
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
       issue_block<T, C::N, C::GS, NT>((const T*)A.GM + e * NN, G1);
     }
     wait_blocks<0>();
-    grad_pass<T, P, QG, GEN, true>(A, e, (T*)A.grad_rho, G1, f, rec, UX, UY, HZ);
+    grad_pass<T, P, QG, GEN, true>(A, e, (T*)A.grad_rho, G1, f, rec, tri3, UX, UY, HZ);
   }
 }
 
