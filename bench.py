@@ -528,6 +528,7 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
     forms["apply_3d_p3_40"] = measure_apply(A, ka, stream, flush, dev)
     forms["assembly_3d_p3_32"] = measure_assembly(W, kappa, stream, flush, dev)
     forms["wq_mass_3d_p3_32"] = measure_wq(W, stream, flush, dev)
+    forms["grad_3d_p3_32"] = measure_grad(W, stream, flush, dev)
     return forms
 
 
@@ -617,6 +618,56 @@ def measure_apply(A, kappa, stream, flush, dev):
             ent["fp64_frac"] = round(f_el * sa.E / (ms * 1e-3) / peak, 4)
         out[pr] = ent
         pl.close()
+    return out
+
+
+def grad_flops_per_element(p, q):
+    """Operations of the element-matrix backward per element (3D, identity
+    geometry, multiply-add = 2, FP64 form): S = G + G^T on the triangle of x
+    blocks, then for the stiffness (3 terms, x pairs (d, d) and (v, v)) and the
+    mass (1 term) the x stage on the triangle, the y stage on the (a3 <= b3)
+    triangle and the z stage."""
+    n = p + 1
+    n2 = n * n
+    tx, t3 = n2 * (n2 + 1) // 2, n * (n + 1) // 2
+    adds = 2 * tx * n2
+    fma_k = q * tx * (2 * n2 + 2 * n) + q * 3 * t3 * q * (n2 + n) + q * 3 * q * q * (n2 + n)
+    fma_m = q * tx * (n2 + n) + q * t3 * q * (n2 + n) + q * q * q * (n2 + n)
+    return adds + 2 * (fma_k + fma_m)
+
+
+def measure_grad(W, stream, flush, dev):
+    """Backward of the 32^3 p=3 element matrices (dL/dkappa and dL/drho from
+    dL/dK_e and dL/dM_e), FP64 and FP32: bytes = both upstream blocks read and
+    both gradients written."""
+    import torch
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+    sp = W.spec
+    peaks = measured_peaks()[0]
+    f_el = grad_flops_per_element(sp.p, sp.q)
+    out = {"elements": sp.E, "flop_per_element": f_el}
+    for pr in ("fp64", "fp32"):
+        pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="sumfact", precision=pr, blocking=False)
+        dt = pl.out_dtype
+        gen = torch.Generator(device=dev).manual_seed(20220701)
+        GK = torch.randn(pl.info.n_mat_entries, dtype=dt, device=dev, generator=gen)
+        GM = torch.randn(pl.info.n_mat_entries, dtype=dt, device=dev, generator=gen)
+        gk = torch.empty(pl.n_qp, dtype=dt, device=dev)
+        gr = torch.empty(pl.n_qp, dtype=dt, device=dev)
+        ms = _time_steps(lambda: pl.integrate_grad(GK=GK, GM=GM, grad_kappa=gk, grad_rho=gr,
+                                                   stream=stream), 10, stream, flush)
+        esz = 8 if pr == "fp64" else 4
+        bytes_ = 2 * (GK.numel() + pl.n_qp) * esz
+        ent = {"ms_per_step": round(ms, 4), "elements_per_s": round(sp.E / (ms * 1e-3), 1),
+               "gflops": round(f_el * sp.E / (ms * 1e-3) / 1e9, 1),
+               "hbm_frac": round(bytes_ / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+        if pr == "fp64":
+            peak = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            ent["fp64_frac"] = round(f_el * sp.E / (ms * 1e-3) / peak, 4)
+        out[pr] = ent
+        del GK, GM, gk, gr
+        pl.close()
+        torch.cuda.empty_cache()
     return out
 
 
