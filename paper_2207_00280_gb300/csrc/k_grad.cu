@@ -91,8 +91,8 @@ __device__ __forceinline__ void wait_blocks() {
 // One upstream matrix: MASS = GM -> grad_rho, else GK -> grad_kappa.
 template <typename T, int P, int QG, bool GEN, bool MASS>
 __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __restrict__ out, T* G, const T (*f)[2][QG * (P + 1)],
-                                          const double* rec, const unsigned char* tri3, T* UX, T* UY,
-                                          T* HZ) {
+                                          const double* rec, const T* wts, const unsigned char* tri3,
+                                          T* UX, T* UY, T* HZ) {
   using C = GRD<T, P, QG, GEN>;
   constexpr int n = C::n, q = C::q, n2 = C::n2, n4 = C::n4, N = C::N, Q = C::Q, NT = C::NT,
                 REC = C::REC, T3 = C::T3, TX = C::TX, ITX = C::ITX, GS = C::GS;
@@ -261,10 +261,10 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
     for (int it = tid; it < q * q; it += NT) {
       const int q2 = it % q, q3 = it / q;
       const int k = q1 + q * (q2 + q * q3);
-      const double W =
-          0.5 * rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2] * rec[2 * REC + 2 * q * n + q3];
       T g;
       if (GEN) {
+        const double W =
+            0.5 * rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2] * rec[2 * REC + 2 * q * n + q3];
         const double* Gq = A.jac + (e * Q + k) * 9;
         const double g00 = Gq[0], g01 = Gq[1], g02 = Gq[2], g10 = Gq[3], g11 = Gq[4], g12 = Gq[5],
                      g20 = Gq[6], g21 = Gq[7], g22 = Gq[8];
@@ -286,10 +286,10 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
             g += (T)d * HZ[term * q * q + it];
           }
         }
-      } else if (MASS) {
-        g = (T)W * HZ[it];
       } else {
-        g = (T)W * (HZ[it] + HZ[q * q + it] + HZ[2 * q * q + it]);
+        // identity map: the weight in the kernel's precision
+        const T Wt = (T)0.5 * wts[q1] * wts[q + q2] * wts[2 * q + q3];
+        g = MASS ? Wt * HZ[it] : Wt * (HZ[it] + HZ[q * q + it] + HZ[2 * q * q + it]);
       }
       out[e * Q + k] = g;
     }
@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   __shared__ T UY[C::NTY * n2 * q];
   __shared__ T HZ[C::NTY * q * q];
   __shared__ unsigned char tri3[C::T3];   // (a3 << 4 | b3) of the (a3 <= b3) triangle
+  __shared__ T wts[3 * q];                // Gauss weights per direction
   T* G = reinterpret_cast<T*>(grad_dyn);
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
     const int d = i / (2 * q * n), j = i % (2 * q * n);
     (&f[0][0][0])[i] = (T)rec[d * REC + j];
   }
+  if (tid < 3 * q) wts[tid] = (T)rec[(tid / q) * REC + 2 * q * n + tid % q];
   if (tid < C::T3) {
     int a3, b3;
     tri_decode(tid, n, a3, b3);
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   if (A.GK) {
     if (two) wait_blocks<1>();
     else wait_blocks<0>();
-    grad_pass<T, P, QG, GEN, false>(A, e, (T*)A.grad_kappa, G, f, rec, tri3, UX, UY, HZ);
+    grad_pass<T, P, QG, GEN, false>(A, e, (T*)A.grad_kappa, G, f, rec, wts, tri3, UX, UY, HZ);
   }
   if (A.GM) {
     if (A.GK && !two) {
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
       issue_block<T, C::N, C::GS, NT>((const T*)A.GM + e * NN, G1);
     }
     wait_blocks<0>();
-    grad_pass<T, P, QG, GEN, true>(A, e, (T*)A.grad_rho, G1, f, rec, tri3, UX, UY, HZ);
+    grad_pass<T, P, QG, GEN, true>(A, e, (T*)A.grad_rho, G1, f, rec, wts, tri3, UX, UY, HZ);
   }
 }
 
