@@ -88,6 +88,10 @@ def lib():
             L.ora_wq_weights.restype = ctypes.c_int
             L.ora_wq_mass.argtypes = [pp, dp, dp, dp, dp]
             L.ora_wq_mass.restype = ctypes.c_int
+            L.ora_wq_weights_deriv.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
+            L.ora_wq_weights_deriv.restype = ctypes.c_int
+            L.ora_wq_stiffness.argtypes = [pp, dp, dp, dp, dp]
+            L.ora_wq_stiffness.restype = ctypes.c_int
             L.ora_integrate_grad.argtypes = [pp, dp, ctypes.c_int64, dp, dp, dp, dp, dp]
             L.ora_integrate_grad.restype = ctypes.c_int
             _lib = L
@@ -148,12 +152,14 @@ def wq_points(t, p: int) -> np.ndarray:
     return x[:n].copy()
 
 
-def wq_weights(t, p: int, x) -> np.ndarray:
-    """W[n_functions][n_points]: least-norm weighted-quadrature weights."""
+def wq_weights(t, p: int, x, deriv: bool = False) -> np.ndarray:
+    """W[n_functions][n_points]: least-norm weighted-quadrature weights, the
+    mass rule or (deriv) the derivative rule."""
     t = _f64(t)
     x = _f64(x)
     W = np.zeros((len(t) - p - 1, len(x)))
-    if lib().ora_wq_weights(_ptr(t), len(t), p, _ptr(x), len(x), _ptr(W)) != 0:
+    fn = lib().ora_wq_weights_deriv if deriv else lib().ora_wq_weights
+    if fn(_ptr(t), len(t), p, _ptr(x), len(x), _ptr(W)) != 0:
         raise ValueError("oracle: singular weighted-quadrature system")
     return W
 
@@ -290,6 +296,18 @@ class Patch:
         if lib().ora_wq_mass(ctypes.byref(self._s), _ptr(c), _ptr(row_ptr), _ptr(col_idx),
                              _ptr(vals)) != 0:
             raise ValueError("oracle: weighted quadrature failed")
+        return vals
+
+    def wq_stiffness(self, row_ptr, col_idx, c=None):
+        """CSR values of the weighted-quadrature diffusion stiffness (p >= 2);
+        c as for wq_mass."""
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        c = _f64(c)
+        vals = np.zeros(len(col_idx))
+        if lib().ora_wq_stiffness(ctypes.byref(self._s), _ptr(c), _ptr(row_ptr), _ptr(col_idx),
+                                  _ptr(vals)) != 0:
+            raise ValueError("oracle: weighted-quadrature stiffness failed")
         return vals
 
     def integrate_grad(self, GK=None, GM=None, G=None, elems=None):

@@ -701,6 +701,18 @@ static double wq_bspline(const double* t, int m, int i, int p, double x) {
   return ora_bspline(t, i, p, x);
 }
 
+/* B'_{i;p}(x), the right end of the domain taken as the left limit: there
+ * the degree p-1 function of the last non-empty span is 1 and every other one
+ * 0, so the derivative formula (de Boor) reduces to its two end terms. */
+static double wq_bspline_deriv(const double* t, int m, int i, int p, double x) {
+  if (x < t[m - 1]) return ora_bspline_deriv(t, i, p, x);
+  const int s = m - p - 2;   /* last non-empty span */
+  double d = 0.0;
+  if (i == s && t[i + p] > t[i]) d += (double)p / (t[i + p] - t[i]);
+  if (i + 1 == s && t[i + p + 1] > t[i + 1]) d -= (double)p / (t[i + p + 1] - t[i + 1]);
+  return d;
+}
+
 int ora_wq_points(const double* t, int m, int p, double* x, int cap) {
   if (!t || !x || m < 2 * p + 2 || p < 1) return -1;
   int* sp = (int*)malloc(sizeof(int) * (size_t)m);
@@ -752,8 +764,16 @@ static int wq_solve(double* G, double* r, int n) {
   return 0;
 }
 
-int ora_wq_weights(const double* t, int m, int p, const double* x, int np, double* W) {
-  if (!t || !x || !W || np < 1) return -1;
+/* The rule of every test function; der = 0: exact against the values of the
+ * trial functions with the test function's value (the mass rule), der = 1:
+ * exact against the trial derivatives with the test derivative.  The
+ * derivatives sum to zero on every support (the B_j sum to 1), so with
+ * der = 1 the system has exactly one dependent equation and a consistent
+ * right-hand side; the last equation is dropped, which leaves the solution
+ * set, and so its least-norm member, unchanged. */
+static int wq_weights_impl(const double* t, int m, int p, const double* x, int np, double* W,
+                           int der) {
+  if (!t || !x || !W || np < 1 || (der && p < 2)) return -1;
   const int nf = m - p - 1;
   double gx[64], gw[64];
   if (ora_gauss_legendre(p + 1, gx, gw)) return -1;
@@ -781,36 +801,49 @@ int ora_wq_weights(const double* t, int m, int p, const double* x, int np, doubl
       const double ohi = t[i + p + 1] < t[j + p + 1] ? t[i + p + 1] : t[j + p + 1];
       if (ohi > olo && nj < 64) js[nj++] = j;
     }
-    if (nj > cap || nq < nj) { rc = -1; break; }
+    const int ns = der ? nj - 1 : nj;   /* equations kept */
+    if (nj > cap || nq < ns) { rc = -1; break; }
     for (int a = 0; a < nj; ++a) {
-      for (int q = 0; q < nq; ++q) A[a * nq + q] = wq_bspline(t, m, js[a], p, x[qlo + q]);
-      /* exact int B_i B_j: Gauss with p + 1 points on every element */
+      for (int q = 0; q < nq; ++q)
+        A[a * nq + q] = der ? wq_bspline_deriv(t, m, js[a], p, x[qlo + q])
+                            : wq_bspline(t, m, js[a], p, x[qlo + q]);
+      /* exact int B_i B_j (or B'_i B'_j): Gauss with p + 1 points on every element */
       double s = 0.0;
       for (int e = 0; e < K; ++e) {
         const double ea = t[sp[e]], eb = t[sp[e] + 1];
         if (eb <= lo || ea >= hi) continue;
         for (int g = 0; g < p + 1; ++g) {
           const double xi = 0.5 * (ea + eb) + 0.5 * (eb - ea) * gx[g];
-          s += 0.5 * (eb - ea) * gw[g] * ora_bspline(t, i, p, xi) * ora_bspline(t, js[a], p, xi);
+          s += der ? 0.5 * (eb - ea) * gw[g] * ora_bspline_deriv(t, i, p, xi) *
+                         ora_bspline_deriv(t, js[a], p, xi)
+                   : 0.5 * (eb - ea) * gw[g] * ora_bspline(t, i, p, xi) * ora_bspline(t, js[a], p, xi);
         }
       }
       r[a] = s;
     }
-    for (int a = 0; a < nj; ++a)
-      for (int b = 0; b < nj; ++b) {
+    for (int a = 0; a < ns; ++a)
+      for (int b = 0; b < ns; ++b) {
         double s = 0.0;
         for (int q = 0; q < nq; ++q) s += A[a * nq + q] * A[b * nq + q];
-        G[a * nj + b] = s;
+        G[a * ns + b] = s;
       }
-    if (wq_solve(G, r, nj)) { rc = -1; break; }
+    if (wq_solve(G, r, ns)) { rc = -1; break; }
     for (int q = 0; q < nq; ++q) {
       double s = 0.0;
-      for (int a = 0; a < nj; ++a) s += A[a * nq + q] * r[a];
+      for (int a = 0; a < ns; ++a) s += A[a * nq + q] * r[a];
       W[(size_t)i * np + qlo + q] = s;
     }
   }
   free(sp); free(A); free(G); free(r);
   return rc;
+}
+
+int ora_wq_weights(const double* t, int m, int p, const double* x, int np, double* W) {
+  return wq_weights_impl(t, m, p, x, np, W, 0);
+}
+
+int ora_wq_weights_deriv(const double* t, int m, int p, const double* x, int np, double* W) {
+  return wq_weights_impl(t, m, p, x, np, W, 1);
 }
 
 int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
@@ -863,6 +896,74 @@ int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
     }
   }
   for (int k = 0; k < 3; ++k) { free(x[k]); free(W[k]); free(Bv[k]); }
+  free_layout(&L);
+  return rc;
+}
+
+int ora_wq_stiffness(const ora_patch* pt, const double* c, const int64_t* row_ptr,
+                     const int32_t* col_idx, double* values) {
+  layout L;
+  if (!row_ptr || !col_idx || !values || make_layout(pt, &L)) { free_layout(&L); return -1; }
+  const int d = L.d, p = L.p;
+  /* per direction: R[0] mass rule, R[1] derivative rule; B[0] values, B[1] derivatives */
+  double* x[3] = {NULL, NULL, NULL};
+  double* R[3][2] = {{NULL, NULL}, {NULL, NULL}, {NULL, NULL}};
+  double* B[3][2] = {{NULL, NULL}, {NULL, NULL}, {NULL, NULL}};
+  int np[3] = {1, 1, 1}, nf[3] = {1, 1, 1};
+  int rc = p < 2 ? -1 : 0;
+  for (int k = 0; k < d && rc == 0; ++k) {
+    const int m = pt->m[k];
+    nf[k] = m - p - 1;
+    const int cap = 4 * m + 8;
+    x[k] = (double*)malloc(sizeof(double) * (size_t)cap);
+    np[k] = ora_wq_points(pt->t[k], m, p, x[k], cap);
+    if (np[k] < 1) { rc = -1; break; }
+    for (int v = 0; v < 2; ++v) {
+      R[k][v] = (double*)malloc(sizeof(double) * (size_t)nf[k] * np[k]);
+      B[k][v] = (double*)malloc(sizeof(double) * (size_t)nf[k] * np[k]);
+    }
+    if (ora_wq_weights(pt->t[k], m, p, x[k], np[k], R[k][0]) ||
+        ora_wq_weights_deriv(pt->t[k], m, p, x[k], np[k], R[k][1])) { rc = -1; break; }
+    for (int j = 0; j < nf[k]; ++j)
+      for (int q = 0; q < np[k]; ++q) {
+        B[k][0][(size_t)j * np[k] + q] = wq_bspline(pt->t[k], m, j, p, x[k][q]);
+        B[k][1][(size_t)j * np[k] + q] = wq_bspline_deriv(pt->t[k], m, j, p, x[k][q]);
+      }
+  }
+  if (rc == 0) {
+    const int64_t nd = (int64_t)nf[0] * nf[1] * nf[2];
+    for (int64_t i = 0; i < nd; ++i) {
+      const int i1 = (int)(i % nf[0]), i2 = (int)((i / nf[0]) % nf[1]), i3 = (int)(i / ((int64_t)nf[0] * nf[1]));
+      for (int64_t z = row_ptr[i]; z < row_ptr[i + 1]; ++z) {
+        const int64_t j = col_idx[z];
+        const int j1 = (int)(j % nf[0]), j2 = (int)((j / nf[0]) % nf[1]), j3 = (int)(j / ((int64_t)nf[0] * nf[1]));
+        double s = 0.0;
+        /* term k: derivatives in direction k, values in the others */
+        for (int k = 0; k < d; ++k) {
+          const int v1 = k == 0, v2 = k == 1, v3 = k == 2;
+          for (int q3 = 0; q3 < np[2]; ++q3) {
+            const double f3 = (d == 3) ? R[2][v3][(size_t)i3 * np[2] + q3] * B[2][v3][(size_t)j3 * np[2] + q3] : 1.0;
+            if (f3 == 0.0) continue;
+            for (int q2 = 0; q2 < np[1]; ++q2) {
+              const double f2 = R[1][v2][(size_t)i2 * np[1] + q2] * B[1][v2][(size_t)j2 * np[1] + q2];
+              if (f2 == 0.0) continue;
+              for (int q1 = 0; q1 < np[0]; ++q1) {
+                const double f1 = R[0][v1][(size_t)i1 * np[0] + q1] * B[0][v1][(size_t)j1 * np[0] + q1];
+                if (f1 == 0.0) continue;
+                const double cq = c ? c[q1 + (int64_t)np[0] * (q2 + (int64_t)np[1] * q3)] : 1.0;
+                s += f1 * f2 * f3 * cq;
+              }
+            }
+          }
+        }
+        values[z] = s;
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    free(x[k]);
+    for (int v = 0; v < 2; ++v) { free(R[k][v]); free(B[k][v]); }
+  }
   free_layout(&L);
   return rc;
 }

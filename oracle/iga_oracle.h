@@ -153,6 +153,25 @@ int ora_wq_weights(const double* t, int m, int p, const double* x, int np, doubl
 int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
                 const int32_t* col_idx, double* values);
 
+/* The derivative rule of one direction (p >= 2, where the B'_j are
+ * continuous at the points): W[nf][np] with sum_q W[i][q] B'_j(x_q) =
+ * int B'_i B'_j for every j, least-norm, zero outside the closed support of
+ * B_i; B' at the right end of the domain is the left limit.  The B'_j sum to
+ * zero on every support, so one equation of each system is dependent (with a
+ * consistent right-hand side) and is dropped before the solve.  Returns 0,
+ * or -1. */
+int ora_wq_weights_deriv(const double* t, int m, int p, const double* x, int np, double* W);
+
+/* Global diffusion stiffness by weighted quadrature (p >= 2), on the CSR
+ * pattern of ora_csr_pattern:
+ *   values[z] of (i, j) = sum_k sum_q c[q] prod_l R^(k,l)_{i_l}(x_{q_l}) D^(k,l)_{j_l}(x_{q_l})
+ * where for direction l = k the derivative rule and B'_{j_l}, for l != k the
+ * mass rule and B_{j_l}: the reference-gradient form int c grad B_i . grad B_j
+ * with c the coefficient (kappa |det G| for the identity map) at every grid
+ * point (layout of ora_wq_mass), or NULL = 1.  Returns 0, or -1. */
+int ora_wq_stiffness(const ora_patch* pt, const double* c, const int64_t* row_ptr,
+                     const int32_t* col_idx, double* values);
+
 /* Backward of the element matrices with respect to the coefficients (not in
  * the paper; the element integrals of eq. 10 and of the stiffness are linear
  * in kappa and rho): given upstream gradients GK[n_sel][N][N] = dL/dK_e and

@@ -43,8 +43,19 @@ MUTANTS = {
     "wq_right_end": ("  if (x >= t[m - 1]) return (i == m - p - 2) ? 1.0 : 0.0;",
                      "  if (x >= t[m - 1]) return 0.0;", "test_oracle_wq.py"),
     # weighted quadrature: Gauss weights without the half-length factor
-    "wq_gram_weight": ("s += 0.5 * (eb - ea) * gw[g] * ora_bspline(t, i, p, xi)",
-                       "s += gw[g] * ora_bspline(t, i, p, xi)", "test_oracle_wq.py"),
+    "wq_gram_weight": (": 0.5 * (eb - ea) * gw[g] * ora_bspline(t, i, p, xi)",
+                       ": gw[g] * ora_bspline(t, i, p, xi)", "test_oracle_wq.py"),
+    # weighted quadrature: the derivative rule made exact against trial values
+    "wq_deriv_values": ("A[a * nq + q] = der ? wq_bspline_deriv(t, m, js[a], p, x[qlo + q])",
+                        "A[a * nq + q] = der ? wq_bspline(t, m, js[a], p, x[qlo + q])",
+                        "test_oracle_wq.py"),
+    # weighted quadrature: B' at the right end of the domain taken from the half-open recursion (0)
+    "wq_deriv_right_end": ("  if (x < t[m - 1]) return ora_bspline_deriv(t, i, p, x);",
+                           "  if (x <= t[m - 1]) return ora_bspline_deriv(t, i, p, x);",
+                           "test_oracle_wq.py"),
+    # weighted-quadrature stiffness: the y and z derivative terms exchanged
+    "wq_stiff_direction": ("const int v1 = k == 0, v2 = k == 1, v3 = k == 2;",
+                           "const int v1 = k == 0, v2 = k == 2, v3 = k == 1;", "test_oracle_wq.py"),
     # weighted quadrature: test and trial weights exchanged in direction 2
     "wq_transposed": ("const double f2 = W[1][(size_t)i2 * np[1] + q2] * Bv[1][(size_t)j2 * np[1] + q2];",
                       "const double f2 = W[1][(size_t)j2 * np[1] + q2] * Bv[1][(size_t)i2 * np[1] + q2];",
