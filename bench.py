@@ -577,10 +577,12 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
     return forms
 
 
-def wq_flops(knots, p, xs):
+def wq_flops(knots, p, xs, stiffness=False):
     """Algorithmic flops of the weighted-quadrature mass, row by row: for row
     i with n_k support points and w_k coupled functions per direction,
-    2 (w3 n1 n2 n3 + w2 w3 n1 n2 + w1 w2 w3 n1)."""
+    2 (w3 n1 n2 n3 + w2 w3 n1 n2 + w1 w2 w3 n1); the stiffness contracts two
+    tables in z, three products in y and two in x:
+    2 (2 w3 n1 n2 n3 + 3 w2 w3 n1 n2 + 2 w1 w2 w3 n1)."""
     import numpy as np
     per_dir = []
     for t, x in zip(knots, xs):
@@ -592,13 +594,15 @@ def wq_flops(knots, p, xs):
     (n1, w1), (n2, w2), (n3, w3) = per_dir
     N1, N2, N3 = np.meshgrid(n1, n2, n3, indexing="ij")
     W1, W2, W3 = np.meshgrid(w1, w2, w3, indexing="ij")
-    return float(2 * (W3 * N1 * N2 * N3 + W2 * W3 * N1 * N2 + W1 * W2 * W3 * N1).sum())
+    a, b = (2, 3) if stiffness else (1, 1)
+    return float(2 * (a * W3 * N1 * N2 * N3 + b * W2 * W3 * N1 * N2 + a * W1 * W2 * W3 * N1).sum())
 
 
 def measure_wq(W, stream, flush, dev):
-    """Weighted-quadrature mass (FP64, lognormal coefficient on the point grid)
-    on the 32^3 p=3 mesh, next to the Gauss form of the same matrix: element
-    mass matrices by sum factorization plus their CSR assembly."""
+    """Weighted-quadrature mass and diffusion stiffness (FP64, lognormal
+    coefficient on the point grid) on the 32^3 p=3 mesh, each next to the Gauss
+    form of the same matrix: element matrices by sum factorization plus their
+    CSR assembly."""
     import torch
     from paper_2207_00280_gb300 import workloads as wl
     from paper_2207_00280_gb300.plan import IgaPlan, Patch
@@ -622,6 +626,23 @@ def measure_wq(W, stream, flush, dev):
         pl.integrate(rho=rho, M=M, stream=stream)
         pl.assemble(M, values=vals, stream=stream)
     out["gauss_sumfact_plus_assembly_ms"] = round(_time_steps(gauss, 10, stream, flush), 4)
+    pl.close()
+    # the diffusion stiffness by weighted quadrature, next to its Gauss route
+    pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="sumfact", precision="fp64", mass=False,
+                 stiffness=True, blocking=False)
+    ms = _time_steps(lambda: pl.wq_stiffness(c=c, values=vals, stream=stream), 10, stream, flush)
+    fl = wq_flops(sp.knots, sp.p, pl.wq_points(0), stiffness=True)
+    st = {"ms_per_matrix": round(ms, 4), "rows_per_s": round(pl.n_dofs / (ms * 1e-3), 1),
+          "flop_per_matrix": fl, "fp64_frac": round(fl / (ms * 1e-3) / peak, 4)}
+    K, _, _ = pl.empty_outputs(device=dev, dof=False)
+    kap = torch.as_tensor(wl.lognormal(pl.n_qp, 95), device=dev)
+
+    def gauss_k():
+        pl.integrate(kappa=kap, K=K, stream=stream)
+        pl.assemble(K, values=vals, stream=stream)
+    st["gauss_sumfact_plus_assembly_ms"] = round(_time_steps(gauss_k, 10, stream, flush), 4)
+    out["stiffness"] = st
+    del K
     pl.close()
     return out
 

@@ -254,6 +254,22 @@ int iga_integrate_grad(iga_plan_t plan, const double* jac, const void* GK, const
 int iga_wq_points(iga_plan_t plan, int patch, int dir, double* x_out, int64_t* n_out);
 int iga_wq_mass(iga_plan_t plan, const double* c, double* values, void* cuda_stream);
 
+/* Weighted quadrature for the diffusion stiffness (3D, 2 <= p <= 4; the same
+ * variant extended to derivatives, not defined in the paper).  Besides the
+ * mass rule above, each test function B_i has a derivative rule w'_{i,q} on
+ * the same points: least-norm among the rules with sum_q w'_{i,q} B'_j(x_q) =
+ * int B'_i B'_j for every spline B_j (the B'_j sum to zero on the support, so
+ * one of these equations is dependent and is left out of the solve; B' at the
+ * right end of the domain is the left limit).  The global matrix is formed
+ * row by row,
+ *   K_ij = sum_q c(x_q) sum_k prod_l R^{(l == k)}_{i_l}(x_{q_l}) B^{(l == k)}_{j_l}(x_{q_l}),
+ * R^(0) the mass rule, R^(1) the derivative rule, B^(0) = B, B^(1) = B': the
+ * reference-gradient form int c grad B_i . grad B_j (c = kappa |det G| for the
+ * identity map).  With c = 1 it is the exact stiffness.  FP64 plans only;
+ * c and values as for iga_wq_mass.  IGA_ERR_UNSUPPORTED for 2D, p < 2 or
+ * p > 4, or rule tables beyond shared memory. */
+int iga_wq_stiffness(iga_plan_t plan, const double* c, double* values, void* cuda_stream);
+
 /* With opts.profile = 1: synchronize on the last recorded event and return
  * the summed device time (ms) of the element-matrix kernel launches since the
  * previous call, timed by CUDA events recorded on the caller's stream

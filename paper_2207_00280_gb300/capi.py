@@ -42,6 +42,7 @@ IGA_SCHED_PERSISTENT_GRAPH = 3
 EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_integrate_grad",
             "iga_basis_tables",
             "iga_csr_pattern", "iga_assemble", "iga_apply", "iga_wq_points", "iga_wq_mass",
+            "iga_wq_stiffness",
             "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str")
 
 
@@ -112,6 +113,8 @@ def lib() -> ctypes.CDLL:
             L.iga_wq_points.restype = i32
             L.iga_wq_mass.argtypes = [vp, vp, vp, vp]
             L.iga_wq_mass.restype = i32
+            L.iga_wq_stiffness.argtypes = [vp, vp, vp, vp]
+            L.iga_wq_stiffness.restype = i32
             L.iga_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
             L.iga_profile_read.restype = i32
@@ -176,6 +179,10 @@ def iga_wq_points(plan, patch, dir_, x_out, n_out) -> int:
 
 def iga_wq_mass(plan, c, values, stream) -> int:
     return lib().iga_wq_mass(plan, c, values, stream)
+
+
+def iga_wq_stiffness(plan, c, values, stream) -> int:
+    return lib().iga_wq_stiffness(plan, c, values, stream)
 
 
 def iga_profile_read(plan):

@@ -57,6 +57,7 @@ struct iga_plan_s {
     int* d_qlo = nullptr;
     int* d_qn = nullptr;
     double* d_V = nullptr;
+    double* d_V1 = nullptr;     // derivative rule x trial derivatives (p >= 2)
   };
   std::vector<WqDir> wq;        // [patch * 3 + k]
   std::vector<int64_t> wq_coef_off;  // [n_patches + 1] prefix of the grid sizes
@@ -199,6 +200,77 @@ double host_bspline(const double* t, const std::vector<int>& spans, int p, int j
   return N[j - (s - p)];
 }
 
+// Derivatives of the p+1 B-splines non-zero on span s at x (de Boor's
+// formula from the degree p-1 values of the span, so the right end of the
+// span gives the left limit): dN[r] = B'_{s-p+r;p}(x).
+void host_basis_deriv(const double* t, int p, int s, double x, double* dN) {
+  double Nm[kMaxDegree2D + 1];
+  host_basis(t, p - 1, s, x, Nm);   // Nm[r] = B_{s-p+1+r;p-1}(x), r = 0..p-1
+  for (int r = 0; r <= p; ++r) {
+    const int j = s - p + r;
+    double d = 0.0;
+    if (r >= 1) d += Nm[r - 1] / (t[j + p] - t[j]);
+    if (r <= p - 1) d -= Nm[r] / (t[j + p + 1] - t[j + 1]);
+    dN[r] = p * d;
+  }
+}
+
+double host_bspline_deriv(const double* t, const std::vector<int>& spans, int p, int j, double x) {
+  size_t e = std::upper_bound(spans.begin(), spans.end(), 0, [&](int, int s) { return x < t[s]; }) -
+             spans.begin();
+  e = e == 0 ? 0 : e - 1;
+  const int s = spans[e];
+  if (j < s - p || j > s) return 0.0;
+  double dN[kMaxDegree2D + 1];
+  host_basis_deriv(t, p, s, x, dN);
+  return dN[j - (s - p)];
+}
+
+// Least-norm w = A^T y with (A A^T) y = r for the first ns rows of A [nj][nq]
+// (Cholesky of the Gram matrix); V[(i W + jj) qmax + qq] = w_q A[jj][q] for
+// every jj < nj.  Returns IGA_OK, or IGA_ERR_UNSUPPORTED if the Gram matrix is
+// not positive definite.
+int wq_least_norm(const std::vector<double>& A, std::vector<double> r, int nj, int ns, int nq,
+                  int i, int W, int qmax, std::vector<double>* V_out) {
+  std::vector<double> G((size_t)ns * ns, 0.0);
+  for (int u = 0; u < ns; ++u)
+    for (int v = 0; v <= u; ++v) {
+      double acc = 0.0;
+      for (int qq = 0; qq < nq; ++qq) acc += A[(size_t)u * nq + qq] * A[(size_t)v * nq + qq];
+      G[(size_t)u * ns + v] = acc;
+    }
+  // Cholesky G = L L^T (lower triangle in place), then L L^T y = r
+  for (int u = 0; u < ns; ++u) {
+    for (int v = 0; v <= u; ++v) {
+      double acc = G[(size_t)u * ns + v];
+      for (int k = 0; k < v; ++k) acc -= G[(size_t)u * ns + k] * G[(size_t)v * ns + k];
+      if (u == v) {
+        if (!(acc > 0.0)) return IGA_ERR_UNSUPPORTED;
+        G[(size_t)u * ns + u] = std::sqrt(acc);
+      } else {
+        G[(size_t)u * ns + v] = acc / G[(size_t)v * ns + v];
+      }
+    }
+  }
+  for (int u = 0; u < ns; ++u) {
+    double acc = r[u];
+    for (int k = 0; k < u; ++k) acc -= G[(size_t)u * ns + k] * r[k];
+    r[u] = acc / G[(size_t)u * ns + u];
+  }
+  for (int u = ns - 1; u >= 0; --u) {
+    double acc = r[u];
+    for (int k = u + 1; k < ns; ++k) acc -= G[(size_t)k * ns + u] * r[k];
+    r[u] = acc / G[(size_t)u * ns + u];
+  }
+  std::vector<double>& V = *V_out;
+  for (int qq = 0; qq < nq; ++qq) {
+    double w = 0.0;
+    for (int jj = 0; jj < ns; ++jj) w += A[(size_t)jj * nq + qq] * r[jj];
+    for (int jj = 0; jj < nj; ++jj) V[((size_t)i * W + jj) * qmax + qq] = w * A[(size_t)jj * nq + qq];
+  }
+  return IGA_OK;
+}
+
 // One direction of the weighted quadrature of the mass matrix: the global
 // points (each element's left end and midpoint, p+1 points in the p boundary
 // elements at each end, the right end), and for each test function i the
@@ -209,7 +281,7 @@ double host_bspline(const double* t, const std::vector<int>& spans, int p, int j
 int wq_build_direction(const double* t, int p, const std::vector<int>& spans,
                        const std::vector<FnCouple>& fc, std::vector<double>* x_out,
                        std::vector<int>* qlo_out, std::vector<int>* qn_out,
-                       std::vector<double>* V_out, int* qmax_out) {
+                       std::vector<double>* V_out, std::vector<double>* V1_out, int* qmax_out) {
   const int K = (int)spans.size(), nf = (int)fc.size(), W = 2 * p + 1;
   std::vector<double>& x = *x_out;
   x.clear();
@@ -240,10 +312,11 @@ int wq_build_direction(const double* t, int p, const std::vector<int>& spans,
   }
   std::vector<double>& V = *V_out;
   V.assign((size_t)nf * W * qmax, 0.0);
+  if (V1_out) V1_out->assign((size_t)nf * W * qmax, 0.0);
   for (int i = 0; i < nf; ++i) {
     const int nj = fc[i].fhi - fc[i].flo + 1, nq = qn[i];
     if (nj > W || nq < nj) return IGA_ERR_UNSUPPORTED;
-    std::vector<double> A((size_t)nj * nq), r(nj, 0.0), G((size_t)nj * nj, 0.0);
+    std::vector<double> A((size_t)nj * nq), r(nj, 0.0);
     for (int jj = 0; jj < nj; ++jj)
       for (int qq = 0; qq < nq; ++qq)
         A[(size_t)jj * nq + qq] = host_bspline(t, spans, p, fc[i].flo + jj, x[qlo[i] + qq]);
@@ -261,40 +334,31 @@ int wq_build_direction(const double* t, int p, const std::vector<int>& spans,
         }
       }
     }
-    for (int u = 0; u < nj; ++u)
-      for (int v = 0; v <= u; ++v) {
-        double acc = 0.0;
-        for (int qq = 0; qq < nq; ++qq) acc += A[(size_t)u * nq + qq] * A[(size_t)v * nq + qq];
-        G[(size_t)u * nj + v] = acc;
-      }
-    // Cholesky G = L L^T (lower triangle in place), then L L^T y = r
-    for (int u = 0; u < nj; ++u) {
-      for (int v = 0; v <= u; ++v) {
-        double acc = G[(size_t)u * nj + v];
-        for (int k = 0; k < v; ++k) acc -= G[(size_t)u * nj + k] * G[(size_t)v * nj + k];
-        if (u == v) {
-          if (!(acc > 0.0)) return IGA_ERR_UNSUPPORTED;
-          G[(size_t)u * nj + u] = std::sqrt(acc);
-        } else {
-          G[(size_t)u * nj + v] = acc / G[(size_t)v * nj + v];
+    int rc = wq_least_norm(A, r, nj, nj, nq, i, W, qmax, &V);
+    if (rc != IGA_OK) return rc;
+    if (V1_out) {
+      // the derivative rule: exact against B'_j with B'_i; the B'_j sum to zero
+      // on the support, so the last equation is dependent and is dropped
+      std::vector<double> A1((size_t)nj * nq), r1(nj, 0.0);
+      for (int jj = 0; jj < nj; ++jj)
+        for (int qq = 0; qq < nq; ++qq)
+          A1[(size_t)jj * nq + qq] = host_bspline_deriv(t, spans, p, fc[i].flo + jj, x[qlo[i] + qq]);
+      for (int e = fc[i].elo; e <= fc[i].ehi; ++e) {
+        const int s = spans[e];
+        const double ea = t[s], eb = t[s + 1];
+        double dN[kMaxDegree2D + 1];
+        for (int g = 0; g <= p; ++g) {
+          const double xi = 0.5 * (ea + eb) + 0.5 * (eb - ea) * gx[g];
+          host_basis_deriv(t, p, s, xi, dN);
+          const double di = dN[i - (s - p)], wg = 0.5 * (eb - ea) * gw[g];
+          for (int jj = 0; jj < nj; ++jj) {
+            const int j = fc[i].flo + jj;
+            if (j >= s - p && j <= s) r1[jj] += wg * di * dN[j - (s - p)];
+          }
         }
       }
-    }
-    for (int u = 0; u < nj; ++u) {
-      double acc = r[u];
-      for (int k = 0; k < u; ++k) acc -= G[(size_t)u * nj + k] * r[k];
-      r[u] = acc / G[(size_t)u * nj + u];
-    }
-    for (int u = nj - 1; u >= 0; --u) {
-      double acc = r[u];
-      for (int k = u + 1; k < nj; ++k) acc -= G[(size_t)k * nj + u] * r[k];
-      r[u] = acc / G[(size_t)u * nj + u];
-    }
-    for (int qq = 0; qq < nq; ++qq) {
-      double w = 0.0;
-      for (int jj = 0; jj < nj; ++jj) w += A[(size_t)jj * nq + qq] * r[jj];
-      for (int jj = 0; jj < nj; ++jj)
-        V[((size_t)i * W + jj) * qmax + qq] = w * A[(size_t)jj * nq + qq];
+      rc = wq_least_norm(A1, r1, nj, nj - 1, nq, i, W, qmax, V1_out);
+      if (rc != IGA_OK) return rc;
     }
   }
   *qmax_out = qmax;
@@ -342,6 +406,7 @@ void free_plan_memory(iga_plan_s* P) {
     cudaFree(w.d_qlo);
     cudaFree(w.d_qn);
     cudaFree(w.d_V);
+    cudaFree(w.d_V1);
   }
 }
 
@@ -849,14 +914,15 @@ int wq_ensure(iga_plan_s* P) {
       std::vector<FnCouple> all(P->fc_host.begin() + c.fn_offset[k],
                                 P->fc_host.begin() + c.fn_offset[k] + pd.nf[k]);
       std::vector<int> qlo, qn;
-      std::vector<double> V;
+      std::vector<double> V, V1;
       const double* t = P->knots_host.data() + pd.knot_offset[k];
       rc = wq_build_direction(t, pd.p, P->spans_h[(size_t)ip * P->dim + k], all, &w.x, &qlo, &qn, &V,
-                              &w.qmax);
+                              pd.p >= 2 ? &V1 : nullptr, &w.qmax);
       if (rc != IGA_OK) break;
       cudaError_t e = upload(&w.d_qlo, qlo.data(), qlo.size());
       if (e == cudaSuccess) e = upload(&w.d_qn, qn.data(), qn.size());
       if (e == cudaSuccess) e = upload(&w.d_V, V.data(), V.size());
+      if (e == cudaSuccess && pd.p >= 2) e = upload(&w.d_V1, V1.data(), V1.size());
       if (e != cudaSuccess) { cudaGetLastError(); rc = map_cuda(e); }
       grid *= (int64_t)w.x.size();
     }
@@ -910,12 +976,51 @@ extern "C" int iga_wq_mass(iga_plan_t P, const double* c, double* values, void* 
       a.d[k].qlo = w.d_qlo;
       a.d[k].qn = w.d_qn;
       a.d[k].V = w.d_V;
+      a.d[k].V1 = w.d_V1;
       a.d[k].np = (int)w.x.size();
       a.d[k].qmax = w.qmax;
     }
     a.coef = c ? c + P->wq_coef_off[ip] : nullptr;
     a.values = values;
     e = launch_wq_mass(a, P->ph[ip].p, st);
+  }
+  return finish(P, st, e);
+}
+
+extern "C" int iga_wq_stiffness(iga_plan_t P, const double* c, double* values, void* cuda_stream) {
+  NvtxRange range("iga_wq_stiffness");
+  if (!P || !values) return IGA_ERR_ARG;
+  if (P->sticky != IGA_OK) return P->sticky;
+  if (P->opts.precision != IGA_FP64 && P->opts.precision != IGA_FP64_DF) return IGA_ERR_UNSUPPORTED;
+  for (const PatchDev& pd : P->ph)
+    if (!wq_stiffness_supported(pd.dim, pd.p)) return IGA_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
+  const int rc = wq_ensure(P);
+  if (rc != IGA_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSuccess;
+  for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip) {
+    WqPatchArgs a{};
+    a.c = P->csr[ip];
+    a.fc = P->d_fc;
+    for (int k = 0; k < 3; ++k) {
+      const iga_plan_s::WqDir& w = P->wq[(size_t)ip * 3 + k];
+      a.d[k].qlo = w.d_qlo;
+      a.d[k].qn = w.d_qn;
+      a.d[k].V = w.d_V;
+      a.d[k].V1 = w.d_V1;
+      a.d[k].np = (int)w.x.size();
+      a.d[k].qmax = w.qmax;
+    }
+    a.coef = c ? c + P->wq_coef_off[ip] : nullptr;
+    a.values = values;
+    e = launch_wq_stiffness(a, P->ph[ip].p, st);
+    // a patch whose rule tables exceed shared memory (very short knot vectors)
+    if (e == cudaErrorInvalidValue) {
+      cudaGetLastError();
+      return IGA_ERR_UNSUPPORTED;
+    }
   }
   return finish(P, st, e);
 }

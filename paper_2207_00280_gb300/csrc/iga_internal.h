@@ -212,6 +212,7 @@ struct WqDirDev {
   const int* qlo;
   const int* qn;
   const double* V;
+  const double* V1;   // derivative rule x trial derivatives, same layout (p >= 2), or null
   int np;      // points of the direction
   int qmax;    // padding of the point index in V
 };
@@ -223,5 +224,9 @@ struct WqPatchArgs {
   double* values;        // global CSR values
 };
 cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, cudaStream_t st);
+// Diffusion stiffness by weighted quadrature (3D, FP64, 2 <= p <= 4): values of
+// the rows of one patch, sum over the three derivative directions.
+cudaError_t launch_wq_stiffness(const WqPatchArgs& a, int p, cudaStream_t st);
+bool wq_stiffness_supported(int dim, int p);
 
 }  // namespace iga

@@ -296,6 +296,131 @@ __global__ void __launch_bounds__(128) k_wq_mass(const WqPatchArgs A) {
   }
 }
 
+// Global diffusion stiffness by weighted quadrature (3D, FP64): one CTA per
+// row i.  Direction k has two tables of test function i_k, V0_k (mass rule x
+// trial values) and V1_k (derivative rule x trial derivatives); the row is
+//   K[j] = sum_q c(q) (V1_1 V0_2 V0_3 + V0_1 V1_2 V0_3 + V0_1 V0_2 V1_3)[j](q),
+// contracted one direction at a time:
+//   z: Z0[j3][q1][q2] = sum_q3 V0_3 c,  Z1 = sum_q3 V1_3 c
+//   y: Ya[j2][j3][q1] = sum_q2 V0_2 Z0,  Yb = sum_q2 (V1_2 Z0 + V0_2 Z1)
+//   x: K[j1][j2][j3]  = sum_q1 (V1_1 Ya + V0_1 Yb)
+// and written to the row's CSR entries (j3, j2, j1 ascending).
+template <int P>
+__global__ void __launch_bounds__(128) k_wq_stiff(const WqPatchArgs A) {
+  constexpr int W = 2 * P + 1, NT = 128;
+  extern __shared__ double wsm[];
+  const CsrPatch& c = A.c;
+  const int64_t n_rows = (int64_t)c.nf[0] * c.nf[1] * c.nf[2];
+  for (int64_t row = blockIdx.x; row < n_rows; row += gridDim.x) {
+    int ii[3];
+    const RowGeom g = row_geom(c, A.fc, row, ii);
+    int qlo[3], qn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      qlo[k] = A.d[k].qlo[ii[k]];
+      qn[k] = A.d[k].qn[ii[k]];
+    }
+    const int n1 = qn[0], n2 = qn[1], n3 = qn[2];
+    const int w1 = g.w[0], w2 = g.w[1], w3 = g.w[2];
+    double* V[3][2];
+    V[0][0] = wsm;                       // [w1][n1]
+    V[0][1] = V[0][0] + W * n1;
+    V[1][0] = V[0][1] + W * n1;          // [w2][n2]
+    V[1][1] = V[1][0] + W * n2;
+    V[2][0] = V[1][1] + W * n2;          // [w3][n3]
+    V[2][1] = V[2][0] + W * n3;
+    double* Z0 = V[2][1] + W * n3;                // [w3][n1][n2]
+    double* Z1 = Z0 + (size_t)W * n1 * n2;
+    double* Ya = Z1 + (size_t)W * n1 * n2;        // [w2][w3][n1]
+    double* Yb = Ya + (size_t)W * W * n1;
+    __syncthreads();                     // the previous row's buffers are no longer read
+    for (int k = 0; k < 3; ++k) {
+      const int wk = g.w[k], nk = qn[k];
+      for (int v = 0; v < 2; ++v) {
+        const double* src = (v ? A.d[k].V1 : A.d[k].V) + (size_t)ii[k] * W * A.d[k].qmax;
+        double* dst = V[k][v];
+        for (int t = threadIdx.x; t < wk * nk; t += NT) dst[t] = src[(t / nk) * A.d[k].qmax + t % nk];
+      }
+    }
+    __syncthreads();
+    // z: one coefficient load per point, both tables' sums in registers
+    const int64_t np1 = A.d[0].np, np2 = A.d[1].np;
+    const double* V30 = V[2][0];
+    const double* V31 = V[2][1];
+    for (int it = threadIdx.x; it < n1 * n2; it += NT) {
+      const int q1 = it % n1, q2 = it / n1;
+      double a0[W], a1[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) a0[j] = a1[j] = 0.0;
+      for (int q3 = 0; q3 < n3; ++q3) {
+        const double cq = A.coef ? A.coef[(qlo[0] + q1) + np1 * ((qlo[1] + q2) + np2 * (qlo[2] + q3))] : 1.0;
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w3) {
+            a0[j] = fma(V30[j * n3 + q3], cq, a0[j]);
+            a1[j] = fma(V31[j * n3 + q3], cq, a1[j]);
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j < w3) {
+          Z0[((size_t)j * n1 + q1) * n2 + q2] = a0[j];
+          Z1[((size_t)j * n1 + q1) * n2 + q2] = a1[j];
+        }
+    }
+    __syncthreads();
+    // y
+    const double* V20 = V[1][0];
+    const double* V21 = V[1][1];
+    for (int it = threadIdx.x; it < n1 * w3; it += NT) {
+      const int q1 = it % n1, j3 = it / n1;
+      const double* z0 = Z0 + ((size_t)j3 * n1 + q1) * n2;
+      const double* z1 = Z1 + ((size_t)j3 * n1 + q1) * n2;
+      double aa[W], ab[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) aa[j] = ab[j] = 0.0;
+      for (int q2 = 0; q2 < n2; ++q2) {
+        const double t0 = z0[q2], t1 = z1[q2];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w2) {
+            const double v0 = V20[j * n2 + q2];
+            aa[j] = fma(v0, t0, aa[j]);
+            ab[j] = fma(V21[j * n2 + q2], t0, fma(v0, t1, ab[j]));
+          }
+      }
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j < w2) {
+          Ya[((size_t)j * w3 + j3) * n1 + q1] = aa[j];
+          Yb[((size_t)j * w3 + j3) * n1 + q1] = ab[j];
+        }
+    }
+    __syncthreads();
+    // x, then the row's entries
+    const double* V10 = V[0][0];
+    const double* V11 = V[0][1];
+    for (int it = threadIdx.x; it < w2 * w3; it += NT) {
+      const int j2 = it % w2, j3 = it / w2;
+      const double* ya = Ya + ((size_t)j2 * w3 + j3) * n1;
+      const double* yb = Yb + ((size_t)j2 * w3 + j3) * n1;
+      double acc[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int q1 = 0; q1 < n1; ++q1) {
+        const double ta = ya[q1], tb = yb[q1];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+          if (j < w1) acc[j] = fma(V11[j * n1 + q1], ta, fma(V10[j * n1 + q1], tb, acc[j]));
+      }
+      double* out = A.values + g.start + ((int64_t)j3 * w2 + j2) * w1;
+#pragma unroll
+      for (int j = 0; j < W; ++j)
+        if (j < w1) out[j] = acc[j];
+    }
+  }
+}
+
 template <typename T, int P, int DIM>
 cudaError_t run_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans, const void* A,
                          void* values, cudaStream_t st) {
@@ -379,7 +504,35 @@ cudaError_t run_wq(const WqPatchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t run_wq_stiff(const WqPatchArgs& a, cudaStream_t st) {
+  constexpr int W = 2 * P + 1;
+  const int64_t n_rows = (int64_t)a.c.nf[0] * a.c.nf[1] * a.c.nf[2];
+  if (n_rows == 0) return cudaSuccess;
+  const size_t q1 = a.d[0].qmax, q2 = a.d[1].qmax, q3 = a.d[2].qmax;
+  const size_t smem =
+      sizeof(double) * (2 * W * (q1 + q2 + q3) + 2 * W * q1 * q2 + 2 * (size_t)W * W * q1);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto k = k_wq_stiff<P>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = n_rows < 152 * 64 ? n_rows : 152 * 64;
+  k<<<(unsigned)blocks, 128, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool wq_stiffness_supported(int dim, int p) { return dim == 3 && p >= 2 && p <= 4; }
+
+cudaError_t launch_wq_stiffness(const WqPatchArgs& a, int p, cudaStream_t st) {
+  switch (p) {
+    case 2: return run_wq_stiff<2>(a, st);
+    case 3: return run_wq_stiff<3>(a, st);
+    case 4: return run_wq_stiff<4>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, cudaStream_t st) {
   switch (p) {

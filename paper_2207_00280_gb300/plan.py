@@ -201,6 +201,16 @@ class IgaPlan:
             raise capi.IgaError(rc, "iga_wq_mass")
         return values
 
+    def wq_stiffness(self, c=None, values=None, stream=None):
+        """CSR values of the weighted-quadrature diffusion stiffness (c on the point
+        grid or None = 1; 3D, 2 <= p <= 4)."""
+        if values is None:
+            values = torch.empty(self.n_csr_nnz, dtype=torch.float64, device="cuda")
+        rc = capi.iga_wq_stiffness(self.handle, _ptr(c), _ptr(values), _stream(stream))
+        if rc != capi.IGA_OK:
+            raise capi.IgaError(rc, "iga_wq_stiffness")
+        return values
+
     def profile_read(self):
         """(ms, launches) of the element-matrix kernels since the last read."""
         return capi.iga_profile_read(self.handle)

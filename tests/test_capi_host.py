@@ -100,6 +100,7 @@ def test_argument_errors(capi):
     n = ctypes.c_int64()
     assert L.iga_wq_points(None, 0, 0, None, ctypes.byref(n)) == capi.IGA_ERR_ARG
     assert L.iga_wq_mass(None, None, None, None) == capi.IGA_ERR_ARG
+    assert L.iga_wq_stiffness(None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_integrate_grad(None, None, None, None, None, None, None) == capi.IGA_ERR_ARG
     assert L.iga_destroy(None) == capi.IGA_OK
 

@@ -112,3 +112,103 @@ def test_fp32_plan_rejected():
         plan.wq_mass()
     assert ei.value.code == capi.IGA_ERR_UNSUPPORTED
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Weighted-quadrature diffusion stiffness (iga_wq_stiffness)
+# --------------------------------------------------------------------------
+
+def _stiff_cases():
+    return [c for c in _cases() if c[2] >= 2]
+
+
+@pytest.mark.parametrize("coef", ["one", "lognormal"])
+@pytest.mark.parametrize("case", _stiff_cases(), ids=lambda c: c[0])
+def test_stiffness_matches_oracle(case, coef):
+    _, knots, p = case
+    P = oracle.Patch(list(knots), p, p + 1)
+    rp, ci = P.csr_pattern()
+    plan = IgaPlan(Patch(list(knots), p, p + 1), method="sumfact", precision="fp64")
+    n = plan.wq_grid_size(0)
+    c = None if coef == "one" else wl.lognormal(n, 94)
+    ref = P.wq_stiffness(rp, ci, c=c)
+    ct = torch.as_tensor(c, device=DEV) if c is not None else None
+    vals = plan.wq_stiffness(c=ct).cpu().numpy()
+    assert np.abs(vals - ref).max() <= 1e-12 * np.abs(ref).max()
+    plan.close()
+
+
+def test_stiffness_batch_matches_oracle():
+    specs = [([wl.open_uniform_knots(4, 2), wl.open_uniform_knots(3, 2), wl.open_uniform_knots(5, 2)], 2),
+             ([wl.open_uniform_knots(4, 3), wl.open_uniform_knots(5, 3), wl.open_uniform_knots(4, 3)], 3),
+             ([_nonuniform_knots(2, 63)] * 3, 2)]
+    plan = IgaPlan([Patch(list(k), p, p + 1) for k, p in specs], method="sumfact", precision="fp64")
+    total = plan.wq_grid_size(-1)
+    c = wl.lognormal(total, 95)
+    vals = plan.wq_stiffness(c=torch.as_tensor(c, device=DEV)).cpu().numpy()
+    off, nnz = 0, 0
+    for i, (knots, p) in enumerate(specs):
+        P = oracle.Patch(knots, p, p + 1)
+        rp, ci = P.csr_pattern()
+        g = plan.wq_grid_size(i)
+        ref = P.wq_stiffness(rp, ci, c=c[off:off + g])
+        got = vals[nnz:nnz + len(ci)]
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), i
+        off += g
+        nnz += len(ci)
+    assert off == total and nnz == len(vals)
+    plan.close()
+
+
+def _bspline_integrals(t, p):
+    nf = len(t) - p - 1
+    return np.array([(t[i + p + 1] - t[i]) / (p + 1) for i in range(nf)])
+
+
+def test_stiffness_full_size_closed_forms():
+    """3D p=3, 32^3 elements.  Lognormal c: every row sums to zero (the trial
+    gradients sum to zero at every point).  c = 1 (exact): K x = boundary
+    flux for x the Greville abscissae of one direction (a linear field),
+    (B_{i_k}(1) - B_{i_k}(0)) prod_{l != k} int B_{i_l}, in each direction."""
+    K_el, p = 32, 3
+    t = wl.open_uniform_knots(K_el, p)
+    plan = IgaPlan(Patch([t] * 3, p, p + 1), method="sumfact", precision="fp64")
+    rp, ci = plan.csr_pattern()
+    n = plan.n_dofs
+    seg = torch.repeat_interleave(torch.arange(n, device=DEV), rp[1:] - rp[:-1])
+    c = torch.as_tensor(wl.lognormal(plan.wq_grid_size(0), 96), device=DEV)
+    vals = plan.wq_stiffness(c=c)
+    rows = torch.zeros(n, dtype=torch.float64, device=DEV).index_add_(0, seg, vals)
+    assert float(rows.abs().max()) <= 1e-13 * float(vals.abs().max())
+    vals1 = plan.wq_stiffness()
+    nf = len(t) - p - 1
+    gre = np.array([np.mean(t[i + 1:i + p + 1]) for i in range(nf)])
+    b = _bspline_integrals(t, p)
+    jump = np.zeros(nf)
+    jump[0], jump[-1] = -1.0, 1.0
+    idx = np.arange(n)
+    comp = (idx % nf, (idx // nf) % nf, idx // (nf * nf))
+    for k in range(3):
+        x = torch.as_tensor(gre[comp[k]], device=DEV)
+        y = torch.zeros(n, dtype=torch.float64, device=DEV).index_add_(0, seg, vals1 * x[ci.long()])
+        f = [b, b, b]
+        f[k] = jump
+        flux = np.einsum("k,j,i->kji", f[2], f[1], f[0]).reshape(-1)
+        assert np.abs(y.cpu().numpy() - flux).max() <= 1e-12 * np.abs(flux).max(), k
+    plan.close()
+
+
+def test_stiffness_unsupported():
+    for p in (1, 5):
+        t = wl.open_uniform_knots(3, p)
+        plan = IgaPlan(Patch([t] * 3, p, p + 1), method="sumfact", precision="fp64")
+        with pytest.raises(capi.IgaError) as ei:
+            plan.wq_stiffness()
+        assert ei.value.code == capi.IGA_ERR_UNSUPPORTED
+        plan.close()
+    t = wl.open_uniform_knots(3, 2)
+    plan = IgaPlan(Patch([t] * 3, 2, 3), method="sumfact", precision="fp32")
+    with pytest.raises(capi.IgaError) as ei:
+        plan.wq_stiffness()
+    assert ei.value.code == capi.IGA_ERR_UNSUPPORTED
+    plan.close()
