@@ -264,7 +264,7 @@ int iga_wq_mass(iga_plan_t plan, const double* c, double* values, void* cuda_str
  * row by row,
  *   K_ij = sum_q c(x_q) sum_k prod_l R^{(l == k)}_{i_l}(x_{q_l}) B^{(l == k)}_{j_l}(x_{q_l}),
  * R^(0) the mass rule, R^(1) the derivative rule, B^(0) = B, B^(1) = B': the
- * reference-gradient form int c grad B_i . grad B_j (c = kappa |det G| for the
+ * reference-gradient form int c grad B_i . grad B_j (c = kappa for the
  * identity map).  With c = 1 it is the exact stiffness.  FP64 plans only;
  * c and values as for iga_wq_mass.  IGA_ERR_UNSUPPORTED for 2D, p < 2 or
  * p > 4, or rule tables beyond shared memory. */

@@ -167,7 +167,7 @@ int ora_wq_weights_deriv(const double* t, int m, int p, const double* x, int np,
  *   values[z] of (i, j) = sum_k sum_q c[q] prod_l R^(k,l)_{i_l}(x_{q_l}) D^(k,l)_{j_l}(x_{q_l})
  * where for direction l = k the derivative rule and B'_{j_l}, for l != k the
  * mass rule and B_{j_l}: the reference-gradient form int c grad B_i . grad B_j
- * with c the coefficient (kappa |det G| for the identity map) at every grid
+ * with c the coefficient (kappa for the identity map) at every grid
  * point (layout of ora_wq_mass), or NULL = 1.  Returns 0, or -1. */
 int ora_wq_stiffness(const ora_patch* pt, const double* c, const int64_t* row_ptr,
                      const int32_t* col_idx, double* values);
