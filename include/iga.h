@@ -215,8 +215,9 @@ int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_s
 int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const double* jac,
               const void* x, double alpha, double beta, void* y, void* cuda_stream);
 
-/* Backward of the element matrices with respect to the coefficients (3D,
- * p <= 3 with q = p+1 or p+2, and p = 4 with q = 5; not in the paper).  The
+/* Backward of the element matrices with respect to the coefficients (not in
+ * the paper).  3D: p <= 4 with q = p+1 or p+2, and p = 5 with q = 6 on FP32
+ * plans; 2D (FP64 plans): p <= 5 with q = p+1 or p+2.  The
  * element matrices are linear in kappa and rho, so for upstream gradients
  * GK = dL/dK_e and GM = dL/dM_e (layout and dtype of iga_integrate's K_out):
  *   grad_kappa[k] = w_k |det G_k| sum_ab GK_ab (G_k^{-T} grad phi_a).(G_k^{-T} grad phi_b)
@@ -225,7 +226,7 @@ int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const dou
  * factorization run backwards (x, then y, then z factors), one CTA per
  * element, in FP64 for IGA_FP64/IGA_FP64_DF plans and in FP32 (FP64
  * cofactors and determinant) otherwise.
- *   jac: [n_qp][3][3] or NULL (= identity).
+ *   jac: [n_qp][d][d] or NULL (= identity).
  *   GK, GM: device, NULL skips that gradient (not both NULL).
  *   grad_kappa, grad_rho: device [n_qp], dtype of GK; required where the
  *   matching upstream gradient is given, overwritten. */

@@ -786,12 +786,12 @@ extern "C" int iga_integrate_grad(iga_plan_t P, const double* jac, const void* G
   if (!P) return IGA_ERR_ARG;
   if (P->sticky != IGA_OK) return P->sticky;
   if ((!GK && !GM) || (GK && !grad_kappa) || (GM && !grad_rho)) return IGA_ERR_ARG;
+  const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
   for (const PatchDev& pd : P->ph)
-    if (!grad_supported(pd.dim, pd.p, pd.q)) return IGA_ERR_UNSUPPORTED;
+    if (!grad_supported(pd.dim, pd.p, pd.q, fp64)) return IGA_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   cudaError_t e = launch_basis_tables(P->d_jobs, P->n_jobs, P->d_knots, P->d_gauss,
                                       P->d_tables, st);
@@ -801,12 +801,12 @@ extern "C" int iga_integrate_grad(iga_plan_t P, const double* jac, const void* G
     a.n_elem = (int64_t)pd.K[0] * pd.K[1] * pd.K[2];
     a.K1 = pd.K[0]; a.K2 = pd.K[1]; a.K3 = pd.K[2];
     for (int k = 0; k < 3; ++k) a.tab[k] = P->d_tables + pd.tab_offset[k];
-    a.jac = jac ? jac + pd.qp_offset * 9 : nullptr;
+    a.jac = jac ? jac + pd.qp_offset * pd.dim * pd.dim : nullptr;
     a.GK = GK ? (const char*)GK + esz * pd.mat_offset : nullptr;
     a.GM = GM ? (const char*)GM + esz * pd.mat_offset : nullptr;
     a.grad_kappa = GK ? (char*)grad_kappa + esz * pd.qp_offset : nullptr;
     a.grad_rho = GM ? (char*)grad_rho + esz * pd.qp_offset : nullptr;
-    e = launch_grad(a, pd.p, pd.q, fp64, st);
+    e = launch_grad(a, pd.dim, pd.p, pd.q, fp64, st);
   }
   return finish(P, st, e);
 }

@@ -185,7 +185,7 @@ cudaError_t launch_apply_gather(const CsrPatch& c, const FnCouple* fc, const int
                                 const void* scratch, void* y, bool fp64, cudaStream_t st);
 bool apply_supported(int dim, int p, int q);
 
-// Backward of the element matrices with respect to the coefficients (3D):
+// Backward of the element matrices with respect to the coefficients (2D, 3D):
 // grad_kappa[e*Q + k] = sum_ab GK[e][a][b] dK_ab/dkappa_k and grad_rho[e*Q + k]
 // = sum_ab GM[e][a][b] dM_ab/drho_k.  All pointers are patch-local; GK, GM
 // and the gradients are double (fp64) or float.
@@ -193,15 +193,15 @@ struct GradArgs {
   int64_t n_elem;
   int K1, K2, K3;
   const double* tab[3];
-  const double* jac;     // [E][Q][9] or null (= identity)
+  const double* jac;     // [E][Q][d*d] or null (= identity)
   const void* GK;        // [E][N][N] or null (skip grad_kappa)
   const void* GM;        // [E][N][N] or null (skip grad_rho)
   void* grad_kappa;      // [E][Q]
   void* grad_rho;        // [E][Q]
   bool two_buffers;      // set by the launcher
 };
-cudaError_t launch_grad(const GradArgs& a, int p, int q, bool fp64, cudaStream_t st);
-bool grad_supported(int dim, int p, int q);
+cudaError_t launch_grad(const GradArgs& a, int dim, int p, int q, bool fp64, cudaStream_t st);
+bool grad_supported(int dim, int p, int q, bool fp64);
 
 // ---- weighted quadrature (mass matrix, 3D, FP64) -------------------------------
 // One direction of one patch: the rule of test function i covers the points

@@ -1,6 +1,7 @@
 // k_grad.cu -- backward of the element matrices with respect to the
 // coefficients (3D; not in the paper: the element integrals are linear in
-// kappa and rho, eq. 10 and the stiffness of Sec. 2.2).  Given upstream
+// kappa and rho, eq. 10 and the stiffness of Sec. 2.2; 3D below, 2D in
+// k_grad2).  Given upstream
 // gradients GK = dL/dK_e and GM = dL/dM_e:
 //   dL/dkappa_q = w_q |det G_q| sum_ij (G^{-1} G^{-T})_ij H_ij(q),
 //   H_ij(q)     = sum_ab GK_ab d_i phi_a(q) d_j phi_b(q)   (reference derivatives)
@@ -352,6 +353,140 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   }
 }
 
+// 2D: one CTA per element, both upstream blocks in shared memory (padded rows,
+// cp.async) and replaced by S = G + G^T; for each Gauss point q1 of x the x
+// stage UX_st[a2][b2] = sum_{a1 b1} f^s_x(q1)[a1] S[a][b] f^t_x(q1)[b1] for the
+// pairs the terms need, then one thread per q2 forms every term
+// H_ij(q1, q2) = sum_{a2 b2} f_y(q2)[a2] f_y(q2)[b2] UX[a2][b2] and the
+// geometry: terms (0,0), (1,1) and, for a general map, (0,1) twice.
+template <typename T, int P, int QG, bool GEN>
+__global__ void __launch_bounds__(64) k_grad2(const GradArgs A) {
+  constexpr int n = P + 1, q = QG, N = n * n, GS = N + 1, NT = 64, REC = 2 * q * n + q;
+  constexpr int NP = GEN ? 3 : 2;              // x pairs (d, d), (v, v), (d, v)
+  __shared__ __align__(16) T Gs[2][N * GS];
+  __shared__ double rec[2 * REC];
+  __shared__ T f[2][2][q * n];
+  __shared__ T UX[NP + 1][N];                  // the stiffness pairs, then the mass pair
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const int e1 = (int)(e % A.K1), e2 = (int)(e / A.K1);
+  const int64_t NN = (int64_t)N * N;
+  if (A.GK) issue_block<T, N, GS, NT>((const T*)A.GK + e * NN, Gs[0]);
+  if (A.GM) issue_block<T, N, GS, NT>((const T*)A.GM + e * NN, Gs[1]);
+  for (int i = tid; i < 2 * REC; i += NT) {
+    const int d = i / REC, j = i - d * REC;
+    rec[i] = (d == 0 ? A.tab[0] + (int64_t)e1 * REC : A.tab[1] + (int64_t)e2 * REC)[j];
+  }
+  wait_blocks<0>();
+  for (int i = tid; i < 2 * 2 * q * n; i += NT) {
+    const int d = i / (2 * q * n), j = i % (2 * q * n);
+    (&f[0][0][0])[i] = (T)rec[d * REC + j];
+  }
+  for (int m = 0; m < 2; ++m) {
+    if ((m == 0 && !A.GK) || (m == 1 && !A.GM)) continue;
+    T* G = Gs[m];
+    for (int idx = tid; idx < N * N; idx += NT) {
+      const int a = idx / N, b = idx - a * N;
+      if (a <= b) {
+        const T s = G[a * GS + b] + G[b * GS + a];
+        G[a * GS + b] = s;
+        G[b * GS + a] = s;
+      }
+    }
+  }
+  __syncthreads();
+  const bool doK = A.GK != nullptr, doM = A.GM != nullptr;
+#pragma unroll 1
+  for (int q1 = 0; q1 < q; ++q1) {
+    const T* fx0 = &f[0][0][q1 * n];
+    const T* fx1 = &f[0][1][q1 * n];
+    for (int it = tid; it < 2 * N; it += NT) {
+      const int m = it / N, ab = it - m * N, a2 = ab / n, b2 = ab % n;
+      if ((m == 0 && !doK) || (m == 1 && !doM)) continue;
+      const T* G = Gs[m];
+      T v0[n], v1[n];
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1) {
+        T s0 = 0, s1 = 0;
+#pragma unroll
+        for (int b1 = 0; b1 < n; ++b1) {
+          const T g = G[(a1 + n * a2) * GS + n * b2 + b1];
+          s0 += g * fx0[b1];
+          s1 += g * fx1[b1];
+        }
+        v0[a1] = s0;
+        v1[a1] = s1;
+      }
+      T p00 = 0, p11 = 0, p10 = 0;
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1) {
+        p00 += fx0[a1] * v0[a1];
+        p11 += fx1[a1] * v1[a1];
+        p10 += fx1[a1] * v0[a1];
+      }
+      if (m == 1) {
+        UX[NP][ab] = p00;
+      } else {
+        UX[0][ab] = p11;
+        UX[1][ab] = p00;
+        if (GEN) UX[2][ab] = p10;
+      }
+    }
+    __syncthreads();
+    for (int q2 = tid; q2 < q; q2 += NT) {
+      const T* fy0 = &f[1][0][q2 * n];
+      const T* fy1 = &f[1][1][q2 * n];
+      // H00: x pair (d, d) with y values; H11: (v, v) with y derivatives;
+      // H01: (d, v) with y (value, derivative); the mass: (v, v) with y values
+      T h00 = 0, h11 = 0, h01 = 0, hm = 0;
+#pragma unroll
+      for (int a2 = 0; a2 < n; ++a2) {
+        T s00 = 0, s11 = 0, s01 = 0, sm = 0;
+#pragma unroll
+        for (int b2 = 0; b2 < n; ++b2) {
+          const int ab = a2 * n + b2;
+          if (doK) {
+            s00 += fy0[b2] * UX[0][ab];
+            s11 += fy1[b2] * UX[1][ab];
+            if (GEN) s01 += fy1[b2] * UX[2][ab];
+          }
+          if (doM) sm += fy0[b2] * UX[NP][ab];
+        }
+        h00 += fy0[a2] * s00;
+        h11 += fy1[a2] * s11;
+        h01 += fy0[a2] * s01;
+        hm += fy0[a2] * sm;
+      }
+      const int k = q1 + q * q2;
+      const double W = 0.5 * rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2];
+      if (GEN) {
+        const double* Gq = A.jac + (e * q * q + k) * 4;
+        const double g00 = Gq[0], g01 = Gq[1], g10 = Gq[2], g11 = Gq[3];
+        // cofactors c = [[g11, -g10], [-g01, g00]]; w |det| (G^{-1} G^{-T})_ij
+        // = (w / |det|) sum_m c_mi c_mj
+        const double adet = fabs(g00 * g11 - g01 * g10);
+        const double wk = W / adet;
+        const double d00 = wk * (g11 * g11 + g01 * g01);
+        const double d11 = wk * (g10 * g10 + g00 * g00);
+        const double d01 = wk * (-g11 * g10 - g01 * g00);
+        if (doK)
+          ((T*)A.grad_kappa)[e * q * q + k] = (T)d00 * h00 + (T)d11 * h11 + (T)(2.0 * d01) * h01;
+        if (doM) ((T*)A.grad_rho)[e * q * q + k] = (T)(W * adet) * hm;
+      } else {
+        if (doK) ((T*)A.grad_kappa)[e * q * q + k] = (T)W * (h00 + h11);
+        if (doM) ((T*)A.grad_rho)[e * q * q + k] = (T)W * hm;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P, int QG, bool GEN>
+cudaError_t run2(const GradArgs& a, cudaStream_t st) {
+  k_grad2<T, P, QG, GEN><<<(unsigned)a.n_elem, 64, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int P, int QG, bool GEN>
 cudaError_t run1(GradArgs a, cudaStream_t st) {
   using C = GRD<T, P, QG, GEN>;
@@ -379,26 +514,47 @@ cudaError_t run(const GradArgs& a, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t dispatch(const GradArgs& a, int p, int q, cudaStream_t st) {
+cudaError_t dispatch(const GradArgs& a, int dim, int p, int q, cudaStream_t st) {
   const int dq = q - p;
+  if (dim == 2) {
+    if constexpr (sizeof(T) == 8) {   // 2D plans are FP64 (the FP32 forms are 3D)
+#define C2(PP)                                                                             \
+  if (p == PP && dq == 1)                                                                  \
+    return a.jac ? run2<T, PP, PP + 1, true>(a, st) : run2<T, PP, PP + 1, false>(a, st);   \
+  if (p == PP && dq == 2)                                                                  \
+    return a.jac ? run2<T, PP, PP + 2, true>(a, st) : run2<T, PP, PP + 2, false>(a, st);
+      C2(1) C2(2) C2(3) C2(4) C2(5)
+#undef C2
+    }
+    return cudaErrorInvalidValue;
+  }
 #define C3(PP)                                               \
   if (p == PP && dq == 1) return run<T, PP, PP + 1>(a, st);  \
   if (p == PP && dq == 2) return run<T, PP, PP + 2>(a, st);
   C3(1) C3(2) C3(3)
-  if (p == 4 && dq == 1) return run<T, 4, 5>(a, st);
 #undef C3
+  if (p == 4 && dq == 1) return run<T, 4, 5>(a, st);
+  if (p == 4 && dq == 2) return run<T, 4, 6>(a, st);
+  if constexpr (sizeof(T) == 4) {
+    // the FP32 block of p = 5 (187.5 KB padded) fits one CTA; the FP64 one does not
+    if (p == 5 && dq == 1) return run<T, 5, 6>(a, st);
+  }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool grad_supported(int dim, int p, int q) {
-  return dim == 3 && p >= 1 && ((p <= 3 && (q == p + 1 || q == p + 2)) || (p == 4 && q == 5));
+bool grad_supported(int dim, int p, int q, bool fp64) {
+  const bool q_ok = q == p + 1 || q == p + 2;
+  if (dim == 2) return fp64 && p >= 1 && p <= 5 && q_ok;
+  if (dim != 3 || p < 1) return false;
+  if (p <= 4) return q_ok;
+  return p == 5 && q == 6 && !fp64;
 }
 
-cudaError_t launch_grad(const GradArgs& a, int p, int q, bool fp64, cudaStream_t st) {
+cudaError_t launch_grad(const GradArgs& a, int dim, int p, int q, bool fp64, cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
-  return fp64 ? dispatch<double>(a, p, q, st) : dispatch<float>(a, p, q, st);
+  return fp64 ? dispatch<double>(a, dim, p, q, st) : dispatch<float>(a, dim, p, q, st);
 }
 
 }  // namespace iga

@@ -188,9 +188,60 @@ def test_autograd_integrate(precision):
     plan.close()
 
 
+def _jac2d(n_qp, seed):
+    """Seeded non-symmetric 2x2 Jacobians with positive determinant."""
+    a = wl.normal(4 * n_qp, seed).reshape(n_qp, 2, 2)
+    return np.eye(2)[None] + 0.15 * a
+
+
+@pytest.mark.parametrize("curved", [False, True], ids=["identity", "curved"])
+@pytest.mark.parametrize("p,dq", [(1, 1), (2, 1), (2, 2), (3, 1), (4, 2), (5, 1)])
+def test_grad_2d_matches_oracle(p, dq, curved):
+    """2D (FP64 plans; the FP32 forms are 3D)."""
+    q = p + dq
+    knots = [wl.open_uniform_knots(4, p), _nonuniform_knots(p, 35 + p)]
+    P = oracle.Patch(knots, p, q)
+    G = _jac2d(P.E * P.Q, 1800 + p) if curved else None
+    GK = wl.normal(P.E * P.N * P.N, 1810 + p).reshape(P.E, P.N, P.N)
+    GM = wl.normal(P.E * P.N * P.N, 1820 + p).reshape(P.E, P.N, P.N)
+    rk, rr = P.integrate_grad(GK=GK, GM=GM, G=G)
+    rk, rr = rk.reshape(-1), rr.reshape(-1)
+    plan = IgaPlan(Patch(knots, p, q), method="sumfact", precision="fp64")
+    gk, gr = _grad(plan, GK, GM, G, torch.float64)
+    assert np.abs(gk - rk).max() <= 1e-12 * np.abs(rk).max()
+    assert np.abs(gr - rr).max() <= 1e-12 * np.abs(rr).max()
+    plan.close()
+
+
+@pytest.mark.parametrize("p,q,curved", [(4, 6, True), (5, 6, False), (5, 6, True)])
+def test_grad_high_degree(p, q, curved):
+    """3D p = 4 with q = 6 (FP64 and FP32) and p = 5 (FP32 only: the padded
+    FP64 block of 216 x 217 values exceeds shared memory)."""
+    knots = [wl.open_uniform_knots(K, p) for K in (2, 1, 2)]
+    P = oracle.Patch(knots, p, q)
+    G = wl.curved_map_jacobian(knots, q) if curved else None
+    GK = wl.normal(P.E * P.N * P.N, 1900 + p).reshape(P.E, P.N, P.N)
+    GM = wl.normal(P.E * P.N * P.N, 1910 + p).reshape(P.E, P.N, P.N)
+    rk, rr = P.integrate_grad(GK=GK, GM=GM, G=G)
+    rk, rr = rk.reshape(-1), rr.reshape(-1)
+    for pr, dt, tol in (("fp64", torch.float64, 1e-12), ("fp32", torch.float32, 1e-5)):
+        plan = IgaPlan(Patch(knots, p, q), method="sumfact", precision=pr)
+        if pr == "fp64" and p == 5:
+            g = torch.zeros(plan.info.n_mat_entries, dtype=dt, device=DEV)
+            with pytest.raises(capi.IgaError) as ei:
+                plan.integrate_grad(GK=g)
+            assert ei.value.code == capi.IGA_ERR_UNSUPPORTED
+            plan.close()
+            continue
+        gk, gr = _grad(plan, GK, GM, G, dt)
+        assert np.linalg.norm(gk - rk) <= tol * np.linalg.norm(rk)
+        assert np.linalg.norm(gr - rr) <= tol * np.linalg.norm(rr)
+        plan.close()
+
+
 def test_unsupported_and_bad_arguments():
-    t2 = wl.open_uniform_knots(3, 2)
-    plan2d = IgaPlan(Patch([t2] * 2, 2, 3), method="sumfact")
+    t2 = wl.open_uniform_knots(3, 6)
+    plan2d = IgaPlan(Patch([t2] * 2, 6, 7), method="sumfact")
     g = torch.zeros(plan2d.info.n_mat_entries, dtype=torch.float64, device=DEV)
     with pytest.raises(capi.IgaError) as ei:
         plan2d.integrate_grad(GK=g)
