@@ -7,7 +7,9 @@ one JSON line.  Used for profiling single kernels, e.g.
 Operations: integrate (element matrices), assemble (CSR values of the stiffness
 from its element matrices, integrated once before timing), apply (y = K x + M x),
 adjoint (J and dJ/dkappa) and grad (dL/dkappa, and dL/drho where the workload
-has a mass, from random upstream gradients of the element matrices).
+has a mass, from random upstream gradients of the element matrices), wq_mass and
+wq_stiffness (weighted-quadrature global matrices, lognormal coefficient on the
+point grid, FP64).
 """
 from __future__ import annotations
 
@@ -26,7 +28,8 @@ L2_FLUSH_BYTES = 2 * 129 * 1024 * 1024
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="integrate", choices=["integrate", "assemble", "apply", "adjoint", "grad"])
+    ap.add_argument("--op", default="integrate", choices=["integrate", "assemble", "apply", "adjoint", "grad", "wq_mass",
+                                                 "wq_stiffness"])
     ap.add_argument("--workload", default="3d_p3_16")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_df", "fp32", "bf16"])
     ap.add_argument("--method", default="sumfact", choices=["sumfact", "classical"])
@@ -63,6 +66,14 @@ def main(argv=None):
 
         def step():
             plan.apply(x, kappa=kappa, jac=jac, alpha=1.0, beta=1.0, y=y, stream=stream)
+    elif args.op in ("wq_mass", "wq_stiffness"):
+        del K, M, D
+        c = torch.as_tensor(wl.lognormal(plan.wq_grid_size(0), wl.SEED_ADJ_U), device=dev)
+        vals = torch.empty(plan.n_csr_nnz, dtype=torch.float64, device=dev)
+        fn = plan.wq_mass if args.op == "wq_mass" else plan.wq_stiffness
+
+        def step():
+            fn(c=c, values=vals, stream=stream)
     elif args.op == "grad":
         del D
         gen = torch.Generator(device=dev).manual_seed(wl.SEED_ADJ_U)

@@ -176,6 +176,7 @@ WORKLOADS = {
     "3d_p3_20": Workload("3d_p3_20", PatchSpec(3, 3, 20, 4), SEED_KAPPA_P3),
     # the largest degree class of the 64-patch batch, alone
     "3d_p5_16": Workload("3d_p5_16", PatchSpec(3, 5, 16, 6), SEED_BATCH_KAPPA),
+    "3d_p5_10": Workload("3d_p5_10", PatchSpec(3, 5, 10, 6), SEED_BATCH_KAPPA),
     "3d_p4_16": Workload("3d_p4_16", PatchSpec(3, 4, 16, 5), SEED_BATCH_KAPPA),
     "3d_p4_24_curved": Workload("3d_p4_24_curved", PatchSpec(3, 4, 24, 5), SEED_KAPPA_P4, curved=True),
 }
