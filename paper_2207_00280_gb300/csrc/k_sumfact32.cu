@@ -376,31 +376,26 @@ __device__ __forceinline__ int stage_offset(const float* g) {
   return (4 - head) & 3;
 }
 
-// Copy one staged element matrix (N*N floats) to HBM: scalar head up to a
-// 16-byte boundary of the destination, 16-byte loads and stores, scalar tail.
-template <int NN, int NT>
-__device__ __forceinline__ void copy_out(const float* __restrict__ s, float* __restrict__ g) {
-  const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
-  const int h = head < NN ? head : NN;
-  for (int i = threadIdx.x; i < h; i += NT) g[i] = s[i];
-  const int nv = (NN - h) / 4;
-  float4* g4 = (float4*)(g + h);
-  const float4* s4 = (const float4*)(s + h);
-  for (int i = threadIdx.x; i < nv; i += NT) g4[i] = s4[i];
-  for (int i = h + 4 * nv + threadIdx.x; i < NN; i += NT) g[i] = s[i];
-}
-
-// copy_out with a run-time count (a row block of the staged matrix).
+// Copy nn floats of a staged element matrix (or row block) to HBM: the
+// 16-byte-aligned middle by one bulk asynchronous copy (the untiled form of
+// the tensor memory accelerator, issued by thread 0; the callers fence the
+// staging writes to the async proxy before their barrier), the scalar head
+// and tail by the threads.  Returns once the copy has read shared memory, so
+// the caller's next barrier releases the buffer.
 template <int NT>
-__device__ __forceinline__ void copy_out_n(const float* __restrict__ s, float* __restrict__ g, int nn) {
+__device__ __forceinline__ void copy_out_bulk(const float* __restrict__ s, float* __restrict__ g,
+                                              int nn) {
   const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
   const int h = head < nn ? head : nn;
-  for (int i = threadIdx.x; i < h; i += NT) g[i] = s[i];
   const int nv = (nn - h) / 4;
-  float4* g4 = (float4*)(g + h);
-  const float4* s4 = (const float4*)(s + h);
-  for (int i = threadIdx.x; i < nv; i += NT) g4[i] = s4[i];
+  for (int i = threadIdx.x; i < h; i += NT) g[i] = s[i];
   for (int i = h + 4 * nv + threadIdx.x; i < nn; i += NT) g[i] = s[i];
+  if (threadIdx.x == 0 && nv > 0) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+                 ::"l"(g + h), "r"(smem_u32(s + h)), "r"(nv * 16) : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+  }
 }
 
 // Once per CTA, before its first element: the table of symmetric pairs
@@ -998,8 +993,9 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
               }
           }
         }
+        fence_proxy_async_smem();
         __syncthreads();
-        copy_out<N * N, NT>(stage, g);
+        copy_out_bulk<NT>(stage, g, N * N);
         __syncthreads();
       }
     }
@@ -1023,8 +1019,9 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
       if (isK) gemm_sym<C, C::LDA, C::LDB, C::KA / C::KSTEP>(AK, BK, pairs, stage, g, r0, r1);
       else gemm_sym<C, C::LDAM, C::LDBM, C::KAM / C::KSTEP>(AM, BM, pairs, stage, g, r0, r1);
       if (C::STAGE) {
+        fence_proxy_async_smem();
         __syncthreads();
-        copy_out_n<NT>(stage, gb, (r1 - r0) * N);
+        copy_out_bulk<NT>(stage, gb, (r1 - r0) * N);
         __syncthreads();
       }
     }
