@@ -54,7 +54,11 @@ struct SF3F {
   static constexpr int NS1 = n * (n + 1) / 2;
   static constexpr int Np = n2;
   static constexpr int NSp = Np * (Np + 1) / 2;
-  static constexpr int NT = 256;
+  // threads per CTA: one CTA per SM at p = 5 (its operands and row block fill
+  // shared memory), so there 16 warps instead of 8 hide the latency of the
+  // dependent stages (identity geometry; the general-map variants need more
+  // than the 128 registers a 512-thread CTA allows)
+  static constexpr int NT = (P >= 5 && !GEN) ? 512 : 256;
   static constexpr int REC = 2 * q * n + q;
   static constexpr size_t al4(size_t x) { return (x + 3) / 4 * 4; }
   static constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
@@ -1030,7 +1034,7 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
 }
 
 template <int P, int QG, bool GEN, int MODE, bool BF>
-__global__ void __launch_bounds__(256) k_sf3_f32(const ElemArgs A) {
+__global__ void __launch_bounds__(SF3F<P, QG, GEN, MODE, BF>::NT) k_sf3_f32(const ElemArgs A) {
   extern __shared__ __align__(16) float smf[];
   sf3_f32_cta_setup<P, QG, GEN, MODE, BF>(smf);
   uint32_t phase = 0;
@@ -1045,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_sf3_f32(const ElemArgs A) {
 // time budget, a CTA stops popping once the budget since its start has passed
 // and records IGA_ERR_TIMEOUT; no CTA ever waits on another.
 template <int P, int QG, bool GEN, int MODE, bool BF>
-__global__ void __launch_bounds__(256) k_sf3_f32_queue(const QueueArgs B) {
+__global__ void __launch_bounds__(SF3F<P, QG, GEN, MODE, BF>::NT) k_sf3_f32_queue(const QueueArgs B) {
   extern __shared__ __align__(16) float smf[];
   __shared__ int s_item;
   const unsigned long long t0 = global_timer_ns();
