@@ -41,6 +41,10 @@ def _patch_sets():
         "3d_p2_nonuniform": [([_nonuniform_knots(2, 4), wl.open_uniform_knots(3, 2),
                                _nonuniform_knots(2, 5)], 2)],
         "3d_p5": [([wl.open_uniform_knots(3, 5)] * 3, 5)],
+        # a C0 line (interior knot of multiplicity p), one element in y, a double knot in z
+        "3d_p3_c0_one_element": [([np.array([0.0] * 4 + [0.3, 0.3, 0.3, 0.6] + [1.0] * 4),
+                                   wl.open_uniform_knots(1, 3),
+                                   np.array([0.0] * 4 + [0.5, 0.5] + [1.0] * 4)], 3)],
         "3d_batch": [([wl.open_uniform_knots(3, 1)] * 3, 1),
                      ([wl.open_uniform_knots(4, 3), wl.open_uniform_knots(3, 3),
                        wl.open_uniform_knots(5, 3)], 3),
@@ -160,6 +164,9 @@ def _apply_cases():
                                   _nonuniform_knots(2, 9)], 2, True),
         ("uniform_p4", [wl.open_uniform_knots(3, 4)] * 3, 4, False),
         ("uniform_p5_curved", [wl.open_uniform_knots(2, 5)] * 3, 5, True),
+        ("c0_one_element_p3_curved", [np.array([0.0] * 4 + [0.3, 0.3, 0.3, 0.6] + [1.0] * 4),
+                                      wl.open_uniform_knots(1, 3),
+                                      np.array([0.0] * 4 + [0.5, 0.5] + [1.0] * 4)], 3, True),
     ]
 
 

@@ -44,6 +44,9 @@ def _cases():
         ("p3_q5", [wl.open_uniform_knots(2, 3), _nonuniform_knots(3, 33), wl.open_uniform_knots(2, 3)],
          3, 5),
         ("p4_q5", [wl.open_uniform_knots(K, 4) for K in (2, 2, 3)], 4, 5),
+        ("p3_c0_one_element", [np.array([0.0] * 4 + [0.3, 0.3, 0.3, 0.6] + [1.0] * 4),
+                               wl.open_uniform_knots(1, 3),
+                               np.array([0.0] * 4 + [0.5, 0.5] + [1.0] * 4)], 3, 4),
     ]
 
 

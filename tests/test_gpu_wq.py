@@ -34,6 +34,11 @@ def _cases():
         ("p2_mixed", [wl.open_uniform_knots(4, 2), _nonuniform_knots(2, 61), wl.open_uniform_knots(3, 2)], 2),
         ("p3_uniform", [wl.open_uniform_knots(6, 3)] * 3, 3),
         ("p4_uniform", [wl.open_uniform_knots(3, 4), wl.open_uniform_knots(9, 4), wl.open_uniform_knots(2, 4)], 4),
+        # a C0 line (multiplicity p: B' jumps there and is taken from the right on both
+        # sides), one element in y, a double knot in z
+        ("p3_c0_one_element", [np.array([0.0] * 4 + [0.3, 0.3, 0.3, 0.6] + [1.0] * 4),
+                               wl.open_uniform_knots(1, 3),
+                               np.array([0.0] * 4 + [0.5, 0.5] + [1.0] * 4)], 3),
     ]
 
 
