@@ -705,15 +705,15 @@ def grad_flops_per_element(p, q):
 
 def measure_grad(W, stream, flush, dev):
     """Backward of the 32^3 p=3 element matrices (dL/dkappa and dL/drho from
-    dL/dK_e and dL/dM_e), FP64 and FP32: bytes = both upstream blocks read and
-    both gradients written."""
+    dL/dK_e and dL/dM_e), FP64, float-float (FP64_DF plan) and FP32: bytes =
+    both upstream blocks read and both gradients written."""
     import torch
     from paper_2207_00280_gb300.plan import IgaPlan, Patch
     sp = W.spec
     peaks = measured_peaks()[0]
     f_el = grad_flops_per_element(sp.p, sp.q)
     out = {"elements": sp.E, "flop_per_element": f_el}
-    for pr in ("fp64", "fp32"):
+    for pr in ("fp64", "fp64_df", "fp32"):
         pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="sumfact", precision=pr, blocking=False)
         dt = pl.out_dtype
         gen = torch.Generator(device=dev).manual_seed(20220701)
@@ -723,7 +723,7 @@ def measure_grad(W, stream, flush, dev):
         gr = torch.empty(pl.n_qp, dtype=dt, device=dev)
         ms = _time_steps(lambda: pl.integrate_grad(GK=GK, GM=GM, grad_kappa=gk, grad_rho=gr,
                                                    stream=stream), 10, stream, flush)
-        esz = 8 if pr == "fp64" else 4
+        esz = 4 if pr == "fp32" else 8
         bytes_ = 2 * (GK.numel() + pl.n_qp) * esz
         ent = {"ms_per_step": round(ms, 4), "elements_per_s": round(sp.E / (ms * 1e-3), 1),
                "gflops": round(f_el * sp.E / (ms * 1e-3) / 1e9, 1),

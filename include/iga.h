@@ -33,9 +33,11 @@
  *             IGA_FP64_DF, float for IGA_FP32 and IGA_BF16;
  *   dof_out:  per patch [E][N] int32, concatenated (iga_plan_info.dofmap_offset).
  *
- * Ownership: every pointer passed to iga_integrate/iga_integrate_backward is
+ * Ownership: every array pointer passed to an entry point below (except the
+ * host knot vectors of iga_patch_desc and the host x_out of iga_wq_points) is
  * owned by the caller and must be device memory of the device that was
- * current at iga_plan (no copies are made).  The plan owns its device tables
+ * current at iga_plan (no copies are made; some kernels write their outputs
+ * with bulk asynchronous copies, which need device memory).  The plan owns its device tables
  * and the arrays that iga_plan_info points to; iga_destroy frees them.
  *
  * Errors: argument and knot errors are returned synchronously and nothing is

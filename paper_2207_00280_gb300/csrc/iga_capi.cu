@@ -806,7 +806,7 @@ extern "C" int iga_integrate_grad(iga_plan_t P, const double* jac, const void* G
     a.GM = GM ? (const char*)GM + esz * pd.mat_offset : nullptr;
     a.grad_kappa = GK ? (char*)grad_kappa + esz * pd.qp_offset : nullptr;
     a.grad_rho = GM ? (char*)grad_rho + esz * pd.qp_offset : nullptr;
-    e = launch_grad(a, pd.dim, pd.p, pd.q, fp64, st);
+    e = launch_grad(a, pd.dim, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
   }
   return finish(P, st, e);
 }

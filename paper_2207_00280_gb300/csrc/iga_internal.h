@@ -200,7 +200,9 @@ struct GradArgs {
   void* grad_rho;        // [E][Q]
   bool two_buffers;      // set by the launcher
 };
-cudaError_t launch_grad(const GradArgs& a, int dim, int p, int q, bool fp64, cudaStream_t st);
+// fp64: double arrays; df (with fp64): float-float arithmetic where supported
+cudaError_t launch_grad(const GradArgs& a, int dim, int p, int q, bool fp64, bool df,
+                        cudaStream_t st);
 bool grad_supported(int dim, int p, int q, bool fp64);
 
 // ---- weighted quadrature (mass matrix, 3D, FP64) -------------------------------

@@ -34,11 +34,96 @@ namespace {
 __host__ __device__ constexpr int term_i(int t) { return t < 3 ? t : (t == 5 ? 1 : 0); }
 __host__ __device__ constexpr int term_j(int t) { return t < 3 ? t : (t == 3 ? 1 : 2); }
 
+// Float-float values (IGA_FP64_DF plans): hi + lo, two FP32 numbers, about 48
+// significant bits; products by the exact FMA error term (Dekker/Kahan),
+// sums by Knuth's two-sum, renormalised.  Every multiply-add runs on the FP32
+// pipes.  The upstream blocks stay double in shared memory and are split into
+// hi + lo with integer instructions (the FP64 pipe would otherwise bound it).
+struct ff {
+  float hi, lo;
+  ff() = default;
+  __device__ __forceinline__ ff(int v) : hi((float)v), lo(0.f) {}
+  __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit ff(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+};
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = p + e;
+  return ff(s, e - (s - p));
+}
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);
+  const float l = err + a.lo + b.lo;
+  const float h = s + l;
+  return ff(h, l - (h - s));
+}
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) {
+  a = a + b;
+  return a;
+}
+
+// x as hi + lo without FP64 arithmetic: hi = x with its mantissa cut to 24
+// bits (exact in FP32 within its exponent range), lo = the remaining 29 bits
+// as an integer, converted (rounded to 24 bits) and scaled by 2^(e - 1075).
+// Zeros and values outside the FP32 exponent range take the FP64 path.
+__device__ __forceinline__ ff split_d(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex < 897 || ex > 1150) return ff(x);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned mh = (unsigned)((b >> 29) & 0x7fffffu);
+  const float h = __uint_as_float(sgn | ((unsigned)(ex - 896) << 23) | mh);
+  const unsigned ml = (unsigned)(b & 0x1fffffffu);
+  const int sx = ex - 1075 + 127;   // biased exponent of 2^(e - 1075)
+  float l = sx >= 1 ? __uint2float_rn(ml) * __uint_as_float((unsigned)sx << 23) : 0.f;
+  if (sgn) l = -l;
+  return ff(h, l);
+}
+
+// Dot products: mac(a, x, y) accumulates x * y into a; fin(a) is the value.
+// For ff the accumulator keeps the exact two-sum of the high products in hi
+// and every low-order term in lo, renormalised once by fin, so the
+// loop-carried dependence is one FP32 add.
+template <typename T> __device__ __forceinline__ void mac(T& a, T x, T y) { a += x * y; }
+template <typename T> __device__ __forceinline__ T fin(T a) { return a; }
+template <> __device__ __forceinline__ void mac<ff>(ff& a, ff x, ff y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  const float s = a.hi + p;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (p - bb);
+  a.hi = s;
+  a.lo += err + e;
+}
+template <> __device__ __forceinline__ ff fin<ff>(ff a) {
+  const float h = a.hi + a.lo;
+  return ff(h, a.lo - (h - a.hi));
+}
+
+template <typename T> struct store_of { using type = T; };
+template <> struct store_of<ff> { using type = double; };
+template <typename T> using store_t = typename store_of<T>::type;
+
+template <typename T> __device__ __forceinline__ T to_compute(store_t<T> x) { return x; }
+template <> __device__ __forceinline__ ff to_compute<ff>(double x) { return split_d(x); }
+template <typename T> __device__ __forceinline__ store_t<T> to_store(T x) { return x; }
+template <> __device__ __forceinline__ double to_store<ff>(ff x) { return (double)x.hi + (double)x.lo; }
+
 template <typename T, int P, int QG, bool GEN>
 struct GRD {
   static constexpr int n = P + 1, q = QG, n2 = n * n, n4 = n2 * n2, N = n2 * n, Q = q * q * q;
   static constexpr int GS = N + 1;               // padded row stride of the staged block
-  static constexpr size_t dyn_bytes = sizeof(T) * (size_t)N * GS;   // one block
+  static constexpr size_t dyn_bytes = sizeof(store_t<T>) * (size_t)N * GS;   // one block
   // room for both upstream blocks (the mass block loads during the stiffness pass)
   // (FP32 only: the FP64 kernel is bound by its pipe and wants more CTAs per SM)
   static constexpr bool TWO = sizeof(T) == 4 && 2 * dyn_bytes <= 80 * 1024;
@@ -91,7 +176,8 @@ __device__ __forceinline__ void wait_blocks() {
 
 // One upstream matrix: MASS = GM -> grad_rho, else GK -> grad_kappa.
 template <typename T, int P, int QG, bool GEN, bool MASS>
-__device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __restrict__ out, T* G, const T (*f)[2][QG * (P + 1)],
+__device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, store_t<T>* __restrict__ out,
+                                          store_t<T>* G, const T (*f)[2][QG * (P + 1)],
                                           const double* rec, const T* wts, const unsigned char* tri3,
                                           T* UX, T* UY, T* HZ) {
   using C = GRD<T, P, QG, GEN>;
@@ -105,11 +191,11 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
   // The caller has waited for this pass's block and synchronized.  S = G + G^T
   // (twice the symmetric part; the 1/2 goes into the weights): formed while
   // loading the register blocks, else in place.
-  if (!HOLD) {
+  if constexpr (!HOLD) {
     for (int idx = tid; idx < N * N; idx += NT) {
       const int a = idx / N, b = idx - a * N;
       if (a <= b) {
-        const T s = G[a * GS + b] + G[b * GS + a];
+        const store_t<T> s = G[a * GS + b] + G[b * GS + a];
         G[a * GS + b] = s;
         G[b * GS + a] = s;
       }
@@ -136,7 +222,8 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
 #pragma unroll
         for (int b1 = 0; b1 < n; ++b1)
           Gr[HOLD ? k : 0][HOLD ? a1 * n + b1 : 0] =
-              G[(a1 + n * ia[k]) * GS + n * ib[k] + b1] + G[(b1 + n * ib[k]) * GS + n * ia[k] + a1];
+              to_compute<T>(G[(a1 + n * ia[k]) * GS + n * ib[k] + b1]) +
+              to_compute<T>(G[(b1 + n * ib[k]) * GS + n * ia[k] + a1]);
     }
   }
 #pragma unroll 1
@@ -154,26 +241,31 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
         T s0 = 0, s1 = 0;
 #pragma unroll
         for (int b1 = 0; b1 < n; ++b1) {
-          const T g = HOLD ? Gr[HOLD ? k : 0][HOLD ? a1 * n + b1 : 0]
-                           : G[(a1 + n * a23) * GS + n * b23 + b1];
-          s0 += g * fx0[b1];
-          if (!MASS) s1 += g * fx1[b1];
+          T g;
+          if constexpr (HOLD) g = Gr[k][a1 * n + b1];
+          else g = to_compute<T>(G[(a1 + n * a23) * GS + n * b23 + b1]);
+          mac(s0, g, fx0[b1]);
+          if (!MASS) mac(s1, g, fx1[b1]);
         }
-        v0[a1] = s0;
-        v1[a1] = s1;
+        v0[a1] = fin(s0);
+        v1[a1] = fin(s1);
       }
       T p00 = 0, p11 = 0, p10 = 0, p01 = 0;
 #pragma unroll
       for (int a1 = 0; a1 < n; ++a1) {
-        p00 += fx0[a1] * v0[a1];
+        mac(p00, fx0[a1], v0[a1]);
         if (!MASS) {
-          p11 += fx1[a1] * v1[a1];
+          mac(p11, fx1[a1], v1[a1]);
           if (GEN) {
-            p10 += fx1[a1] * v0[a1];
-            if (TRI) p01 += fx0[a1] * v1[a1];
+            mac(p10, fx1[a1], v0[a1]);
+            if (TRI) mac(p01, fx0[a1], v1[a1]);
           }
         }
       }
+      p00 = fin(p00);
+      p11 = fin(p11);
+      p10 = fin(p10);
+      p01 = fin(p01);
       const int u = a23 * n2 + b23, l = b23 * n2 + a23;
       if (MASS) {
         UX[u] = p00;
@@ -229,9 +321,10 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
       for (int a2 = 0; a2 < n; ++a2) {
         T s0 = 0;
 #pragma unroll
-        for (int b2 = 0; b2 < n; ++b2) s0 += fb[b2] * U[(a2 + n * a3) * n2 + b2 + n * b3];
-        acc += fa[a2] * s0;
+        for (int b2 = 0; b2 < n; ++b2) mac(s0, fb[b2], U[(a2 + n * a3) * n2 + b2 + n * b3]);
+        mac(acc, fa[a2], fin(s0));
       }
+      acc = fin(acc);
       UY[(term * n2 + a3 * n + b3) * q + q2] = acc;
       if (mirror) UY[(term * n2 + b3 * n + a3) * q + q2] = acc;
     }
@@ -252,10 +345,10 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
       for (int a3 = 0; a3 < n; ++a3) {
         T s0 = 0;
 #pragma unroll
-        for (int b3 = 0; b3 < n; ++b3) s0 += fb[b3] * U[(a3 * n + b3) * q];
-        acc += fa[a3] * s0;
+        for (int b3 = 0; b3 < n; ++b3) mac(s0, fb[b3], U[(a3 * n + b3) * q]);
+        mac(acc, fa[a3], fin(s0));
       }
-      HZ[term * q * q + r] = acc;
+      HZ[term * q * q + r] = fin(acc);
     }
     __syncthreads();
     // geometry at the q^2 points of this slice
@@ -284,15 +377,16 @@ __device__ __forceinline__ void grad_pass(const GradArgs& A, int64_t e, T* __res
             const int i = term_i(term), j = term_j(term);
             const double d = (term < 3 ? wk : 2.0 * wk) *
                              (c[0][i] * c[0][j] + c[1][i] * c[1][j] + c[2][i] * c[2][j]);
-            g += (T)d * HZ[term * q * q + it];
+            mac(g, (T)d, HZ[term * q * q + it]);
           }
+          g = fin(g);
         }
       } else {
         // identity map: the weight in the kernel's precision
         const T Wt = (T)0.5 * wts[q1] * wts[q + q2] * wts[2 * q + q3];
         g = MASS ? Wt * HZ[it] : Wt * (HZ[it] + HZ[q * q + it] + HZ[2 * q * q + it]);
       }
-      out[e * Q + k] = g;
+      out[e * Q + k] = to_store<T>(g);
     }
   }
 }
@@ -309,7 +403,8 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   __shared__ T HZ[C::NTY * q * q];
   __shared__ unsigned char tri3[C::T3];   // (a3 << 4 | b3) of the (a3 <= b3) triangle
   __shared__ T wts[3 * q];                // Gauss weights per direction
-  T* G = reinterpret_cast<T*>(grad_dyn);
+  using S = store_t<T>;
+  S* G = reinterpret_cast<S*>(grad_dyn);
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
   const int e1 = (int)(e % A.K1);
@@ -335,21 +430,21 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   // both blocks in flight at once when the launch gave two buffers
   constexpr int64_t NN = (int64_t)C::N * C::N;
   const bool two = A.GK && A.GM && A.two_buffers;
-  T* G1 = two ? G + C::N * C::GS : G;
-  if (A.GK) issue_block<T, C::N, C::GS, NT>((const T*)A.GK + e * NN, G);
-  if (A.GM && (two || !A.GK)) issue_block<T, C::N, C::GS, NT>((const T*)A.GM + e * NN, G1);
+  S* G1 = two ? G + C::N * C::GS : G;
+  if (A.GK) issue_block<S, C::N, C::GS, NT>((const S*)A.GK + e * NN, G);
+  if (A.GM && (two || !A.GK)) issue_block<S, C::N, C::GS, NT>((const S*)A.GM + e * NN, G1);
   if (A.GK) {
     if (two) wait_blocks<1>();
     else wait_blocks<0>();
-    grad_pass<T, P, QG, GEN, false>(A, e, (T*)A.grad_kappa, G, f, rec, wts, tri3, UX, UY, HZ);
+    grad_pass<T, P, QG, GEN, false>(A, e, (S*)A.grad_kappa, G, f, rec, wts, tri3, UX, UY, HZ);
   }
   if (A.GM) {
     if (A.GK && !two) {
       __syncthreads();   // the stiffness pass is done with the buffer
-      issue_block<T, C::N, C::GS, NT>((const T*)A.GM + e * NN, G1);
+      issue_block<S, C::N, C::GS, NT>((const S*)A.GM + e * NN, G1);
     }
     wait_blocks<0>();
-    grad_pass<T, P, QG, GEN, true>(A, e, (T*)A.grad_rho, G1, f, rec, wts, tri3, UX, UY, HZ);
+    grad_pass<T, P, QG, GEN, true>(A, e, (S*)A.grad_rho, G1, f, rec, wts, tri3, UX, UY, HZ);
   }
 }
 
@@ -542,6 +637,16 @@ cudaError_t dispatch(const GradArgs& a, int dim, int p, int q, cudaStream_t st) 
   return cudaErrorInvalidValue;
 }
 
+cudaError_t dispatch_ff(const GradArgs& a, int p, int q, cudaStream_t st) {
+  const int dq = q - p;
+#define CF(PP)                                                \
+  if (p == PP && dq == 1) return run<ff, PP, PP + 1>(a, st);  \
+  if (p == PP && dq == 2) return run<ff, PP, PP + 2>(a, st);
+  CF(1) CF(2) CF(3)
+#undef CF
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 bool grad_supported(int dim, int p, int q, bool fp64) {
@@ -552,8 +657,11 @@ bool grad_supported(int dim, int p, int q, bool fp64) {
   return p == 5 && q == 6 && !fp64;
 }
 
-cudaError_t launch_grad(const GradArgs& a, int dim, int p, int q, bool fp64, cudaStream_t st) {
+cudaError_t launch_grad(const GradArgs& a, int dim, int p, int q, bool fp64, bool df,
+                        cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
+  // float-float where the blocks stay in registers (3D p <= 3), else FP64
+  if (df && dim == 3 && p <= 3) return dispatch_ff(a, p, q, st);
   return fp64 ? dispatch<double>(a, dim, p, q, st) : dispatch<float>(a, dim, p, q, st);
 }
 
