@@ -660,7 +660,8 @@ def apply_flops_per_element(p, q):
 
 
 def measure_apply(A, kappa, stream, flush, dev):
-    """Matrix-free y = K(kappa) x + M x on the 40^3 p=3 workload, FP64 and FP32."""
+    """Matrix-free y = K(kappa) x + M x on the 40^3 p=3 workload, FP64, float-float
+    (FP64_DF plan) and FP32."""
     import torch
     from paper_2207_00280_gb300 import workloads as wl
     from paper_2207_00280_gb300.plan import IgaPlan, Patch
@@ -668,13 +669,13 @@ def measure_apply(A, kappa, stream, flush, dev):
     peaks = measured_peaks()[0]
     f_el = apply_flops_per_element(sa.p, sa.q)
     out = {"elements": sa.E, "dofs": sa.n_dofs, "flop_per_element": f_el}
-    for pr, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+    for pr, dt in (("fp64", torch.float64), ("fp64_df", torch.float64), ("fp32", torch.float32)):
         pl = IgaPlan(Patch(sa.knots, sa.p, sa.q), method="sumfact", precision=pr, blocking=False)
         x = torch.as_tensor(wl.normal(sa.n_dofs, wl.SEED_ADJ_U), device=dev, dtype=dt)
         y = torch.empty_like(x)
         ms = _time_steps(lambda: pl.apply(x, kappa=kappa, alpha=1.0, beta=1.0, y=y, stream=stream),
                          10, stream, flush)
-        esz = 8 if pr == "fp64" else 4
+        esz = 4 if pr == "fp32" else 8
         # kappa, the per-element results written and read back, x gathered, y written
         bytes_ = sa.E * sa.Q * 8 + 2 * sa.E * (sa.p + 1) ** 3 * esz + 2 * sa.n_dofs * esz
         ent = {"ms_per_step": round(ms, 4), "elements_per_s": round(sa.E / (ms * 1e-3), 1),

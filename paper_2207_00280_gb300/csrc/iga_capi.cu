@@ -889,7 +889,7 @@ extern "C" int iga_apply(iga_plan_t P, const double* kappa, const double* rho, c
     a.x = x;
     a.alpha = alpha; a.beta = beta;
     a.scratch = (char*)P->d_apply_scratch + esz * pd.dofmap_offset;
-    e = launch_apply(a, pd.p, pd.q, fp64, st);
+    e = launch_apply(a, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
     if (e == cudaSuccess)
       e = launch_apply_gather(P->csr[ip], P->d_fc, P->d_spans, a.scratch, y, fp64, st);
   }

@@ -180,7 +180,7 @@ struct ApplyArgs {
   double alpha, beta;
   void* scratch;         // patch-local [N][E], double or float
 };
-cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, cudaStream_t st);
+cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st);
 cudaError_t launch_apply_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
                                 const void* scratch, void* y, bool fp64, cudaStream_t st);
 bool apply_supported(int dim, int p, int q);

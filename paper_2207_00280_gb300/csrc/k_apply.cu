@@ -13,7 +13,9 @@
 // The element result goes to scratch[a * E + e]; k_apply_gather then sums the
 // contributions of every dof in ascending element order (deterministic, no
 // atomics).  T = double is FP64 throughout; T = float keeps the Jacobian
-// cofactors and determinant in FP64 and the rest in FP32.
+// cofactors and determinant in FP64 and the rest in FP32; T = ff (FP64_DF
+// plans) is float-float on the FP32 pipes with double inputs and results.
+#include "ff.cuh"
 #include "iga_internal.h"
 
 namespace iga {
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
     const int a1 = a % n, a2 = (a / n) % n, a3 = a / n2;
     const int64_t g =
         A.dof_offset + (s1 + a1) + (int64_t)A.nf0 * ((s2 + a2) + (int64_t)A.nf1 * (s3 + a3));
-    xe[a] = ((const T*)A.x)[g];
+    xe[a] = to_compute<T>(((const store_t<T>*)A.x)[g]);
   }
   __syncthreads();
   for (int i = tid; i < 3 * 2 * q * n; i += NT) {
@@ -67,8 +69,8 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
     const T* B = &tb[0][s][q1 * n];
     T acc = 0;
 #pragma unroll
-    for (int a1 = 0; a1 < n; ++a1) acc += xe[a1 + n * a23] * B[a1];
-    U1[s][r] = acc;
+    for (int a1 = 0; a1 < n; ++a1) mac(acc, xe[a1 + n * a23], B[a1]);
+    U1[s][r] = fin(acc);
   }
   __syncthreads();
   // a2: U2[c][a3][q1 q2], c = vv (x value, y value), dv (x der), vd (y der)
@@ -79,8 +81,8 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
     const T* B = &tb[1][c == 2 ? 1 : 0][q2 * n];
     T acc = 0;
 #pragma unroll
-    for (int a2 = 0; a2 < n; ++a2) acc += U[(a2 + n * a3) * q + q1] * B[a2];
-    U2[c][r] = acc;
+    for (int a2 = 0; a2 < n; ++a2) mac(acc, U[(a2 + n * a3) * q + q1], B[a2]);
+    U2[c][r] = fin(acc);
   }
   __syncthreads();
   // a3 at every quadrature point, then the flux
@@ -92,11 +94,15 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
     for (int a3 = 0; a3 < n; ++a3) {
       const T vz = tb[2][0][q3 * n + a3], dz = tb[2][1][q3 * n + a3];
       const int o = a3 * q * q + qq;
-      g0 += U2[1][o] * vz;
-      g1 += U2[2][o] * vz;
-      g2 += U2[0][o] * dz;
-      u += U2[0][o] * vz;
+      mac(g0, U2[1][o], vz);
+      mac(g1, U2[2][o], vz);
+      mac(g2, U2[0][o], dz);
+      mac(u, U2[0][o], vz);
     }
+    g0 = fin(g0);
+    g1 = fin(g1);
+    g2 = fin(g2);
+    u = fin(u);
     const double wq = rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2] * rec[2 * REC + 2 * q * n + q3];
     const double kap = A.kappa ? A.kappa[e * Q + k] : 1.0;
     const double rh = A.rho ? A.rho[e * Q + k] : 1.0;
@@ -112,20 +118,23 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
       const double c20 = g01 * g12 - g02 * g11, c21 = g02 * g10 - g00 * g12, c22 = g00 * g11 - g01 * g10;
       const double det = g00 * c00 + g01 * c01 + g02 * c02;
       const double adet = fabs(det);
-      const T sK = (T)(A.alpha * wq * kap / adet);
-      const T h0 = (T)c00 * g0 + (T)c01 * g1 + (T)c02 * g2;
-      const T h1 = (T)c10 * g0 + (T)c11 * g1 + (T)c12 * g2;
-      const T h2 = (T)c20 * g0 + (T)c21 * g1 + (T)c22 * g2;
-      f0 = sK * ((T)c00 * h0 + (T)c10 * h1 + (T)c20 * h2);
-      f1 = sK * ((T)c01 * h0 + (T)c11 * h1 + (T)c21 * h2);
-      f2 = sK * ((T)c02 * h0 + (T)c12 * h1 + (T)c22 * h2);
-      m = (T)(A.beta * wq * adet * rh) * u;
+      const T sK = from_double<T>(A.alpha * wq * kap / adet);
+      const T C00 = from_double<T>(c00), C01 = from_double<T>(c01), C02 = from_double<T>(c02);
+      const T C10 = from_double<T>(c10), C11 = from_double<T>(c11), C12 = from_double<T>(c12);
+      const T C20 = from_double<T>(c20), C21 = from_double<T>(c21), C22 = from_double<T>(c22);
+      const T h0 = C00 * g0 + C01 * g1 + C02 * g2;
+      const T h1 = C10 * g0 + C11 * g1 + C12 * g2;
+      const T h2 = C20 * g0 + C21 * g1 + C22 * g2;
+      f0 = sK * (C00 * h0 + C10 * h1 + C20 * h2);
+      f1 = sK * (C01 * h0 + C11 * h1 + C21 * h2);
+      f2 = sK * (C02 * h0 + C12 * h1 + C22 * h2);
+      m = from_double<T>(A.beta * wq * adet * rh) * u;
     } else {
-      const T sK = (T)(A.alpha * wq * kap);
+      const T sK = from_double<T>(A.alpha * wq * kap);
       f0 = sK * g0;
       f1 = sK * g1;
       f2 = sK * g2;
-      m = (T)(A.beta * wq * rh) * u;
+      m = from_double<T>(A.beta * wq * rh) * u;
     }
     F[0][k] = f0;
     F[1][k] = f1;
@@ -141,11 +150,14 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
     for (int q3 = 0; q3 < q; ++q3) {
       const T vz = tb[2][0][q3 * n + a3];
       const int k = qq + q * q * q3;
-      if (c == 0) acc += vz * F[0][k];
-      else if (c == 1) acc += vz * F[1][k];
-      else acc += tb[2][1][q3 * n + a3] * F[2][k] + vz * F[3][k];
+      if (c == 0) mac(acc, vz, F[0][k]);
+      else if (c == 1) mac(acc, vz, F[1][k]);
+      else {
+        mac(acc, tb[2][1][q3 * n + a3], F[2][k]);
+        mac(acc, vz, F[3][k]);
+      }
     }
-    R[c][r] = acc;
+    R[c][r] = fin(acc);
   }
   __syncthreads();
   // q2: S0 = sum v_y R0 (pairs with d_x), S1 = sum (d_y R1 + v_y R2) (pairs with v_x)
@@ -157,21 +169,26 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
     for (int q2 = 0; q2 < q; ++q2) {
       const T vy = tb[1][0][q2 * n + a2];
       const int o = a3 * q * q + q1 + q * q2;
-      if (c == 0) acc += vy * R[0][o];
-      else acc += tb[1][1][q2 * n + a2] * R[1][o] + vy * R[2][o];
+      if (c == 0) mac(acc, vy, R[0][o]);
+      else {
+        mac(acc, tb[1][1][q2 * n + a2], R[1][o]);
+        mac(acc, vy, R[2][o]);
+      }
     }
-    S[c][r] = acc;
+    S[c][r] = fin(acc);
   }
   __syncthreads();
   // q1: y[a] = sum (d_x S0 + v_x S1); one value per local function
-  T* out = (T*)A.scratch;
+  store_t<T>* out = (store_t<T>*)A.scratch;
   for (int a = tid; a < N; a += NT) {
     const int a1 = a % n, a23 = a / n;
     T acc = 0;
 #pragma unroll
-    for (int q1 = 0; q1 < q; ++q1)
-      acc += tb[0][1][q1 * n + a1] * S[0][a23 * q + q1] + tb[0][0][q1 * n + a1] * S[1][a23 * q + q1];
-    out[(int64_t)a * A.n_elem + e] = acc;
+    for (int q1 = 0; q1 < q; ++q1) {
+      mac(acc, tb[0][1][q1 * n + a1], S[0][a23 * q + q1]);
+      mac(acc, tb[0][0][q1 * n + a1], S[1][a23 * q + q1]);
+    }
+    out[(int64_t)a * A.n_elem + e] = to_store<T>(fin(acc));
   }
 }
 
@@ -200,8 +217,9 @@ bool apply_supported(int dim, int p, int q) {
   return dim == 3 && p >= 1 && p <= 5 && (q == p + 1 || (q == p + 2 && p <= 4));
 }
 
-cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, cudaStream_t st) {
+cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
+  if (df) return dispatch<ff>(a, p, q, st);
   return fp64 ? dispatch<double>(a, p, q, st) : dispatch<float>(a, p, q, st);
 }
 
