@@ -561,7 +561,7 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
     sa = A.spec
     ka = torch.as_tensor(A.kappa(), device=dev)
     adj = {"elements": sa.E, "qp": sa.E * sa.Q}
-    for pr, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+    for pr, dt in (("fp64", torch.float64), ("fp64_df", torch.float64), ("fp32", torch.float32)):
         pl = IgaPlan(Patch(sa.knots, sa.p, sa.q), method="sumfact", precision=pr, blocking=False)
         u = torch.as_tensor(wl.normal(sa.n_dofs, wl.SEED_ADJ_U), device=dev, dtype=dt)
         v = torch.as_tensor(wl.normal(sa.n_dofs, wl.SEED_ADJ_V), device=dev, dtype=dt)

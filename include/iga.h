@@ -159,8 +159,10 @@ int iga_integrate(iga_plan_t plan, const double* kappa, const double* rho,
  * at every quadrature point, computed by sum-factorized interpolation of u and
  * v from the basis tables (no element matrix is formed), and
  *   J_out = sum_k kappa_k grad_kappa[k]   (deterministic fixed-order reduction).
- * u, v: [n_dofs] global vectors; double for IGA_FP64 and IGA_FP64_DF plans
- * (both use the FP64 adjoint), float otherwise.
+ * u, v: [n_dofs] global vectors; double for IGA_FP64 and IGA_FP64_DF plans,
+ * float otherwise.  IGA_FP64 computes in FP64, IGA_FP64_DF in float-float
+ * on the FP32 pipes (FP64-accurate), the others in FP32 with FP64 Jacobian
+ * cofactors and determinant.
  * grad_kappa: [n_qp], same dtype as u.  J_out: one double, may be NULL.
  * kappa may be NULL only if J_out is NULL.  jac as for iga_integrate. */
 int iga_integrate_backward(iga_plan_t plan, const double* kappa, const double* jac,
@@ -211,7 +213,8 @@ int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_s
  *   kappa, rho: [n_qp] or NULL (= 1);  jac: [n_qp][3][3] or NULL (= identity);
  *   x, y: [n_dofs] device vectors, double for IGA_FP64/IGA_FP64_DF plans,
  *         float otherwise (FP32 arithmetic with FP64 Jacobian cofactors and
- *         determinant); y is overwritten and must not alias x.
+ *         determinant; IGA_FP64_DF computes in float-float on the FP32 pipes,
+ *         FP64-accurate); y is overwritten and must not alias x.
  * The first call allocates plan-owned scratch of n_dofmap_entries values
  * (freed by iga_destroy). */
 int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const double* jac,
@@ -226,8 +229,9 @@ int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const dou
  *   grad_rho[k]   = w_k |det G_k| sum_ab GM_ab phi_a(x_k) phi_b(x_k)
  * at every quadrature point.  The double sum over (a, b) is evaluated by sum
  * factorization run backwards (x, then y, then z factors), one CTA per
- * element, in FP64 for IGA_FP64/IGA_FP64_DF plans and in FP32 (FP64
- * cofactors and determinant) otherwise.
+ * element, in FP64 for IGA_FP64 plans, in float-float on the FP32 pipes for
+ * IGA_FP64_DF plans (3D p <= 3; FP64 otherwise) and in FP32 (FP64 cofactors
+ * and determinant) for the others.
  *   jac: [n_qp][d][d] or NULL (= identity).
  *   GK, GM: device, NULL skips that gradient (not both NULL).
  *   grad_kappa, grad_rho: device [n_qp], dtype of GK; required where the

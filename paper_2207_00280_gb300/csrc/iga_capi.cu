@@ -773,7 +773,7 @@ extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const d
     a.grad = grad_kappa ? (char*)grad_kappa + gsz * pd.qp_offset : nullptr;
     a.partial = J_out ? P->d_partial : nullptr;
     a.partial_offset = pd.elem_offset;
-    e = launch_adjoint(a, pd.p, pd.q, fp64, st);
+    e = launch_adjoint(a, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
   }
   if (e == cudaSuccess && J_out) e = launch_reduce_fixed(P->d_partial, P->info.n_elements, J_out, st);
   return finish(P, st, e);
@@ -1198,7 +1198,7 @@ extern "C" int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* ka
     a.grad = grad_kappa;
     a.partial = J_out ? scratch + kNaPartials : nullptr;
     a.partial_offset = 0;
-    e = launch_adjoint(a, p, q, true, st);
+    e = launch_adjoint(a, p, q, true, false, st);
   }
   if (e == cudaSuccess && J_out) e = launch_reduce_fixed(scratch + kNaPartials, E, J_out, st);
   if (e != cudaSuccess) return map_cuda(e);

@@ -119,7 +119,7 @@ struct AdjArgs {
   double* partial;       // [n_elements] or null
   int64_t partial_offset;
 };
-cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st);
 cudaError_t launch_reduce_fixed(const double* partial, int64_t n, double* out, cudaStream_t st);
 bool adjoint_supported(int dim, int p, int q);
 

@@ -10,22 +10,14 @@
 // one-direction-at-a-time order as Algorithm 2 of Sec. 3.2.
 // J is reduced deterministically: a fixed-order per-element sum written to
 // scratch (one double per element), then one block sums the scratch array in
-// a fixed order.  No floating-point atomics.
+// a fixed order.  No floating-point atomics.  T = double (FP64), float (FP32
+// with FP64 cofactors and determinant) or ff (float-float on the FP32 pipes
+// with double inputs and results, FP64_DF plans).
+#include "ff.cuh"
 #include "iga_internal.h"
 
 namespace iga {
 namespace {
-
-template <typename T>
-struct ScalarOps;
-template <>
-struct ScalarOps<double> {
-  static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
-};
-template <>
-struct ScalarOps<float> {
-  static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-};
 
 template <typename T, int P, int QG, bool GEN>
 struct ADJ {
@@ -37,7 +29,6 @@ struct ADJ {
 template <typename T, int P, int QG, bool GEN>
 __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjArgs A) {
   using C = ADJ<T, P, QG, GEN>;
-  using O = ScalarOps<T>;
   constexpr int n = C::n, q = C::q, Q = C::Q, n2 = C::n2, N = C::N, NT = C::NT, REC = C::REC;
   __shared__ double rec[3 * REC];
   __shared__ T tabT[3 * 2 * q * n];            // [dir][val/der][q][n] in T
@@ -61,8 +52,8 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
   for (int a = tid; a < N; a += NT) {
     const int a1 = a % n, a2 = (a / n) % n, a3 = a / n2;
     const int64_t g = A.dof_offset + (s1 + a1) + (int64_t)A.nf0 * ((s2 + a2) + (int64_t)A.nf1 * (s3 + a3));
-    ue[a] = ((const T*)A.u)[g];
-    ve[a] = ((const T*)A.v)[g];
+    ue[a] = to_compute<T>(((const store_t<T>*)A.u)[g]);
+    ve[a] = to_compute<T>(((const store_t<T>*)A.v)[g]);
   }
   __syncthreads();
   for (int i = tid; i < 3 * 2 * q * n; i += NT) {
@@ -80,11 +71,11 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
     T au = 0, av = 0;
 #pragma unroll
     for (int a1 = 0; a1 < n; ++a1) {
-      au = O::fma_(ue[a1 + n * a23], F[a1], au);
-      av = O::fma_(ve[a1 + n * a23], F[a1], av);
+      mac(au, ue[a1 + n * a23], F[a1]);
+      mac(av, ve[a1 + n * a23], F[a1]);
     }
-    U1[0][s][a23 * q + q1] = au;
-    U1[1][s][a23 * q + q1] = av;
+    U1[0][s][a23 * q + q1] = fin(au);
+    U1[1][s][a23 * q + q1] = fin(av);
   }
   __syncthreads();
   // contract a2: U2[vec][c][a3][q1 + q q2], c = vv (s=0,t=0), dv (s=1,t=0), vd (s=0,t=1)
@@ -96,11 +87,11 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
     T au = 0, av = 0;
 #pragma unroll
     for (int a2 = 0; a2 < n; ++a2) {
-      au = O::fma_(U1[0][s][(a2 + n * a3) * q + q1], F[a2], au);
-      av = O::fma_(U1[1][s][(a2 + n * a3) * q + q1], F[a2], av);
+      mac(au, U1[0][s][(a2 + n * a3) * q + q1], F[a2]);
+      mac(av, U1[1][s][(a2 + n * a3) * q + q1], F[a2]);
     }
-    U2[0][c][a3 * q * q + qq] = au;
-    U2[1][c][a3 * q * q + qq] = av;
+    U2[0][c][a3 * q * q + qq] = fin(au);
+    U2[1][c][a3 * q * q + qq] = fin(av);
   }
   __syncthreads();
   // contract a3 at every quadrature point, then the geometry and the product
@@ -113,15 +104,20 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
     for (int a3 = 0; a3 < n; ++a3) {
       const T fz = vz[q3 * n + a3], dfz = dz[q3 * n + a3];
       const int o = a3 * q * q + qq;
-      gu[0] = O::fma_(U2[0][1][o], fz, gu[0]);
-      gu[1] = O::fma_(U2[0][2][o], fz, gu[1]);
-      gu[2] = O::fma_(U2[0][0][o], dfz, gu[2]);
-      gv[0] = O::fma_(U2[1][1][o], fz, gv[0]);
-      gv[1] = O::fma_(U2[1][2][o], fz, gv[1]);
-      gv[2] = O::fma_(U2[1][0][o], dfz, gv[2]);
+      mac(gu[0], U2[0][1][o], fz);
+      mac(gu[1], U2[0][2][o], fz);
+      mac(gu[2], U2[0][0][o], dfz);
+      mac(gv[0], U2[1][1][o], fz);
+      mac(gv[1], U2[1][2][o], fz);
+      mac(gv[2], U2[1][0][o], dfz);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      gu[i] = fin(gu[i]);
+      gv[i] = fin(gv[i]);
     }
     const double* w0 = rec + 2 * q * n;
-    const T W = (T)(w0[q1] * (w0 + REC)[q2] * (w0 + 2 * REC)[q3]);
+    const double Wd = w0[q1] * (w0 + REC)[q2] * (w0 + 2 * REC)[q3];
     T gq;
     if (GEN) {
       // g = (W / |det|) (c gu) . (c gv),  c = cofactor matrix: G^{-T} = c / det
@@ -131,23 +127,24 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
       const double d00 = g11 * g22 - g12 * g21, d01 = g12 * g20 - g10 * g22,
                    d02 = g10 * g21 - g11 * g20;
       const double det = g00 * d00 + g01 * d01 + g02 * d02;
-      const T c00 = (T)d00, c01 = (T)d01, c02 = (T)d02;
-      const T c10 = (T)(g02 * g21 - g01 * g22), c11 = (T)(g00 * g22 - g02 * g20),
-              c12 = (T)(g01 * g20 - g00 * g21);
-      const T c20 = (T)(g01 * g12 - g02 * g11), c21 = (T)(g02 * g10 - g00 * g12),
-              c22 = (T)(g00 * g11 - g01 * g10);
+      const T c00 = from_double<T>(d00), c01 = from_double<T>(d01), c02 = from_double<T>(d02);
+      const T c10 = from_double<T>(g02 * g21 - g01 * g22), c11 = from_double<T>(g00 * g22 - g02 * g20),
+              c12 = from_double<T>(g01 * g20 - g00 * g21);
+      const T c20 = from_double<T>(g01 * g12 - g02 * g11), c21 = from_double<T>(g02 * g10 - g00 * g12),
+              c22 = from_double<T>(g00 * g11 - g01 * g10);
       const T pu0 = c00 * gu[0] + c01 * gu[1] + c02 * gu[2];
       const T pu1 = c10 * gu[0] + c11 * gu[1] + c12 * gu[2];
       const T pu2 = c20 * gu[0] + c21 * gu[1] + c22 * gu[2];
       const T pv0 = c00 * gv[0] + c01 * gv[1] + c02 * gv[2];
       const T pv1 = c10 * gv[0] + c11 * gv[1] + c12 * gv[2];
       const T pv2 = c20 * gv[0] + c21 * gv[1] + c22 * gv[2];
-      gq = W / (T)fabs(det) * (pu0 * pv0 + pu1 * pv1 + pu2 * pv2);
+      gq = from_double<T>(Wd / fabs(det)) * (pu0 * pv0 + pu1 * pv1 + pu2 * pv2);
     } else {
-      gq = W * (gu[0] * gv[0] + gu[1] * gv[1] + gu[2] * gv[2]);
+      gq = from_double<T>(Wd) * (gu[0] * gv[0] + gu[1] * gv[1] + gu[2] * gv[2]);
     }
-    if (A.grad) ((T*)A.grad)[e * Q + k] = gq;
-    if (A.partial) part += (A.kappa ? A.kappa[e * Q + k] : 1.0) * (double)gq;
+    const store_t<T> gs = to_store<T>(gq);
+    if (A.grad) ((store_t<T>*)A.grad)[e * Q + k] = gs;
+    if (A.partial) part += (A.kappa ? A.kappa[e * Q + k] : 1.0) * (double)gs;
   }
   if (A.partial) {
     // fixed-order block reduction: warp tree, then warp 0 over the warp sums
@@ -209,8 +206,9 @@ bool adjoint_supported(int dim, int p, int q) {
   return dim == 3 && p >= 1 && p <= 5 && (q == p + 1 || (q == p + 2 && p <= 4));
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, cudaStream_t st) {
+cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
+  if (df) return dispatch<ff>(a, p, q, st);
   return fp64 ? dispatch<double>(a, p, q, st) : dispatch<float>(a, p, q, st);
 }
 

@@ -42,6 +42,11 @@ def test_adjoint_vs_oracle(oracle_mod, p, dq, curved):
     g, J = _adj(plan, kappa, u, v, G)
     assert np.abs(g - gr.reshape(-1)).max() <= 1e-12 * np.abs(gr).max()
     assert J == pytest.approx(Jr, rel=1e-12, abs=1e-13 * np.abs(kappa * gr.reshape(-1)).sum())
+    # FP64_DF plans: float-float on the FP32 pipes, the FP64 bound
+    pdf = IgaPlan(Patch(knots, p, q), method="sumfact", precision="fp64_df")
+    gd, Jd = _adj(pdf, kappa, u, v, G)
+    assert np.abs(gd - gr.reshape(-1)).max() <= 1e-12 * np.abs(gr).max()
+    assert Jd == pytest.approx(Jr, rel=1e-12, abs=1e-13 * np.abs(kappa * gr.reshape(-1)).sum())
     plan32 = IgaPlan(Patch(knots, p, q), method="sumfact", precision="fp32")
     g32, J32 = _adj(plan32, kappa, u, v, G, dtype=torch.float32)
     assert np.linalg.norm(g32 - gr.reshape(-1)) <= 1e-5 * np.linalg.norm(gr)
