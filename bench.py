@@ -645,6 +645,14 @@ def measure_wq(W, stream, flush, dev):
     out["stiffness"] = st
     del K
     pl.close()
+    # the same two matrices in float-float arithmetic (FP64_DF plan)
+    pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method="sumfact", precision="fp64_df", blocking=False)
+    out["fp64_df_ms_per_matrix"] = {
+        "mass": round(_time_steps(lambda: pl.wq_mass(c=c, values=vals, stream=stream), 10, stream,
+                                  flush), 4),
+        "stiffness": round(_time_steps(lambda: pl.wq_stiffness(c=c, values=vals, stream=stream), 10,
+                                       stream, flush), 4)}
+    pl.close()
     return out
 
 

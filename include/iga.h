@@ -254,7 +254,8 @@ int iga_integrate_grad(iga_plan_t plan, const double* jac, const void* GK, const
  * patch `patch`; dir = -1 gives the patch's grid size (x_out NULL), patch = -1
  * (with dir = -1) the total over patches.  The first call of either entry
  * builds the plan's tables (host least-norm solves, device upload).
- * iga_wq_mass: FP64 plans only.  c: device, the coefficient (rho |det G| for
+ * iga_wq_mass: FP64 plans only (IGA_FP64_DF computes in float-float on the
+ * FP32 pipes, FP64-accurate).  c: device, the coefficient (rho |det G| for
  * a mass) at every grid point, patches concatenated, each [n3][n2][n1] with x
  * fastest; NULL = 1.  values: device [n_csr_nnz] doubles on the pattern of
  * iga_csr_pattern, overwritten. */

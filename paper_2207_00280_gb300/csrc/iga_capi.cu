@@ -982,7 +982,7 @@ extern "C" int iga_wq_mass(iga_plan_t P, const double* c, double* values, void* 
     }
     a.coef = c ? c + P->wq_coef_off[ip] : nullptr;
     a.values = values;
-    e = launch_wq_mass(a, P->ph[ip].p, st);
+    e = launch_wq_mass(a, P->ph[ip].p, P->opts.precision == IGA_FP64_DF, st);
   }
   return finish(P, st, e);
 }
@@ -1015,7 +1015,7 @@ extern "C" int iga_wq_stiffness(iga_plan_t P, const double* c, double* values, v
     }
     a.coef = c ? c + P->wq_coef_off[ip] : nullptr;
     a.values = values;
-    e = launch_wq_stiffness(a, P->ph[ip].p, st);
+    e = launch_wq_stiffness(a, P->ph[ip].p, P->opts.precision == IGA_FP64_DF, st);
     // a patch whose rule tables exceed shared memory (very short knot vectors)
     if (e == cudaErrorInvalidValue) {
       cudaGetLastError();

@@ -225,10 +225,11 @@ struct WqPatchArgs {
   const double* coef;    // patch block of the coefficient grid [np3][np2][np1], or null = 1
   double* values;        // global CSR values
 };
-cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, cudaStream_t st);
+// df: float-float arithmetic (FP64_DF plans), else FP64
+cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, bool df, cudaStream_t st);
 // Diffusion stiffness by weighted quadrature (3D, FP64, 2 <= p <= 4): values of
 // the rows of one patch, sum over the three derivative directions.
-cudaError_t launch_wq_stiffness(const WqPatchArgs& a, int p, cudaStream_t st);
+cudaError_t launch_wq_stiffness(const WqPatchArgs& a, int p, bool df, cudaStream_t st);
 bool wq_stiffness_supported(int dim, int p);
 
 }  // namespace iga

@@ -17,6 +17,7 @@
 // The pattern is the tensor product of 1D coupling ranges: in each direction
 // the functions that share an element with i_k form the range flo..fhi, so a
 // row holds (j3, j2, j1) in flo..fhi of each direction, ascending.
+#include "ff.cuh"
 #include "iga_internal.h"
 
 namespace iga {
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(256)
 //   T2[j2][j3][q1] = sum_q2 V2[j2][q2] T1[j3][q1][q2]
 //   M[j1][j2][j3]  = sum_q1 V1[j1][q1] T2[j2][j3][q1]
 // and written to the row's CSR entries (j3, j2, j1 ascending).
-template <int P>
+template <typename T, int P>
 __global__ void __launch_bounds__(128) k_wq_mass(const WqPatchArgs A) {
   constexpr int W = 2 * P + 1, NT = 128;
   extern __shared__ double wsm[];
@@ -226,72 +227,74 @@ __global__ void __launch_bounds__(128) k_wq_mass(const WqPatchArgs A) {
     }
     const int n1 = qn[0], n2 = qn[1], n3 = qn[2];
     const int w1 = g.w[0], w2 = g.w[1], w3 = g.w[2];
-    double* V1 = wsm;                    // [w1][n1]
-    double* V2 = V1 + W * n1;            // [w2][n2]
-    double* V3 = V2 + W * n2;            // [w3][n3]
-    double* T1 = V3 + W * n3;            // [w3][n1][n2]
-    double* T2 = T1 + (size_t)W * n1 * n2;   // [w2][w3][n1]
+    T* V1 = reinterpret_cast<T*>(wsm);   // [w1][n1]
+    T* V2 = V1 + W * n1;                 // [w2][n2]
+    T* V3 = V2 + W * n2;                 // [w3][n3]
+    T* T1 = V3 + W * n3;                 // [w3][n1][n2]
+    T* T2 = T1 + (size_t)W * n1 * n2;    // [w2][w3][n1]
     __syncthreads();                     // the previous row's buffers are no longer read
     for (int k = 0; k < 3; ++k) {
       const int wk = g.w[k], nk = qn[k];
       const double* src = A.d[k].V + (size_t)ii[k] * W * A.d[k].qmax;
-      double* dst = k == 0 ? V1 : (k == 1 ? V2 : V3);
-      for (int t = threadIdx.x; t < wk * nk; t += NT) dst[t] = src[(t / nk) * A.d[k].qmax + t % nk];
+      T* dst = k == 0 ? V1 : (k == 1 ? V2 : V3);
+      for (int t = threadIdx.x; t < wk * nk; t += NT)
+        dst[t] = to_compute<T>(src[(t / nk) * A.d[k].qmax + t % nk]);
     }
     __syncthreads();
     // q3: one coefficient load per point, all w3 sums of the point in registers
     const int64_t np1 = A.d[0].np, np2 = A.d[1].np;
     for (int it = threadIdx.x; it < n1 * n2; it += NT) {
       const int q1 = it % n1, q2 = it / n1;
-      double acc[W];
+      T acc[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int j = 0; j < W; ++j) acc[j] = 0;
       for (int q3 = 0; q3 < n3; ++q3) {
-        const double cq = A.coef ? A.coef[(qlo[0] + q1) + np1 * ((qlo[1] + q2) + np2 * (qlo[2] + q3))] : 1.0;
+        const T cq = A.coef ? to_compute<T>(A.coef[(qlo[0] + q1) + np1 * ((qlo[1] + q2) + np2 * (qlo[2] + q3))])
+                            : T(1);
 #pragma unroll
         for (int j = 0; j < W; ++j)
-          if (j < w3) acc[j] = fma(V3[j * n3 + q3], cq, acc[j]);
+          if (j < w3) mac(acc[j], V3[j * n3 + q3], cq);
       }
 #pragma unroll
       for (int j = 0; j < W; ++j)
-        if (j < w3) T1[((size_t)j * n1 + q1) * n2 + q2] = acc[j];
+        if (j < w3) T1[((size_t)j * n1 + q1) * n2 + q2] = fin(acc[j]);
     }
     __syncthreads();
     // q2
     for (int it = threadIdx.x; it < n1 * w3; it += NT) {
       const int q1 = it % n1, j3 = it / n1;
-      const double* t1 = T1 + ((size_t)j3 * n1 + q1) * n2;
-      double acc[W];
+      const T* t1 = T1 + ((size_t)j3 * n1 + q1) * n2;
+      T acc[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int j = 0; j < W; ++j) acc[j] = 0;
       for (int q2 = 0; q2 < n2; ++q2) {
-        const double tv = t1[q2];
+        const T tv = t1[q2];
 #pragma unroll
         for (int j = 0; j < W; ++j)
-          if (j < w2) acc[j] = fma(V2[j * n2 + q2], tv, acc[j]);
+          if (j < w2) mac(acc[j], V2[j * n2 + q2], tv);
       }
 #pragma unroll
       for (int j = 0; j < W; ++j)
-        if (j < w2) T2[((size_t)j * w3 + j3) * n1 + q1] = acc[j];
+        if (j < w2) T2[((size_t)j * w3 + j3) * n1 + q1] = fin(acc[j]);
     }
     __syncthreads();
     // q1, then the row's entries
     for (int it = threadIdx.x; it < w2 * w3; it += NT) {
       const int j2 = it % w2, j3 = it / w2;
-      const double* t2 = T2 + ((size_t)j2 * w3 + j3) * n1;
-      double acc[W];
+      const T* t2 = T2 + ((size_t)j2 * w3 + j3) * n1;
+      T acc[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int j = 0; j < W; ++j) acc[j] = 0;
       for (int q1 = 0; q1 < n1; ++q1) {
-        const double tv = t2[q1];
+        const T tv = t2[q1];
 #pragma unroll
         for (int j = 0; j < W; ++j)
-          if (j < w1) acc[j] = fma(V1[j * n1 + q1], tv, acc[j]);
+          if (j < w1) mac(acc[j], V1[j * n1 + q1], tv);
       }
       double* out = A.values + g.start + ((int64_t)j3 * w2 + j2) * w1;
 #pragma unroll
       for (int j = 0; j < W; ++j)
-        if (j < w1) out[j] = acc[j];
+        if (j < w1) out[j] = to_store<T>(fin(acc[j]));
     }
   }
 }
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(128) k_wq_mass(const WqPatchArgs A) {
 //   y: Ya[j2][j3][q1] = sum_q2 V0_2 Z0,  Yb = sum_q2 (V1_2 Z0 + V0_2 Z1)
 //   x: K[j1][j2][j3]  = sum_q1 (V1_1 Ya + V0_1 Yb)
 // and written to the row's CSR entries (j3, j2, j1 ascending).
-template <int P>
+template <typename T, int P>
 __global__ void __launch_bounds__(128) k_wq_stiff(const WqPatchArgs A) {
   constexpr int W = 2 * P + 1, NT = 128;
   extern __shared__ double wsm[];
@@ -322,101 +325,107 @@ __global__ void __launch_bounds__(128) k_wq_stiff(const WqPatchArgs A) {
     }
     const int n1 = qn[0], n2 = qn[1], n3 = qn[2];
     const int w1 = g.w[0], w2 = g.w[1], w3 = g.w[2];
-    double* V[3][2];
-    V[0][0] = wsm;                       // [w1][n1]
+    T* V[3][2];
+    V[0][0] = reinterpret_cast<T*>(wsm);   // [w1][n1]
     V[0][1] = V[0][0] + W * n1;
     V[1][0] = V[0][1] + W * n1;          // [w2][n2]
     V[1][1] = V[1][0] + W * n2;
     V[2][0] = V[1][1] + W * n2;          // [w3][n3]
     V[2][1] = V[2][0] + W * n3;
-    double* Z0 = V[2][1] + W * n3;                // [w3][n1][n2]
-    double* Z1 = Z0 + (size_t)W * n1 * n2;
-    double* Ya = Z1 + (size_t)W * n1 * n2;        // [w2][w3][n1]
-    double* Yb = Ya + (size_t)W * W * n1;
+    T* Z0 = V[2][1] + W * n3;                // [w3][n1][n2]
+    T* Z1 = Z0 + (size_t)W * n1 * n2;
+    T* Ya = Z1 + (size_t)W * n1 * n2;        // [w2][w3][n1]
+    T* Yb = Ya + (size_t)W * W * n1;
     __syncthreads();                     // the previous row's buffers are no longer read
     for (int k = 0; k < 3; ++k) {
       const int wk = g.w[k], nk = qn[k];
       for (int v = 0; v < 2; ++v) {
         const double* src = (v ? A.d[k].V1 : A.d[k].V) + (size_t)ii[k] * W * A.d[k].qmax;
-        double* dst = V[k][v];
-        for (int t = threadIdx.x; t < wk * nk; t += NT) dst[t] = src[(t / nk) * A.d[k].qmax + t % nk];
+        T* dst = V[k][v];
+        for (int t = threadIdx.x; t < wk * nk; t += NT)
+          dst[t] = to_compute<T>(src[(t / nk) * A.d[k].qmax + t % nk]);
       }
     }
     __syncthreads();
     // z: one coefficient load per point, both tables' sums in registers
     const int64_t np1 = A.d[0].np, np2 = A.d[1].np;
-    const double* V30 = V[2][0];
-    const double* V31 = V[2][1];
+    const T* V30 = V[2][0];
+    const T* V31 = V[2][1];
     for (int it = threadIdx.x; it < n1 * n2; it += NT) {
       const int q1 = it % n1, q2 = it / n1;
-      double a0[W], a1[W];
+      T a0[W], a1[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) a0[j] = a1[j] = 0.0;
+      for (int j = 0; j < W; ++j) a0[j] = a1[j] = 0;
       for (int q3 = 0; q3 < n3; ++q3) {
-        const double cq = A.coef ? A.coef[(qlo[0] + q1) + np1 * ((qlo[1] + q2) + np2 * (qlo[2] + q3))] : 1.0;
+        const T cq = A.coef ? to_compute<T>(A.coef[(qlo[0] + q1) + np1 * ((qlo[1] + q2) + np2 * (qlo[2] + q3))])
+                            : T(1);
 #pragma unroll
         for (int j = 0; j < W; ++j)
           if (j < w3) {
-            a0[j] = fma(V30[j * n3 + q3], cq, a0[j]);
-            a1[j] = fma(V31[j * n3 + q3], cq, a1[j]);
+            mac(a0[j], V30[j * n3 + q3], cq);
+            mac(a1[j], V31[j * n3 + q3], cq);
           }
       }
 #pragma unroll
       for (int j = 0; j < W; ++j)
         if (j < w3) {
-          Z0[((size_t)j * n1 + q1) * n2 + q2] = a0[j];
-          Z1[((size_t)j * n1 + q1) * n2 + q2] = a1[j];
+          Z0[((size_t)j * n1 + q1) * n2 + q2] = fin(a0[j]);
+          Z1[((size_t)j * n1 + q1) * n2 + q2] = fin(a1[j]);
         }
     }
     __syncthreads();
     // y
-    const double* V20 = V[1][0];
-    const double* V21 = V[1][1];
+    const T* V20 = V[1][0];
+    const T* V21 = V[1][1];
     for (int it = threadIdx.x; it < n1 * w3; it += NT) {
       const int q1 = it % n1, j3 = it / n1;
-      const double* z0 = Z0 + ((size_t)j3 * n1 + q1) * n2;
-      const double* z1 = Z1 + ((size_t)j3 * n1 + q1) * n2;
-      double aa[W], ab[W];
+      const T* z0 = Z0 + ((size_t)j3 * n1 + q1) * n2;
+      const T* z1 = Z1 + ((size_t)j3 * n1 + q1) * n2;
+      T aa[W], ab[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) aa[j] = ab[j] = 0.0;
+      for (int j = 0; j < W; ++j) aa[j] = ab[j] = 0;
       for (int q2 = 0; q2 < n2; ++q2) {
-        const double t0 = z0[q2], t1 = z1[q2];
+        const T t0 = z0[q2], t1 = z1[q2];
 #pragma unroll
         for (int j = 0; j < W; ++j)
           if (j < w2) {
-            const double v0 = V20[j * n2 + q2];
-            aa[j] = fma(v0, t0, aa[j]);
-            ab[j] = fma(V21[j * n2 + q2], t0, fma(v0, t1, ab[j]));
+            const T v0 = V20[j * n2 + q2];
+            mac(aa[j], v0, t0);
+            mac(ab[j], v0, t1);
+            mac(ab[j], V21[j * n2 + q2], t0);
           }
       }
 #pragma unroll
       for (int j = 0; j < W; ++j)
         if (j < w2) {
-          Ya[((size_t)j * w3 + j3) * n1 + q1] = aa[j];
-          Yb[((size_t)j * w3 + j3) * n1 + q1] = ab[j];
+          Ya[((size_t)j * w3 + j3) * n1 + q1] = fin(aa[j]);
+          Yb[((size_t)j * w3 + j3) * n1 + q1] = fin(ab[j]);
         }
     }
     __syncthreads();
     // x, then the row's entries
-    const double* V10 = V[0][0];
-    const double* V11 = V[0][1];
+    const T* V10 = V[0][0];
+    const T* V11 = V[0][1];
     for (int it = threadIdx.x; it < w2 * w3; it += NT) {
       const int j2 = it % w2, j3 = it / w2;
-      const double* ya = Ya + ((size_t)j2 * w3 + j3) * n1;
-      const double* yb = Yb + ((size_t)j2 * w3 + j3) * n1;
-      double acc[W];
+      const T* ya = Ya + ((size_t)j2 * w3 + j3) * n1;
+      const T* yb = Yb + ((size_t)j2 * w3 + j3) * n1;
+      T acc[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) acc[j] = 0.0;
+      for (int j = 0; j < W; ++j) acc[j] = 0;
       for (int q1 = 0; q1 < n1; ++q1) {
-        const double ta = ya[q1], tb = yb[q1];
+        const T ta = ya[q1], tb = yb[q1];
 #pragma unroll
         for (int j = 0; j < W; ++j)
-          if (j < w1) acc[j] = fma(V11[j * n1 + q1], ta, fma(V10[j * n1 + q1], tb, acc[j]));
+          if (j < w1) {
+            mac(acc[j], V10[j * n1 + q1], tb);
+            mac(acc[j], V11[j * n1 + q1], ta);
+          }
       }
       double* out = A.values + g.start + ((int64_t)j3 * w2 + j2) * w1;
 #pragma unroll
       for (int j = 0; j < W; ++j)
-        if (j < w1) out[j] = acc[j];
+        if (j < w1) out[j] = to_store<T>(fin(acc[j]));
     }
   }
 }
@@ -488,7 +497,7 @@ cudaError_t dispatch_gather(const CsrPatch& c, const FnCouple* fc, const int* sp
   }
 }
 
-template <int P>
+template <typename T, int P>
 cudaError_t run_wq(const WqPatchArgs& a, cudaStream_t st) {
   constexpr int W = 2 * P + 1;
   const int64_t n_rows = (int64_t)a.c.nf[0] * a.c.nf[1] * a.c.nf[2];
@@ -496,7 +505,7 @@ cudaError_t run_wq(const WqPatchArgs& a, cudaStream_t st) {
   const size_t q1 = a.d[0].qmax, q2 = a.d[1].qmax, q3 = a.d[2].qmax;
   const size_t smem = sizeof(double) * (W * (q1 + q2 + q3) + W * q1 * q2 + (size_t)W * W * q1);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  auto k = k_wq_mass<P>;
+  auto k = k_wq_mass<T, P>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = n_rows < 152 * 64 ? n_rows : 152 * 64;
@@ -504,7 +513,7 @@ cudaError_t run_wq(const WqPatchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int P>
+template <typename T, int P>
 cudaError_t run_wq_stiff(const WqPatchArgs& a, cudaStream_t st) {
   constexpr int W = 2 * P + 1;
   const int64_t n_rows = (int64_t)a.c.nf[0] * a.c.nf[1] * a.c.nf[2];
@@ -513,7 +522,7 @@ cudaError_t run_wq_stiff(const WqPatchArgs& a, cudaStream_t st) {
   const size_t smem =
       sizeof(double) * (2 * W * (q1 + q2 + q3) + 2 * W * q1 * q2 + 2 * (size_t)W * W * q1);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  auto k = k_wq_stiff<P>;
+  auto k = k_wq_stiff<T, P>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = n_rows < 152 * 64 ? n_rows : 152 * 64;
@@ -525,24 +534,34 @@ cudaError_t run_wq_stiff(const WqPatchArgs& a, cudaStream_t st) {
 
 bool wq_stiffness_supported(int dim, int p) { return dim == 3 && p >= 2 && p <= 4; }
 
-cudaError_t launch_wq_stiffness(const WqPatchArgs& a, int p, cudaStream_t st) {
+template <typename T>
+cudaError_t wq_stiff_p(const WqPatchArgs& a, int p, cudaStream_t st) {
   switch (p) {
-    case 2: return run_wq_stiff<2>(a, st);
-    case 3: return run_wq_stiff<3>(a, st);
-    case 4: return run_wq_stiff<4>(a, st);
+    case 2: return run_wq_stiff<T, 2>(a, st);
+    case 3: return run_wq_stiff<T, 3>(a, st);
+    case 4: return run_wq_stiff<T, 4>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, cudaStream_t st) {
+template <typename T>
+cudaError_t wq_mass_p(const WqPatchArgs& a, int p, cudaStream_t st) {
   switch (p) {
-    case 1: return run_wq<1>(a, st);
-    case 2: return run_wq<2>(a, st);
-    case 3: return run_wq<3>(a, st);
-    case 4: return run_wq<4>(a, st);
-    case 5: return run_wq<5>(a, st);
+    case 1: return run_wq<T, 1>(a, st);
+    case 2: return run_wq<T, 2>(a, st);
+    case 3: return run_wq<T, 3>(a, st);
+    case 4: return run_wq<T, 4>(a, st);
+    case 5: return run_wq<T, 5>(a, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_wq_stiffness(const WqPatchArgs& a, int p, bool df, cudaStream_t st) {
+  return df ? wq_stiff_p<ff>(a, p, st) : wq_stiff_p<double>(a, p, st);
+}
+
+cudaError_t launch_wq_mass(const WqPatchArgs& a, int p, bool df, cudaStream_t st) {
+  return df ? wq_mass_p<ff>(a, p, st) : wq_mass_p<double>(a, p, st);
 }
 
 cudaError_t launch_csr_pattern(const CsrPatch& c, const FnCouple* fc, int64_t* row_ptr,

@@ -55,13 +55,15 @@ def test_points_match_oracle(case):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp64_df"])
 @pytest.mark.parametrize("coef", ["one", "lognormal"])
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c[0])
-def test_mass_matches_oracle(case, coef):
+def test_mass_matches_oracle(case, coef, precision):
+    """fp64_df plans run the contraction in float-float on the FP32 pipes."""
     _, knots, p = case
     P = oracle.Patch(list(knots), p, p + 1)
     rp, ci = P.csr_pattern()
-    plan = IgaPlan(Patch(list(knots), p, p + 1), method="sumfact", precision="fp64")
+    plan = IgaPlan(Patch(list(knots), p, p + 1), method="sumfact", precision=precision)
     n = plan.wq_grid_size(0)
     c = None if coef == "one" else wl.lognormal(n, 91)
     ref = P.wq_mass(rp, ci, c=c)
@@ -127,13 +129,14 @@ def _stiff_cases():
     return [c for c in _cases() if c[2] >= 2]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp64_df"])
 @pytest.mark.parametrize("coef", ["one", "lognormal"])
 @pytest.mark.parametrize("case", _stiff_cases(), ids=lambda c: c[0])
-def test_stiffness_matches_oracle(case, coef):
+def test_stiffness_matches_oracle(case, coef, precision):
     _, knots, p = case
     P = oracle.Patch(list(knots), p, p + 1)
     rp, ci = P.csr_pattern()
-    plan = IgaPlan(Patch(list(knots), p, p + 1), method="sumfact", precision="fp64")
+    plan = IgaPlan(Patch(list(knots), p, p + 1), method="sumfact", precision=precision)
     n = plan.wq_grid_size(0)
     c = None if coef == "one" else wl.lognormal(n, 94)
     ref = P.wq_stiffness(rp, ci, c=c)
