@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
   __syncthreads();
   for (int i = tid; i < 3 * 2 * q * n; i += NT) {
     const int d = i / (2 * q * n), j = i % (2 * q * n);
-    tabT[i] = (T)rec[d * REC + j];
+    tabT[i] = from_double<T>(rec[d * REC + j]);
   }
   __syncthreads();
   const T* vx = tabT;               const T* dx = tabT + q * n;

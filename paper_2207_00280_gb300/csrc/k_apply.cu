@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
   __syncthreads();
   for (int i = tid; i < 3 * 2 * q * n; i += NT) {
     const int d = i / (2 * q * n), j = i % (2 * q * n);
-    (&tb[0][0][0])[i] = (T)rec[d * REC + j];
+    (&tb[0][0][0])[i] = from_double<T>(rec[d * REC + j]);
   }
   __syncthreads();
   // interpolation, a1: U1[s][a23][q1] = sum_a1 x[a1, a23] B^s_x(q1)[a1]

@@ -335,9 +335,9 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   __syncthreads();
   for (int i = tid; i < 3 * 2 * q * n; i += NT) {
     const int d = i / (2 * q * n), j = i % (2 * q * n);
-    (&f[0][0][0])[i] = (T)rec[d * REC + j];
+    (&f[0][0][0])[i] = from_double<T>(rec[d * REC + j]);
   }
-  if (tid < 3 * q) wts[tid] = (T)rec[(tid / q) * REC + 2 * q * n + tid % q];
+  if (tid < 3 * q) wts[tid] = from_double<T>(rec[(tid / q) * REC + 2 * q * n + tid % q]);
   if (tid < C::T3) {
     int a3, b3;
     tri_decode(tid, n, a3, b3);
