@@ -201,7 +201,7 @@ int iga_csr_pattern(iga_plan_t plan, int64_t* row_ptr, int32_t* col_idx, void* c
  * scheduling. */
 int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_stream);
 
-/* Matrix-free operator application (3D, every patch):
+/* Matrix-free operator application (3D, or 2D on IGA_FP64 plans; every patch):
  *   y = alpha K(kappa) x + beta M(rho) x,
  * the products K u and M u of the forward-Euler step of Sec. 2.2 (eq. Euler)
  * for the stiffness and mass of iga_integrate, without forming a global or
@@ -210,7 +210,7 @@ int iga_assemble(iga_plan_t plan, const void* A_elem, void* values, void* cuda_s
  * Sec. 3.2), multiplied by the coefficient and geometry factors, and
  * integrated back against the test functions; the element results are then
  * summed per dof in ascending element order (deterministic, no atomics).
- *   kappa, rho: [n_qp] or NULL (= 1);  jac: [n_qp][3][3] or NULL (= identity);
+ *   kappa, rho: [n_qp] or NULL (= 1);  jac: [n_qp][d][d] or NULL (= identity);
  *   x, y: [n_dofs] device vectors, double for IGA_FP64/IGA_FP64_DF plans,
  *         float otherwise (FP32 arithmetic with FP64 Jacobian cofactors and
  *         determinant; IGA_FP64_DF computes in float-float on the FP32 pipes,

@@ -885,11 +885,11 @@ extern "C" int iga_apply(iga_plan_t P, const double* kappa, const double* rho, c
     a.dof_offset = pd.dof_offset;
     a.kappa = kappa ? kappa + pd.qp_offset : nullptr;
     a.rho = rho ? rho + pd.qp_offset : nullptr;
-    a.jac = jac ? jac + pd.qp_offset * 9 : nullptr;
+    a.jac = jac ? jac + pd.qp_offset * pd.dim * pd.dim : nullptr;
     a.x = x;
     a.alpha = alpha; a.beta = beta;
     a.scratch = (char*)P->d_apply_scratch + esz * pd.dofmap_offset;
-    e = launch_apply(a, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
+    e = launch_apply(a, pd.dim, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
     if (e == cudaSuccess)
       e = launch_apply_gather(P->csr[ip], P->d_fc, P->d_spans, a.scratch, y, fp64, st);
   }

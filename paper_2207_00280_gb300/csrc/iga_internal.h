@@ -163,7 +163,7 @@ cudaError_t launch_csr_pattern(const CsrPatch& c, const FnCouple* fc, int64_t* r
 cudaError_t launch_assemble(const CsrPatch& c, const FnCouple* fc, const int* spans,
                             const void* A, void* values, bool fp64, cudaStream_t st);
 
-// y = alpha K(kappa) x + beta M(rho) x, matrix-free (3D).  Phase 1 writes each
+// y = alpha K(kappa) x + beta M(rho) x, matrix-free (3D; 2D for FP64 plans).  Phase 1 writes each
 // element's local result to scratch[a * E + e]; phase 2 sums them per dof in
 // ascending element order.
 struct ApplyArgs {
@@ -175,12 +175,13 @@ struct ApplyArgs {
   int64_t dof_offset;
   const double* kappa;   // patch-local [E][Q] or null (= 1)
   const double* rho;     // patch-local [E][Q] or null (= 1)
-  const double* jac;     // patch-local [E][Q][9] or null
+  const double* jac;     // patch-local [E][Q][d*d] or null
   const void* x;         // global [n_dofs], double or float
   double alpha, beta;
   void* scratch;         // patch-local [N][E], double or float
 };
-cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st);
+cudaError_t launch_apply(const ApplyArgs& a, int dim, int p, int q, bool fp64, bool df,
+                         cudaStream_t st);
 cudaError_t launch_apply_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
                                 const void* scratch, void* y, bool fp64, cudaStream_t st);
 bool apply_supported(int dim, int p, int q);

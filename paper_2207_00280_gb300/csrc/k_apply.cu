@@ -1,5 +1,5 @@
 // k_apply.cu -- matrix-free operator application y = alpha K(kappa) x +
-// beta M(rho) x, 3D (the products K u and M u of the forward-Euler step of
+// beta M(rho) x, 3D and (k_apply2, below) 2D (the products K u and M u of the forward-Euler step of
 // Sec. 2.2, eq. Euler; no global matrix and no element matrix is formed).
 //
 // Per element (one CTA): gather x_e through the dof map, interpolate the
@@ -192,6 +192,132 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
   }
 }
 
+// 2D (FP64 plans): the same steps with two directions.  Interpolation
+// U[s][a2][q1] = sum_a1 x[a1 + n a2] B^s_x(q1)[a1] (value and derivative), at
+// every point g0 = d_x x, g1 = d_y x, u = x; flux f = alpha w kappa |det G|
+// G^{-1} G^{-T} g through the 2x2 cofactors, m = beta w rho |det G| u; back:
+// S0[a2][q1] = sum_q2 v_y f0, S1[a2][q1] = sum_q2 (d_y f1 + v_y m),
+// y_e[a1 + n a2] = sum_q1 (d_x S0 + v_x S1).
+template <typename T, int P, int QG, bool GEN>
+__global__ void __launch_bounds__(64) k_apply2(const ApplyArgs A) {
+  constexpr int n = P + 1, q = QG, N = n * n, Q = q * q, NT = 64, REC = 2 * q * n + q;
+  __shared__ double rec[2 * REC];
+  __shared__ T tb[2][2][q * n];          // [direction][value, derivative][q][n]
+  __shared__ T xe[N];
+  __shared__ T U[2][n * q];              // [value, derivative in x][a2][q1]
+  __shared__ T F[3][Q];                  // f0, f1, m at every quadrature point
+  __shared__ T S[2][n * q];              // [a2][q1]: pairs with d_x, with v_x
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const int e1 = (int)(e % A.K1), e2 = (int)(e / A.K1);
+  for (int i = tid; i < 2 * REC; i += NT) {
+    const int d = i / REC, j = i - d * REC;
+    rec[i] = (d == 0 ? A.tab[0] + (int64_t)e1 * REC : A.tab[1] + (int64_t)e2 * REC)[j];
+  }
+  const int s1 = A.span[0][e1] - P, s2 = A.span[1][e2] - P;
+  for (int a = tid; a < N; a += NT) {
+    const int64_t g = A.dof_offset + (s1 + a % n) + (int64_t)A.nf0 * (s2 + a / n);
+    xe[a] = to_compute<T>(((const store_t<T>*)A.x)[g]);
+  }
+  __syncthreads();
+  for (int i = tid; i < 2 * 2 * q * n; i += NT) {
+    const int d = i / (2 * q * n), j = i % (2 * q * n);
+    (&tb[0][0][0])[i] = from_double<T>(rec[d * REC + j]);
+  }
+  __syncthreads();
+  for (int it = tid; it < 2 * n * q; it += NT) {
+    const int sd = it / (n * q), r = it % (n * q), a2 = r / q, q1 = r % q;
+    const T* B = &tb[0][sd][q1 * n];
+    T acc = 0;
+#pragma unroll
+    for (int a1 = 0; a1 < n; ++a1) mac(acc, xe[a1 + n * a2], B[a1]);
+    U[sd][r] = fin(acc);
+  }
+  __syncthreads();
+  for (int k = tid; k < Q; k += NT) {
+    const int q1 = k % q, q2 = k / q;
+    T g0 = 0, g1 = 0, u = 0;
+#pragma unroll
+    for (int a2 = 0; a2 < n; ++a2) {
+      const T vy = tb[1][0][q2 * n + a2], dy = tb[1][1][q2 * n + a2];
+      mac(g0, U[1][a2 * q + q1], vy);
+      mac(g1, U[0][a2 * q + q1], dy);
+      mac(u, U[0][a2 * q + q1], vy);
+    }
+    g0 = fin(g0);
+    g1 = fin(g1);
+    u = fin(u);
+    const double wq = rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2];
+    const double kap = A.kappa ? A.kappa[e * Q + k] : 1.0;
+    const double rh = A.rho ? A.rho[e * Q + k] : 1.0;
+    if (GEN) {
+      // cofactors c = [[g11, -g10], [-g01, g00]]: G^{-T} = c / det; reference
+      // flux f = (w kappa / |det|) c^T (c g), mass weight w rho |det|
+      const double* G = A.jac + (e * Q + k) * 4;
+      const double g00 = G[0], g01 = G[1], g10 = G[2], g11 = G[3];
+      const double adet = fabs(g00 * g11 - g01 * g10);
+      const T c00 = from_double<T>(g11), c01 = from_double<T>(-g10);
+      const T c10 = from_double<T>(-g01), c11 = from_double<T>(g00);
+      const T sK = from_double<T>(A.alpha * wq * kap / adet);
+      const T h0 = c00 * g0 + c01 * g1, h1 = c10 * g0 + c11 * g1;
+      F[0][k] = sK * (c00 * h0 + c10 * h1);
+      F[1][k] = sK * (c01 * h0 + c11 * h1);
+      F[2][k] = from_double<T>(A.beta * wq * adet * rh) * u;
+    } else {
+      const T sK = from_double<T>(A.alpha * wq * kap);
+      F[0][k] = sK * g0;
+      F[1][k] = sK * g1;
+      F[2][k] = from_double<T>(A.beta * wq * rh) * u;
+    }
+  }
+  __syncthreads();
+  for (int it = tid; it < 2 * n * q; it += NT) {
+    const int c = it / (n * q), r = it % (n * q), a2 = r / q, q1 = r % q;
+    T acc = 0;
+#pragma unroll
+    for (int q2 = 0; q2 < q; ++q2) {
+      const T vy = tb[1][0][q2 * n + a2];
+      const int k = q1 + q * q2;
+      if (c == 0) {
+        mac(acc, vy, F[0][k]);
+      } else {
+        mac(acc, tb[1][1][q2 * n + a2], F[1][k]);
+        mac(acc, vy, F[2][k]);
+      }
+    }
+    S[c][r] = fin(acc);
+  }
+  __syncthreads();
+  store_t<T>* out = (store_t<T>*)A.scratch;
+  for (int a = tid; a < N; a += NT) {
+    const int a1 = a % n, a2 = a / n;
+    T acc = 0;
+#pragma unroll
+    for (int q1 = 0; q1 < q; ++q1) {
+      mac(acc, tb[0][1][q1 * n + a1], S[0][a2 * q + q1]);
+      mac(acc, tb[0][0][q1 * n + a1], S[1][a2 * q + q1]);
+    }
+    out[(int64_t)a * A.n_elem + e] = to_store<T>(fin(acc));
+  }
+}
+
+template <int P, int QG>
+cudaError_t run2(const ApplyArgs& a, cudaStream_t st) {
+  if (a.jac) k_apply2<double, P, QG, true><<<(unsigned)a.n_elem, 64, 0, st>>>(a);
+  else k_apply2<double, P, QG, false><<<(unsigned)a.n_elem, 64, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch2(const ApplyArgs& a, int p, int q, cudaStream_t st) {
+  const int dq = q - p;
+#define C2(PP)                                                \
+  if (p == PP && dq == 1) return run2<PP, PP + 1>(a, st);     \
+  if (p == PP && dq == 2) return run2<PP, PP + 2>(a, st);
+  C2(1) C2(2) C2(3) C2(4) C2(5)
+#undef C2
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, int P, int QG>
 cudaError_t run(const ApplyArgs& a, cudaStream_t st) {
   if (a.jac) k_apply3<T, P, QG, true><<<(unsigned)a.n_elem, 128, 0, st>>>(a);
@@ -214,11 +340,14 @@ cudaError_t dispatch(const ApplyArgs& a, int p, int q, cudaStream_t st) {
 }  // namespace
 
 bool apply_supported(int dim, int p, int q) {
+  if (dim == 2) return p >= 1 && p <= 5 && (q == p + 1 || q == p + 2);
   return dim == 3 && p >= 1 && p <= 5 && (q == p + 1 || (q == p + 2 && p <= 4));
 }
 
-cudaError_t launch_apply(const ApplyArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st) {
+cudaError_t launch_apply(const ApplyArgs& a, int dim, int p, int q, bool fp64, bool df,
+                         cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
+  if (dim == 2) return fp64 ? dispatch2(a, p, q, st) : cudaErrorInvalidValue;
   if (df) return dispatch<ff>(a, p, q, st);
   return fp64 ? dispatch<double>(a, p, q, st) : dispatch<float>(a, p, q, st);
 }

@@ -486,7 +486,7 @@ cudaError_t run_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
 template <typename T>
 cudaError_t dispatch_gather(const CsrPatch& c, const FnCouple* fc, const int* spans,
                             const void* scratch, void* y, cudaStream_t st) {
-  if (c.dim != 3) return cudaErrorInvalidValue;
+  // 2D: the missing direction has one function and one element (fn_couple)
   switch (c.p) {
     case 1: return run_gather<T, 1>(c, fc, spans, scratch, y, st);
     case 2: return run_gather<T, 2>(c, fc, spans, scratch, y, st);

@@ -194,6 +194,36 @@ def test_apply_matches_oracle(case, precision):
     plan.close()
 
 
+@pytest.mark.parametrize("curved", [False, True], ids=["identity", "general"])
+@pytest.mark.parametrize("p,dq", [(1, 1), (2, 1), (2, 2), (3, 1), (4, 2), (5, 1)])
+def test_apply_2d_matches_oracle(p, dq, curved):
+    """2D operator (FP64 plans; the FP32 forms are 3D): against the oracle's
+    element-matrix product, alpha K + beta M for three (alpha, beta), and
+    K 1 = 0 on a general map."""
+    q = p + dq
+    knots = [wl.open_uniform_knots(5, p), _nonuniform_knots(p, 70 + p)]
+    P = oracle.Patch(knots, p, q)
+    kappa = wl.lognormal(P.E * P.Q, 71)
+    rho = wl.lognormal(P.E * P.Q, 72)
+    G = None
+    if curved:
+        G = np.eye(2)[None] + 0.15 * wl.normal(4 * P.E * P.Q, 73).reshape(P.E * P.Q, 2, 2)
+    x = wl.normal(P.n_dofs, 74)
+    yK, yM = P.apply(x, kappa=kappa, rho=rho, G=G)
+    plan = IgaPlan(Patch(list(knots), p, q), method="sumfact", precision="fp64")
+    kt = torch.as_tensor(kappa, device=DEV)
+    rt = torch.as_tensor(rho, device=DEV)
+    jt = torch.as_tensor(G, device=DEV).reshape(-1) if curved else None
+    xt = torch.as_tensor(x, device=DEV)
+    for alpha, beta, ref in ((1.0, 0.0, yK), (0.0, 1.0, yM), (-0.25, 2.0, -0.25 * yK + 2.0 * yM)):
+        y = plan.apply(xt, kappa=kt, rho=rt, jac=jt, alpha=alpha, beta=beta).cpu().numpy()
+        assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max(), (alpha, beta)
+    ones = torch.ones(plan.n_dofs, dtype=torch.float64, device=DEV)
+    y1 = plan.apply(ones, kappa=kt, jac=jt).cpu().numpy()
+    assert np.abs(y1).max() <= 1e-12 * np.abs(yK).max()
+    plan.close()
+
+
 def test_apply_batch_matches_oracle():
     specs = _patch_sets()["3d_batch"]
     plan = _plan(specs)
