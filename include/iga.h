@@ -154,7 +154,8 @@ int iga_integrate(iga_plan_t plan, const double* kappa, const double* rho,
                   const double* jac, void* K_out, void* M_out, int32_t* dof_out,
                   void* cuda_stream);
 
-/* Matrix-free adjoint of J(kappa) = u^T K(kappa) v (not in the paper):
+/* Matrix-free adjoint of J(kappa) = u^T K(kappa) v (not in the paper; 3D,
+ * or 2D on IGA_FP64 plans):
  *   grad_kappa[k] = dJ/dkappa_k = w_k |det G_k| (G_k^{-T} grad u).(G_k^{-T} grad v)
  * at every quadrature point, computed by sum-factorized interpolation of u and
  * v from the basis tables (no element matrix is formed), and

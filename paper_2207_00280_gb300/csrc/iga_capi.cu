@@ -768,12 +768,12 @@ extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const d
     a.nf0 = pd.nf[0]; a.nf1 = pd.nf[1];
     a.dof_offset = pd.dof_offset;
     a.kappa = kappa ? kappa + pd.qp_offset : nullptr;
-    a.jac = jac ? jac + pd.qp_offset * 9 : nullptr;
+    a.jac = jac ? jac + pd.qp_offset * pd.dim * pd.dim : nullptr;
     a.u = u; a.v = v;
     a.grad = grad_kappa ? (char*)grad_kappa + gsz * pd.qp_offset : nullptr;
     a.partial = J_out ? P->d_partial : nullptr;
     a.partial_offset = pd.elem_offset;
-    e = launch_adjoint(a, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
+    e = launch_adjoint(a, pd.dim, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
   }
   if (e == cudaSuccess && J_out) e = launch_reduce_fixed(P->d_partial, P->info.n_elements, J_out, st);
   return finish(P, st, e);
@@ -1198,7 +1198,7 @@ extern "C" int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* ka
     a.grad = grad_kappa;
     a.partial = J_out ? scratch + kNaPartials : nullptr;
     a.partial_offset = 0;
-    e = launch_adjoint(a, p, q, true, false, st);
+    e = launch_adjoint(a, 3, p, q, true, false, st);
   }
   if (e == cudaSuccess && J_out) e = launch_reduce_fixed(scratch + kNaPartials, E, J_out, st);
   if (e != cudaSuccess) return map_cuda(e);

@@ -101,7 +101,7 @@ bool queue_both_fit(int p, int q, bool bf16);
 cudaError_t launch_sumfact_f32(const ElemArgs& a, int dim, int p, int q, bool bf16,
                                cudaStream_t st);
 
-// Matrix-free adjoint (3D): grad[e*Q + k] = dJ/dkappa, partial[partial_offset + e]
+// Matrix-free adjoint (3D; 2D for FP64 plans): grad[e*Q + k] = dJ/dkappa, partial[partial_offset + e]
 // = per-element sum of kappa * grad.  All array pointers are patch-local except
 // u, v (global dof vectors) and partial.
 struct AdjArgs {
@@ -112,14 +112,15 @@ struct AdjArgs {
   int nf0, nf1;
   int64_t dof_offset;
   const double* kappa;   // patch-local [E][Q] or null (= 1)
-  const double* jac;     // patch-local [E][Q][9] or null
+  const double* jac;     // patch-local [E][Q][d*d] or null
   const void* u;         // global [n_dofs], double or float
   const void* v;
   void* grad;            // patch-local [E][Q] or null
   double* partial;       // [n_elements] or null
   int64_t partial_offset;
 };
-cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgs& a, int dim, int p, int q, bool fp64, bool df,
+                           cudaStream_t st);
 cudaError_t launch_reduce_fixed(const double* partial, int64_t n, double* out, cudaStream_t st);
 bool adjoint_supported(int dim, int p, int q);
 

@@ -1,4 +1,4 @@
-// k_adjoint.cu -- matrix-free adjoint of J(kappa) = u^T K(kappa) v, 3D (not
+// k_adjoint.cu -- matrix-free adjoint of J(kappa) = u^T K(kappa) v, 3D and 2D (not
 // in the paper; it differentiates the stiffness of the weak form, Sec. 2.2).
 //
 // J is linear in kappa:  J = sum_q kappa_q g_q  with
@@ -160,6 +160,88 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
   }
 }
 
+// 2D (FP64 plans): u_e and v_e gathered, U[vec][s][a2][q1] = sum_a1 x[a1 + n a2]
+// B^s_x(q1)[a1] (value and derivative), at every point the reference
+// gradients (d_x: derivative in x with the y value; d_y: value in x with the
+// y derivative), g = w (G^{-T} grad u).(G^{-T} grad v) through the 2x2
+// cofactors, and the same fixed-order partial of kappa g as in 3D.
+template <int P, int QG, bool GEN>
+__global__ void __launch_bounds__(64) k_adjoint2(const AdjArgs A) {
+  constexpr int n = P + 1, q = QG, N = n * n, Q = q * q, NT = 64, REC = 2 * q * n + q;
+  __shared__ double rec[2 * REC];
+  __shared__ double ue[N], ve[N];
+  __shared__ double U[2][2][n * q];     // [vec][value, derivative in x][a2][q1]
+  __shared__ double red[NT / 32];
+  const int tid = threadIdx.x;
+  const int64_t e = blockIdx.x;
+  const int e1 = (int)(e % A.K1), e2 = (int)(e / A.K1);
+  for (int i = tid; i < 2 * REC; i += NT) {
+    const int d = i / REC, j = i - d * REC;
+    rec[i] = (d == 0 ? A.tab[0] + (int64_t)e1 * REC : A.tab[1] + (int64_t)e2 * REC)[j];
+  }
+  const int s1 = A.span[0][e1] - P, s2 = A.span[1][e2] - P;
+  for (int a = tid; a < N; a += NT) {
+    const int64_t g = A.dof_offset + (s1 + a % n) + (int64_t)A.nf0 * (s2 + a / n);
+    ue[a] = ((const double*)A.u)[g];
+    ve[a] = ((const double*)A.v)[g];
+  }
+  __syncthreads();
+  const double* vx = rec;               const double* dx = rec + q * n;
+  const double* vy = rec + REC;         const double* dy = vy + q * n;
+  for (int it = tid; it < 2 * n * q; it += NT) {
+    const int sd = it / (n * q), r = it % (n * q), a2 = r / q, q1 = r % q;
+    const double* F = (sd ? dx : vx) + q1 * n;
+    double au = 0.0, av = 0.0;
+#pragma unroll
+    for (int a1 = 0; a1 < n; ++a1) {
+      au = fma(ue[a1 + n * a2], F[a1], au);
+      av = fma(ve[a1 + n * a2], F[a1], av);
+    }
+    U[0][sd][r] = au;
+    U[1][sd][r] = av;
+  }
+  __syncthreads();
+  double part = 0.0;
+  for (int k = tid; k < Q; k += NT) {
+    const int q1 = k % q, q2 = k / q;
+    double gu0 = 0.0, gu1 = 0.0, gv0 = 0.0, gv1 = 0.0;
+#pragma unroll
+    for (int a2 = 0; a2 < n; ++a2) {
+      const double fy = vy[q2 * n + a2], dfy = dy[q2 * n + a2];
+      gu0 = fma(U[0][1][a2 * q + q1], fy, gu0);
+      gu1 = fma(U[0][0][a2 * q + q1], dfy, gu1);
+      gv0 = fma(U[1][1][a2 * q + q1], fy, gv0);
+      gv1 = fma(U[1][0][a2 * q + q1], dfy, gv1);
+    }
+    const double W = rec[2 * q * n + q1] * rec[REC + 2 * q * n + q2];
+    double gq;
+    if (GEN) {
+      // g = (W / |det|) (c gu) . (c gv),  c = [[g11, -g10], [-g01, g00]]: G^{-T} = c / det
+      const double* G = A.jac + (e * Q + k) * 4;
+      const double g00 = G[0], g01 = G[1], g10 = G[2], g11 = G[3];
+      const double adet = fabs(g00 * g11 - g01 * g10);
+      const double pu0 = g11 * gu0 - g10 * gu1, pu1 = -g01 * gu0 + g00 * gu1;
+      const double pv0 = g11 * gv0 - g10 * gv1, pv1 = -g01 * gv0 + g00 * gv1;
+      gq = W / adet * (pu0 * pv0 + pu1 * pv1);
+    } else {
+      gq = W * (gu0 * gv0 + gu1 * gv1);
+    }
+    if (A.grad) ((double*)A.grad)[e * Q + k] = gq;
+    if (A.partial) part += (A.kappa ? A.kappa[e * Q + k] : 1.0) * gq;
+  }
+  if (A.partial) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      A.partial[A.partial_offset + e] = s;
+    }
+  }
+}
+
 // One block sums partial[0..n) in a fixed order (strided per thread, then a
 // fixed tree) and writes the double result.
 __global__ void __launch_bounds__(1024) k_reduce_fixed(const double* __restrict__ partial,
@@ -203,11 +285,31 @@ cudaError_t dispatch(const AdjArgs& a, int p, int q, cudaStream_t st) {
 }  // namespace
 
 bool adjoint_supported(int dim, int p, int q) {
+  if (dim == 2) return p >= 1 && p <= 5 && (q == p + 1 || q == p + 2);
   return dim == 3 && p >= 1 && p <= 5 && (q == p + 1 || (q == p + 2 && p <= 4));
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a, int p, int q, bool fp64, bool df, cudaStream_t st) {
+template <int P, int QG>
+cudaError_t run2(const AdjArgs& a, cudaStream_t st) {
+  if (a.jac) k_adjoint2<P, QG, true><<<(unsigned)a.n_elem, 64, 0, st>>>(a);
+  else k_adjoint2<P, QG, false><<<(unsigned)a.n_elem, 64, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch2(const AdjArgs& a, int p, int q, cudaStream_t st) {
+  const int dq = q - p;
+#define C2(PP)                                              \
+  if (p == PP && dq == 1) return run2<PP, PP + 1>(a, st);   \
+  if (p == PP && dq == 2) return run2<PP, PP + 2>(a, st);
+  C2(1) C2(2) C2(3) C2(4) C2(5)
+#undef C2
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint(const AdjArgs& a, int dim, int p, int q, bool fp64, bool df,
+                           cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
+  if (dim == 2) return fp64 ? dispatch2(a, p, q, st) : cudaErrorInvalidValue;
   if (df) return dispatch<ff>(a, p, q, st);
   return fp64 ? dispatch<double>(a, p, q, st) : dispatch<float>(a, p, q, st);
 }

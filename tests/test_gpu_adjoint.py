@@ -53,6 +53,32 @@ def test_adjoint_vs_oracle(oracle_mod, p, dq, curved):
     assert abs(J32 - Jr) <= 1e-5 * np.abs(kappa * gr.reshape(-1)).sum()
 
 
+@pytest.mark.parametrize("curved", [False, True], ids=["identity", "general"])
+@pytest.mark.parametrize("p,dq", [(1, 1), (2, 1), (2, 2), (3, 1), (4, 2), (5, 1)])
+def test_adjoint_2d_vs_oracle(oracle_mod, p, dq, curved):
+    """2D adjoint (FP64 plans): g and J against the oracle; J also equals
+    u^T K v from the oracle's element matrices (a second oracle path)."""
+    q = p + dq
+    knots = [wl.open_uniform_knots(5, p), wl.open_uniform_knots(3, p)]
+    P = oracle_mod.Patch(knots, p, q)
+    kappa = wl.lognormal(P.E * P.Q, 930 + p)
+    u = wl.normal(P.n_dofs, 931)
+    v = wl.normal(P.n_dofs, 932)
+    G = None
+    if curved:
+        G = np.eye(2)[None] + 0.15 * wl.normal(4 * P.E * P.Q, 933).reshape(P.E * P.Q, 2, 2)
+    gr, Jr = P.adjoint(u, v, kappa=kappa, G=G)
+    Ke, _ = P.classical(kappa=kappa, G=G, mass=False)
+    dof = P.dofmap()
+    Jm = float(np.einsum("ea,eab,eb->", u[dof], Ke, v[dof]))
+    plan = IgaPlan(Patch(knots, p, q), method="sumfact", precision="fp64")
+    g, J = _adj(plan, kappa, u, v, G)
+    assert np.abs(g - gr.reshape(-1)).max() <= 1e-12 * np.abs(gr).max()
+    scale = np.abs(kappa * gr.reshape(-1)).sum()
+    assert abs(J - Jr) <= 1e-13 * scale and abs(J - Jm) <= 1e-12 * scale
+    plan.close()
+
+
 def test_adjoint_greville_identities():
     p, q, K = 3, 4, 4
     t = wl.open_uniform_knots(K, p)
