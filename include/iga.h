@@ -240,7 +240,7 @@ int iga_apply(iga_plan_t plan, const double* kappa, const double* rho, const dou
 int iga_integrate_grad(iga_plan_t plan, const double* jac, const void* GK, const void* GM,
                        void* grad_kappa, void* grad_rho, void* cuda_stream);
 
-/* Weighted quadrature for the mass matrix (3D, p <= 5; the variant Sec. 1.2
+/* Weighted quadrature for the mass matrix (2D and 3D, p <= 5; the variant Sec. 1.2
  * names as a further reduction of the integration cost, which the paper does
  * not define).  Each direction has one global point list: every element's
  * left end and midpoint, p+1 points in the p boundary elements at each end,
@@ -263,7 +263,7 @@ int iga_integrate_grad(iga_plan_t plan, const double* jac, const void* GK, const
 int iga_wq_points(iga_plan_t plan, int patch, int dir, double* x_out, int64_t* n_out);
 int iga_wq_mass(iga_plan_t plan, const double* c, double* values, void* cuda_stream);
 
-/* Weighted quadrature for the diffusion stiffness (3D, 2 <= p <= 4; the same
+/* Weighted quadrature for the diffusion stiffness (2D and 3D, 2 <= p <= 4; the same
  * variant extended to derivatives, not defined in the paper).  Besides the
  * mass rule above, each test function B_i has a derivative rule w'_{i,q} on
  * the same points: least-norm among the rules with sum_q w'_{i,q} B'_j(x_q) =
@@ -275,8 +275,8 @@ int iga_wq_mass(iga_plan_t plan, const double* c, double* values, void* cuda_str
  * R^(0) the mass rule, R^(1) the derivative rule, B^(0) = B, B^(1) = B': the
  * reference-gradient form int c grad B_i . grad B_j (c = kappa for the
  * identity map).  With c = 1 it is the exact stiffness.  FP64 plans only;
- * c and values as for iga_wq_mass.  IGA_ERR_UNSUPPORTED for 2D, p < 2 or
- * p > 4, or rule tables beyond shared memory. */
+ * c and values as for iga_wq_mass.  IGA_ERR_UNSUPPORTED for p < 2 or p > 4,
+ * or rule tables beyond shared memory. */
 int iga_wq_stiffness(iga_plan_t plan, const double* c, double* values, void* cuda_stream);
 
 /* With opts.profile = 1: synchronize on the last recorded event and return

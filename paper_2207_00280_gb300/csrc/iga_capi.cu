@@ -905,10 +905,27 @@ int wq_ensure(iga_plan_s* P) {
   P->wq_coef_off.assign(1, 0);
   for (int ip = 0; ip < P->n_patches && rc == IGA_OK; ++ip) {
     const PatchDev& pd = P->ph[ip];
-    if (pd.dim != 3 || pd.p > 5) { rc = IGA_ERR_UNSUPPORTED; break; }
+    if (pd.p > 5) { rc = IGA_ERR_UNSUPPORTED; break; }
     int64_t grid = 1;
     for (int k = 0; k < 3 && rc == IGA_OK; ++k) {
       iga_plan_s::WqDir& w = P->wq[(size_t)ip * 3 + k];
+      if (k >= pd.dim) {
+        // the missing direction of a 2D patch: one function, one point, a
+        // mass-rule product w B = 1 and a derivative-rule product 0, so the
+        // 3D row kernels give the 2D matrices
+        const int W = 2 * pd.p + 1;
+        w.x.assign(1, 0.0);
+        w.qmax = 1;
+        std::vector<int> qlo(1, 0), qn(1, 1);
+        std::vector<double> V(W, 0.0), V1(W, 0.0);
+        V[0] = 1.0;
+        cudaError_t e = upload(&w.d_qlo, qlo.data(), qlo.size());
+        if (e == cudaSuccess) e = upload(&w.d_qn, qn.data(), qn.size());
+        if (e == cudaSuccess) e = upload(&w.d_V, V.data(), V.size());
+        if (e == cudaSuccess) e = upload(&w.d_V1, V1.data(), V1.size());
+        if (e != cudaSuccess) { cudaGetLastError(); rc = map_cuda(e); }
+        continue;
+      }
       const CsrPatch& c = P->csr[ip];
       // the coupling records of this direction (the planner's host copy)
       std::vector<FnCouple> all(P->fc_host.begin() + c.fn_offset[k],
@@ -950,6 +967,7 @@ extern "C" int iga_wq_points(iga_plan_t P, int patch, int dir, double* x_out, in
     *n_out = P->wq_coef_off[patch + 1] - P->wq_coef_off[patch];
     return IGA_OK;
   }
+  if (dir >= P->ph[patch].dim) return IGA_ERR_ARG;
   const std::vector<double>& x = P->wq[(size_t)patch * 3 + dir].x;
   *n_out = (int64_t)x.size();
   if (x_out) std::memcpy(x_out, x.data(), sizeof(double) * x.size());

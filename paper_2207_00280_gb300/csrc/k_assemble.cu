@@ -532,7 +532,7 @@ cudaError_t run_wq_stiff(const WqPatchArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-bool wq_stiffness_supported(int dim, int p) { return dim == 3 && p >= 2 && p <= 4; }
+bool wq_stiffness_supported(int dim, int p) { return (dim == 2 || dim == 3) && p >= 2 && p <= 4; }
 
 template <typename T>
 cudaError_t wq_stiff_p(const WqPatchArgs& a, int p, cudaStream_t st) {
