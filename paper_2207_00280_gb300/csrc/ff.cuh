@@ -44,21 +44,20 @@ __device__ __forceinline__ ff& operator+=(ff& a, ff b) {
 }
 
 // x as hi + lo without FP64 arithmetic: hi = x with its mantissa cut to 24
-// bits (exact in FP32 within its exponent range), lo = the remaining 29 bits
-// as an integer, converted (rounded to 24 bits) and scaled by 2^(e - 1075).
-// Zeros and values outside the FP32 exponent range take the FP64 path.
+// bits (exact in FP32), lo = the remaining 29 bits as an integer, converted
+// (rounded to 24 bits) and scaled by 2^(e - 1075), both normal FP32 numbers
+// for biased exponents e in [949, 1150] (2^-74 <= |x| < 2^128).  Zeros and
+// values outside that range take the exact FP64 conversion.
 __device__ __forceinline__ ff split_d(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex < 897 || ex > 1150) return ff(x);
+  if (ex < 949 || ex > 1150) return ff(x);
   const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
   const unsigned mh = (unsigned)((b >> 29) & 0x7fffffu);
   const float h = __uint_as_float(sgn | ((unsigned)(ex - 896) << 23) | mh);
   const unsigned ml = (unsigned)(b & 0x1fffffffu);
-  const int sx = ex - 1075 + 127;   // biased exponent of 2^(e - 1075)
-  float l = sx >= 1 ? __uint2float_rn(ml) * __uint_as_float((unsigned)sx << 23) : 0.f;
-  if (sgn) l = -l;
-  return ff(h, l);
+  const float l = __uint2float_rn(ml) * __uint_as_float((unsigned)(ex - 948) << 23);
+  return ff(h, sgn ? -l : l);
 }
 
 // Dot products: mac(a, x, y) accumulates x * y into a; fin(a) is the value.
