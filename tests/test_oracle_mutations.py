@@ -64,6 +64,10 @@ MUTANTS = {
     "grad_mass_product": ("if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[b];",
                           "if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[a];",
                           "test_oracle_assembly.py"),
+    # element-matrix backward: every component of the trial gradient replaced by its x component
+    "grad_stiff_component": ("for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + i];",
+                             "for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + 0];",
+                             "test_oracle_assembly.py"),
     # sparsity pattern misses the first function of every element
     "pattern_drop": ("for (int b = 0; b < N; ++b)\n        if (mark[dof[b]] != i)",
                      "for (int b = 1; b < N; ++b)\n        if (mark[dof[b]] != i)", "test_oracle_assembly.py"),
