@@ -64,6 +64,8 @@ MUTANTS = {
     "grad_mass_product": ("if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[b];",
                           "if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[a];",
                           "test_oracle_assembly.py"),
+    # Algorithm 1: the trial function's y index taken from the test function
+    "classical_trial_index": ("int b = j1 + n * (j2 + n * j3);", "int b = j1 + n * (i2 + n * j3);"),
     # element-matrix backward: every component of the trial gradient replaced by its x component
     "grad_stiff_component": ("for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + i];",
                              "for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + 0];",
