@@ -389,6 +389,32 @@ def test_adjoint_greville_identities(oracle_mod):
     assert np.abs(g).max() <= 1e-14
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adjoint_affine_closed_form(oracle_mod, dim):
+    """A constant non-symmetric Jacobian G (an affine map of the unit square
+    or cube): the Greville interpolants of xi_i reproduce xi_i, whose
+    physical gradients are the columns of G^{-T}, so J(u = xi_i, v = xi_j)
+    with kappa = 1 equals (G^{-T} e_i).(G^{-T} e_j) |det G| exactly."""
+    p = 2
+    knots = [wl.open_uniform_knots(K, p) for K in (3, 4, 2)[:dim]]
+    P = oracle_mod.Patch(knots, p, p + 1)
+    Gc = np.array([[1.2, 0.3, -0.2], [-0.1, 0.9, 0.25], [0.15, -0.05, 1.1]])[:dim, :dim]
+    G = np.broadcast_to(Gc, (P.E * P.Q, dim, dim)).copy()
+    GinvT = np.linalg.inv(Gc).T
+    det = abs(np.linalg.det(Gc))
+    nf = [len(t) - p - 1 for t in knots]
+    idx = np.arange(P.n_dofs)
+    comp = [idx % nf[0], (idx // nf[0]) % nf[1]] + ([idx // (nf[0] * nf[1])] if dim == 3 else [])
+    xi = [_greville(knots[k], p)[comp[k]] for k in range(dim)]
+    ones = np.ones(P.E * P.Q)
+    for i in range(dim):
+        for j in range(dim):
+            g, J = P.adjoint(xi[i], xi[j], kappa=ones, G=G)
+            ref = float(GinvT[:, i] @ GinvT[:, j]) * det
+            assert J == pytest.approx(ref, rel=1e-12, abs=1e-14), (i, j)
+            assert g.sum() == pytest.approx(ref, rel=1e-12, abs=1e-14)
+
+
 @pytest.mark.parametrize("curved", [False, True])
 def test_adjoint_vs_matrices_and_fd(oracle_mod, curved):
     p, K = 2, 3
