@@ -87,6 +87,46 @@ def measured_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def fp_rate_probe(stream_ptr):
+    """Measured arithmetic rates of this GPU (include/iga_probe.h): FP64 FMA on
+    the CUDA cores, FP64 MMA (mma.sync m8n8k4) and FP32 FMA, each a ~0.1-0.3 s
+    kernel over all SMs, best of three.  The FP64 kernels of this library are
+    bound by the first; the second is the FP64 tensor path they do not use."""
+    from paper_2207_00280_gb300 import capi
+    out = {}
+    for name, kind, iters in (("dfma", capi.IGA_PROBE_DFMA, 1 << 16),
+                              ("dmma", capi.IGA_PROBE_DMMA, 1 << 14),
+                              ("ffma", capi.IGA_PROBE_FFMA, 1 << 20)):
+        best = 0.0
+        for ctas in (2, 4):
+            for _ in range(3):
+                ms, fl = capi.iga_probe_rate(kind, iters, ctas, stream_ptr)
+                best = max(best, fl / (ms * 1e-3) / 1e12)
+        out[f"{name}_tflops"] = round(best, 4)
+    out["how"] = ("iga_probe_rate: independent FMA chains (8 per thread) or MMA "
+                  "accumulators (4 per warp), 2 and 4 CTAs of 256 threads per SM, best of 3 "
+                  "CUDA-event timings each")
+    return out
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms in a thread."""
 
@@ -188,9 +228,13 @@ def weak_scaling_value(ws, units_per_rank, steps, max_ms):
     return ws * units_per_rank * steps / (max_ms / 1e3)
 
 
-def cpu_baseline_oracle(workload, budget_s=12.0, method="sumfact", max_elems=None):
-    """Time the FP64 oracle (as it stands, one core) on a bounded sample of the
-    workload's elements; returns elements/s and a description."""
+def cpu_baseline_oracle(workload, budget_s=12.0, method="sumfact", max_elems=None, threads=1):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload's
+    elements; returns elements/s, the elements done and the seconds taken.
+    threads > 1 runs chunks of elements concurrently on that many host threads
+    (the oracle has no global state and ctypes releases the GIL during its
+    calls), the over-elements parallelism of the paper's OpenMP runs."""
+    import concurrent.futures as cf
     import numpy as np
     import oracle
     from paper_2207_00280_gb300 import workloads as wl
@@ -202,14 +246,51 @@ def cpu_baseline_oracle(workload, budget_s=12.0, method="sumfact", max_elems=Non
     fn = P.sumfact if method == "sumfact" else P.classical
     rng = np.random.default_rng(2207)
     order = rng.permutation(sp.E)
-    done, t0, chunk = 0, time.perf_counter(), 64
+    chunk = 64 if method == "sumfact" else 8
     limit = max_elems or sp.E
-    while done < limit and time.perf_counter() - t0 < budget_s:
-        el = order[done:done + chunk]
-        fn(el, kappa=kappa, G=G, stiffness=True, mass=G is None)
-        done += len(el)
+    done, t0 = 0, time.perf_counter()
+    if threads <= 1:
+        while done < limit and time.perf_counter() - t0 < budget_s:
+            el = order[done:done + chunk]
+            fn(el, kappa=kappa, G=G, stiffness=True, mass=G is None)
+            done += len(el)
+        return done / (time.perf_counter() - t0), done, time.perf_counter() - t0
+    lock = threading.Lock()
+    state = {"next": 0, "done": 0}
+
+    def worker():
+        while time.perf_counter() - t0 < budget_s:
+            with lock:
+                a = state["next"]
+                if a >= limit:
+                    return
+                state["next"] = a + chunk
+            el = order[a:a + chunk]
+            fn(el, kappa=kappa, G=G, stiffness=True, mass=G is None)
+            with lock:
+                state["done"] += len(el)
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = [ex.submit(worker) for _ in range(threads)]
+        for f in futs:
+            f.result()
     dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    return state["done"] / dt, state["done"], dt
+
+
+def cpu_baselines(workload, E, seconds):
+    """The oracle's Algorithm 2 (sum factorization) and Algorithm 1 (classical)
+    on one host thread and on every host core, each on a bounded seeded sample
+    of the workload's elements."""
+    cores = os.cpu_count() or 1
+    res = {}
+    for meth in ("sumfact", "classical"):
+        for th in (1, cores):
+            rate, done, dt = cpu_baseline_oracle(workload, budget_s=seconds, method=meth,
+                                                 threads=th)
+            res[f"{meth}_{'1_thread' if th == 1 else 'all_cores'}"] = {
+                "value": round(rate, 2), "threads": th, "elements": done, "seconds": round(dt, 2)}
+    return res, cores
 
 
 def run_ours(args, ws, rank, local):
@@ -236,6 +317,10 @@ def run_ours(args, ws, rank, local):
 
     def step():
         plan.integrate(kappa=kappa, jac=jac, K=K, M=M, dof=D, stream=stream)
+
+    # measured FP64/FP32 rates of this GPU, before the warm-up (a few seconds)
+    import ctypes
+    probe = fp_rate_probe(ctypes.c_void_p(stream.cuda_stream)) if args.probe else None
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -293,6 +378,16 @@ def run_ours(args, ws, rank, local):
                 "peak_source": src,
                 "hbm_frac": round(b_el * E / (launch_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                 "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src}
+        if args.method == "sumfact" and not general:
+            # the same time under the count of all d^2 stiffness terms (the
+            # off-diagonal ones are identically zero for the identity map)
+            f_gen = flops_per_element(len(sp.knots), sp.p, sp.q, True, mass, True)
+            roof["flop_per_element_all_terms"] = f_gen
+            roof["frac_all_terms"] = round(f_gen * E / (launch_ms * 1e-3) / 1e12 / peak_tf, 4)
+        if probe and args.precision == "fp64":
+            roof["measured_dfma_tflops"] = probe["dfma_tflops"]
+            roof["frac_of_measured_dfma"] = round(achieved / probe["dfma_tflops"], 4)
+            roof["measured_dmma_tflops"] = probe["dmma_tflops"]
     else:
         ach = b_el * E / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
@@ -397,12 +492,15 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if args.cpu_baseline and rank == 0 and ws == 1:
-        rate, done, dt = cpu_baseline_oracle(args.workload, budget_s=args.cpu_seconds,
-                                             method=args.method if args.method == "classical" else "sumfact")
-        cpu = {"value": round(rate, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{done} of {E} elements (seeded permutation), oracle "
-                         f"{'Algorithm 2 sum factorization' if args.method == 'sumfact' else 'Algorithm 1 classical'}"
-                         f", FP64, one thread, {dt:.1f} s"}
+        per, cores = cpu_baselines(args.workload, E, args.cpu_seconds / 4)
+        key = ("sumfact" if args.method == "sumfact" else "classical") + "_all_cores"
+        cpu = {"value": per[key]["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "cpu_model": cpu_model(),
+               "sample": (f"{per[key]['elements']} of {E} elements (seeded permutation), FP64 oracle "
+                          f"{'Algorithm 2 sum factorization' if args.method == 'sumfact' else 'Algorithm 1 classical'}"
+                          f", chunks of elements on {cores} host threads, {per[key]['seconds']} s"),
+               "runs": per,
+               "note": "each run: a bounded seeded sample of the workload's elements; elements/s"}
 
     n_kernels_per_step = 3  # basis tables, dof map, element matrices
     line = {
@@ -421,6 +519,7 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "clocks": clocks, "e2e": e2e, "gpu_launches": n_kernels_per_step * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "forms": forms or None,
+        "fp_rate_probe": probe,
         "wall_s_timed_region": round(t_wall, 4),
         "kernel_ms_per_launch": round(launch_ms, 4),
     }
@@ -523,6 +622,7 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
                 v["speedup_vs_classical_fp64"] = round(base / v["ms_per_step"], 3)
     if not args.extra_forms:
         return forms
+    forms["3d_p4_48_curved"] = measure_curved_p4(stream, flush, dev)
     # 2D p=2 16x16 (256 elements, kappa = 1): launch-latency bound, reported in microseconds
     W2 = wl.WORKLOADS["2d_p2_16"]
     s2 = W2.spec
@@ -581,6 +681,68 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
     forms["wq_mass_3d_p3_32"] = measure_wq(W, stream, flush, dev)
     forms["grad_3d_p3_32"] = measure_grad(W, stream, flush, dev)
     return forms
+
+
+def measure_curved_p4(stream, flush, dev):
+    """3D p=4, 48^3 elements, 5^3 Gauss points, the curved map, seeded lognormal
+    kappa: the stiffness by sum factorization in FP64, float-float (FP64_DF
+    plan), FP32 and BF16, and by FP64 classical integration.  Each form gets its
+    step time, the element kernel's own time (CUDA events around it), its
+    roofline fraction (FP64 issue rate for FP64 and classical, the float-float
+    rate for FP64_DF, HBM for FP32/BF16, whose bytes are the output) and its
+    speed-up over FP64 classical."""
+    import numpy as np
+    import torch
+    from paper_2207_00280_gb300 import workloads as wl
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+    W3 = wl.WORKLOADS["3d_p4_48_curved"]
+    sp = W3.spec
+    E = sp.E
+    kappa = torch.as_tensor(W3.kappa(), device=dev)
+    jac = torch.as_tensor(np.ascontiguousarray(W3.jacobian()), device=dev).reshape(-1)
+    peaks = measured_peaks()[0]
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = N_SM * DFMA_PER_SM_CLK * 2 * mhz * 1e6
+    df_peak = N_SM * 128 * mhz * 1e6 / DF_OPS_PER_FMA * 2
+    f_sf = flops_per_element(3, sp.p, sp.q, True, False, True)
+    f_cl = classical_flops_per_element(3, sp.p, sp.q, True, False)
+    out = {"elements": E, "degree": sp.p, "gauss_per_dir": sp.q, "geometry": "curved",
+           "matrices": "stiffness", "flop_per_element_sumfact": f_sf,
+           "flop_per_element_classical": f_cl}
+    for meth, pr in (("classical", "fp64"), ("sumfact", "fp64"), ("sumfact", "fp64_df"),
+                     ("sumfact", "fp32"), ("sumfact", "bf16")):
+        key = f"{meth}_{pr}"
+        pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method=meth, precision=pr, mass=False,
+                     stiffness=True, blocking=False, profile=True)
+        K, _, _ = pl.empty_outputs(device=dev, dof=False)
+        pl.integrate(kappa=kappa, jac=jac, K=K, stream=stream)
+        torch.cuda.synchronize(dev)
+        pl.profile_read()
+        ms = _time_steps(lambda: pl.integrate(kappa=kappa, jac=jac, K=K, stream=stream),
+                         3 if meth == "classical" else 5, stream, flush)
+        kern_ms, launches = pl.profile_read()
+        kms = kern_ms / max(1, launches)
+        esz = 8 if pr in ("fp64", "fp64_df") else 4
+        b_el = bytes_per_element(3, sp.p, sp.q, esz, True, False, True, dof=False)
+        ent = {"ms_per_step": round(ms, 4), "kernel_ms": round(kms, 4),
+               "value": round(E / (ms * 1e-3), 1),
+               "hbm_frac": round(b_el * E / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+               "bytes_per_element": b_el, **FORM_ERR.get(key, {})}
+        f_el = f_cl if meth == "classical" else f_sf
+        if pr == "fp64":
+            ent["fp64_frac"] = round(f_el * E / (kms * 1e-3) / fp64_peak, 4)
+        elif pr == "fp64_df":
+            ent["float_float_frac"] = round(f_el * E / (kms * 1e-3) / df_peak, 4)
+        ent["roofline_frac"] = ent.get("fp64_frac", ent.get("float_float_frac", ent["hbm_frac"]))
+        out[key] = ent
+        del K
+        pl.close()
+        torch.cuda.empty_cache()
+    base = out["classical_fp64"]["ms_per_step"]
+    for k, v in out.items():
+        if isinstance(v, dict) and "ms_per_step" in v:
+            v["speedup_vs_classical_fp64"] = round(base / v["ms_per_step"], 3)
+    return out
 
 
 def wq_flops(knots, p, xs, stiffness=False):
@@ -858,7 +1020,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-extra-forms", dest="extra_forms", action="store_false")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-probe", dest="probe", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=24.0)
     ap.add_argument("--ref-elements", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:

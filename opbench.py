@@ -2,7 +2,7 @@
 workload, times it with CUDA events (L2 flushed before every step) and prints
 one JSON line.  Used for profiling single kernels, e.g.
 
-  python -m paper_2207_00280_gb300.opbench --op assemble --workload 3d_p3_16 --precision fp32
+  python opbench.py --op assemble --workload 3d_p3_16 --precision fp32
 
 Operations: integrate (element matrices), assemble (CSR values of the stiffness
 from its element matrices, integrated once before timing), apply (y = K x + M x),
@@ -20,8 +20,8 @@ import statistics
 import numpy as np
 import torch
 
-from . import workloads as wl
-from .plan import IgaPlan, Patch
+from paper_2207_00280_gb300 import workloads as wl
+from paper_2207_00280_gb300.plan import IgaPlan, Patch
 
 L2_FLUSH_BYTES = 2 * 129 * 1024 * 1024
 

@@ -37,13 +37,18 @@ IGA_SCHED_AUTO = 0
 IGA_SCHED_PER_PATCH = 1
 IGA_SCHED_PERSISTENT = 2
 IGA_SCHED_PERSISTENT_GRAPH = 3
+IGA_PROBE_DFMA = 0
+IGA_PROBE_DMMA = 1
+IGA_PROBE_FFMA = 2
 
-# Every exported symbol of include/iga.h (checked by tests/test_capi_symbols.py).
+# Every exported symbol of include/iga.h and include/iga_probe.h (checked by
+# tests/test_capi_host.py).
 EXPORTED = ("iga_plan", "iga_integrate", "iga_integrate_backward", "iga_integrate_grad",
             "iga_basis_tables",
             "iga_csr_pattern", "iga_assemble", "iga_apply", "iga_wq_points", "iga_wq_mass",
             "iga_wq_stiffness",
-            "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str")
+            "iga_profile_read", "iga_adjoint_noalloc", "iga_destroy", "iga_status_str",
+            "iga_probe_rate")
 
 
 class IgaError(RuntimeError):
@@ -124,7 +129,9 @@ def lib() -> ctypes.CDLL:
             L.iga_destroy.restype = i32
             L.iga_status_str.argtypes = [i32]
             L.iga_status_str.restype = ctypes.c_char_p
-            _ = i64
+            L.iga_probe_rate.argtypes = [i32, i64, i32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), vp]
+            L.iga_probe_rate.restype = i32
             _lib = L
     return _lib
 
@@ -197,3 +204,14 @@ def iga_profile_read(plan):
 
 def iga_destroy(plan) -> int:
     return lib().iga_destroy(plan)
+
+
+def iga_probe_rate(kind: int, iters: int, ctas_per_sm: int, stream) -> tuple:
+    """(device ms, flops) of one arithmetic-rate probe (include/iga_probe.h)."""
+    ms = ctypes.c_double()
+    fl = ctypes.c_double()
+    rc = lib().iga_probe_rate(int(kind), int(iters), int(ctas_per_sm), ctypes.byref(ms),
+                              ctypes.byref(fl), stream)
+    if rc != IGA_OK:
+        raise IgaError(rc, "iga_probe_rate")
+    return ms.value, fl.value

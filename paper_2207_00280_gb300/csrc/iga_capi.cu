@@ -1093,9 +1093,47 @@ constexpr int64_t kNaDoubles = kNaPartials + kNaMaxElements;      // 3.7 MiB in 
 // library, kept until the process exits and shared by every call.
 static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
 
-// Per-device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch per CUDA context.  The address belongs
+// to the context that loaded the module: a cudaDeviceReset, or a context the
+// caller created through the driver API, gets a new one.  The cache is keyed by
+// the context's process-unique id (cuCtxGetId), which is never reused, so a
+// stale address is never handed to a kernel.  The two driver calls are reached
+// through cudaGetDriverEntryPointByVersion, so the library does not link libcuda.
+typedef int (*PfnCtxGetCurrent)(void** ctx);
+typedef int (*PfnCtxGetId)(void* ctx, unsigned long long* id);
 std::mutex g_na_mu;
-double* g_na_ptr[64] = {nullptr};
+PfnCtxGetCurrent g_ctx_current = nullptr;
+PfnCtxGetId g_ctx_id = nullptr;
+std::vector<std::pair<unsigned long long, double*>> g_na_ptr;
+
+// Id of the context current on this thread (created by the runtime if none
+// is); false if the driver entry points are unavailable.
+bool current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+      return false;
+    g_ctx_current = (PfnCtxGetCurrent)f0;
+    g_ctx_id = (PfnCtxGetId)f1;
+  }
+  void* ctx = nullptr;
+  if (g_ctx_current(&ctx) != 0) return false;
+  if (!ctx) {
+    // no context yet on this thread: cudaSetDevice makes the runtime's
+    // primary context of the current device current (CUDA >= 12)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess ||
+        g_ctx_current(&ctx) != 0 || !ctx)
+      return false;
+  }
+  return g_ctx_id(ctx, id) == 0;
+}
 
 struct NaParams {
   double knots[3][kNaMaxKnots];
@@ -1169,18 +1207,20 @@ extern "C" int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* ka
   }
   if (E > kNaMaxElements || tab > kNaTableDoubles) return IGA_ERR_TOO_LARGE;
 
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return IGA_ERR_CUDA;
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    unsigned long long id = 0;
+    if (!current_context_id(&id)) return IGA_ERR_CUDA;
+    for (const auto& kv : g_na_ptr)
+      if (kv.first == id) scratch = kv.second;
+    if (!scratch) {
       void* ptr = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess || !ptr) return IGA_ERR_CUDA;
-      g_na_ptr[dev] = (double*)ptr;
+      scratch = (double*)ptr;
+      g_na_ptr.push_back({id, scratch});
     }
-    scratch = g_na_ptr[dev];
   }
   NaParams P;
   for (int k = 0; k < 3; ++k) {

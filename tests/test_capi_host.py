@@ -150,3 +150,21 @@ def test_valid_plan_without_gpu_reports_cuda_error(capi):
     d, keep = _desc(capi)
     rc = _plan_rc(capi, [d], _opts(capi))
     assert rc in (capi.IGA_OK, capi.IGA_ERR_CUDA)
+
+
+def test_noalloc_size_limits_on_host(capi):
+    """iga_adjoint_noalloc rejects a patch beyond its fixed scratch on the host,
+    before any CUDA call: more knots per direction than the scratch holds, and
+    more elements (p = 1, 70^3 = 343,000 > 262,144).  The pointers are never
+    dereferenced on these paths."""
+    from paper_2207_00280_gb300 import workloads as wl
+    L = capi.lib()
+    dummy = ctypes.c_void_p(64)
+    cases = [
+        ([wl.open_uniform_knots(1100, 3), wl.open_uniform_knots(2, 3), wl.open_uniform_knots(2, 3)], 3, 4),
+        ([wl.open_uniform_knots(70, 1)] * 3, 1, 2),
+    ]
+    for knots, p, q in cases:
+        d, keep = _desc(capi, p=p, q=q, knots=knots)
+        rc = L.iga_adjoint_noalloc(ctypes.byref(d), dummy, None, dummy, dummy, dummy, None, None)
+        assert rc == capi.IGA_ERR_TOO_LARGE, (p, q, rc)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import run_gpu
+from gpu_util import sample_elements, run_gpu
 from paper_2207_00280_gb300 import workloads as wl
 from paper_2207_00280_gb300.autograd import iga_bilinear
 from paper_2207_00280_gb300.plan import IgaPlan, Patch
@@ -130,14 +130,22 @@ def test_3d_p3_40_autograd_and_fd(oracle_mod, prec):
     assert torch.isfinite(g).all()
     # J = kappa . g exactly (linearity), any precision
     assert float((kappa.detach() * g).sum()) == pytest.approx(float(J), rel=1e-5 if prec == "fp32" else 1e-12)
-    # sampled elements against the oracle's analytic gradient
+    # a seeded 1% sample of the elements plus the corners against the oracle's
+    # analytic gradient, point by point: |g - g_oracle| <= tol sqrt(g_uu g_vv)
+    # with g_uu = w |det G| |G^{-T} grad u|^2 (Cauchy--Schwarz bounds |g| by it,
+    # so the bound is relative to the magnitudes that meet at the point and
+    # stays meaningful where the dot product cancels)
     P = oracle_mod.Patch(sp.knots, sp.p, sp.q)
-    el = np.array([0, 1, 39, 1600, 31999, 63999], dtype=np.int64)
-    gr, _ = P.adjoint(u.double().cpu().numpy(), v.double().cpu().numpy(),
-                      kappa=kappa.detach().cpu().numpy(), elems=el)
-    gs = g.view(sp.E, sp.Q)[torch.as_tensor(el, device=dev)].cpu().numpy()
+    el = sample_elements(sp.E, 0.01, seed=wl.SEED_ADJ_KAPPA, K=40)
+    uh, vh = u.double().cpu().numpy(), v.double().cpu().numpy()
+    gr, _ = P.adjoint(uh, vh, kappa=kappa.detach().cpu().numpy(), elems=el)
+    guu, _ = P.adjoint(uh, uh, elems=el)
+    gvv, _ = P.adjoint(vh, vh, elems=el)
+    gs = g.view(sp.E, sp.Q)[torch.as_tensor(el, device=dev)].double().cpu().numpy()
     tol = 1e-12 if prec == "fp64" else 1e-5
-    assert np.abs(gs - gr).max() <= tol * np.abs(gr).max() * 4
+    ratio = np.abs(gs - gr) / (tol * np.sqrt(guu * gvv))
+    print(f"{prec} adjoint 40^3: {gr.size} points, worst error / bound {ratio.max():.3e}")
+    assert ratio.max() <= 1.0
     if prec == "fp64":
         rng = np.random.default_rng(wl.SEED_ADJ_FD)
         pts = rng.choice(sp.E * sp.Q, size=1000, replace=False)

@@ -69,17 +69,45 @@ def test_persistent_equals_per_patch_and_oracle(oracle_mod, prec):
         np.testing.assert_array_equal(dof, P.dofmap(el) + plan.dof_offset[i])
 
 
-def test_64_patch_batch_full():
+def test_64_patch_batch_full(oracle_mod):
     """64 patches, p ~ U{1..5}, elements per side ~ U{4..24} (seeded), q = p+1,
-    lognormal kappa, FP32 mass + stiffness: one persistent CUDA-graph launch
-    equals the 64 per-patch launches bit for bit."""
+    lognormal kappa, FP32 mass + stiffness (the benchmark's batch): one
+    persistent CUDA-graph launch equals the 64 per-patch launches bit for bit,
+    and a seeded sample of every patch's elements (its 8 corners and 4 random
+    elements; every patch of every degree, so each p = 5 patch) matches the
+    oracle within the FP32 tolerance, dof maps bit-exact with the patch offset."""
     specs = wl.batch_specs()
     nqp = sum(s.E * s.Q for s in specs)
     kappa = torch.as_tensor(wl.lognormal(nqp, wl.SEED_BATCH_KAPPA), device=dev)
     a = _batch(specs, kappa, "per_patch")
     b = _batch(specs, kappa, "graph")
     assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2]) and torch.equal(a[3], b[3])
-    assert torch.isfinite(b[1]).all() and torch.isfinite(b[2]).all()
+    del a
+    plan, K, M, D = b
+    assert torch.isfinite(K).all() and torch.isfinite(M).all()
+    assert sum(1 for s in specs if s.p == 5) > 0
+    kh = kappa.cpu().numpy()
+    rng = np.random.default_rng(2209)
+    worst = {}
+    for i, s in enumerate(specs):
+        P = oracle_mod.Patch(s.knots, s.p, s.q)
+        Kk = s.K
+        corners = {c0 + Kk * (c1 + Kk * c2) for c0 in (0, Kk - 1) for c1 in (0, Kk - 1)
+                   for c2 in (0, Kk - 1)}
+        el = np.array(sorted(corners | set(rng.choice(P.E, size=4, replace=False).tolist())),
+                      dtype=np.int64)
+        q0, q1 = plan.qp_offset[i], plan.qp_offset[i + 1]
+        Kr, Mr = P.sumfact(el, kappa=kh[q0:q1])
+        idx = torch.as_tensor(el, device=dev)
+        Kg = plan.patch_view(K, i)[idx].cpu().numpy()
+        Mg = plan.patch_view(M, i)[idx].cpu().numpy()
+        ek, em = rel_frob(Kg, Kr), rel_frob(Mg, Mr)
+        worst[s.p] = max(worst.get(s.p, 0.0), ek, em)
+        assert ek <= FP32_TOL and em <= FP32_TOL, (i, s, ek, em)
+        d0, d1 = plan.dofmap_offset[i], plan.dofmap_offset[i + 1]
+        dof = D[d0:d1].view(-1, P.N)[idx].cpu().numpy()
+        np.testing.assert_array_equal(dof, P.dofmap(el) + plan.dof_offset[i])
+    print("64-patch batch, worst FP32 error per degree:", worst)
 
 
 def test_curved_batch_stiffness_only(oracle_mod):

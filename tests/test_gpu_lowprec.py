@@ -5,12 +5,12 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import BF16_TOL, FP32_TOL, rel_frob, run_gpu, sample_elements
+from gpu_util import BF16_TOL, FP32_TOL, FP64_TOL, rel_frob, run_gpu, sample_elements
 from paper_2207_00280_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": FP32_TOL, "bf16": BF16_TOL}
+TOL = {"fp32": FP32_TOL, "bf16": BF16_TOL, "fp64": FP64_TOL, "fp64_df": FP64_TOL}
 
 
 def _cmp(oracle_mod, knots, p, q, kappa, rho, G, prec, mass=True, stiffness=True, elems=None):
@@ -60,23 +60,39 @@ def test_single_matrix_modes(oracle_mod, prec, which):
          stiffness=which == "stiffness")
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+_ORACLE_48 = {}
+
+
+def _oracle_48(oracle_mod, W, el, kappa, G):
+    """The oracle's stiffness of the sampled 48^3 elements, computed once for
+    every precision."""
+    if "K" not in _ORACLE_48:
+        sp = W.spec
+        P = oracle_mod.Patch(sp.knots, sp.p, sp.q)
+        _ORACLE_48["K"] = P.sumfact(el, kappa=kappa, G=G, mass=False)[0]
+        _ORACLE_48["dof"] = P.dofmap()
+    return _ORACLE_48["K"], _ORACLE_48["dof"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_df", "fp32", "bf16"])
 def test_3d_p4_48_curved_full_size(oracle_mod, prec):
-    """3D, p=4, 48^3 elements, 5^3 Gauss points, cyclic sine map, lognormal kappa:
-    the stiffness of every element is computed; a seeded 1% sample plus the
-    corners is compared with the oracle, K 1 = 0 is checked on all elements."""
+    """3D, p=4, 48^3 elements, 5^3 Gauss points, cyclic sine map, lognormal kappa,
+    in the benchmark's launch: the stiffness of every element is computed; a
+    seeded 1% sample plus the corners is compared with the oracle, K 1 = 0 is
+    checked on every element, and the dof map of every element is compared
+    with the oracle's bit for bit."""
     W = wl.WORKLOADS["3d_p4_48_curved"]
     sp = W.spec
     kappa = W.kappa()
     G = W.jacobian()
     out = run_gpu(sp.knots, sp.p, sp.q, kappa=kappa, G=G, precision=prec, mass=False)
     K = out["K"]
-    one = torch.ones(sp.N, dtype=torch.float32, device="cuda")
+    one = torch.ones(sp.N, dtype=K.dtype, device="cuda")
     r = (K @ one).abs().amax(dim=1) / K.flatten(1).norm(dim=1)
-    assert float(r.max()) <= TOL[prec]
+    assert float(r.max()) <= (1e-13 if prec in ("fp64", "fp64_df") else TOL[prec])
     el = sample_elements(sp.E, 0.01, seed=2208, K=48)
-    P = oracle_mod.Patch(sp.knots, sp.p, sp.q)
-    Kr, _ = P.sumfact(el, kappa=kappa, G=G, mass=False)
+    Kr, dof = _oracle_48(oracle_mod, W, el, kappa, G)
     err = rel_frob(K[torch.as_tensor(el, device="cuda")].cpu().numpy(), Kr)
     print(f"{prec} 48^3 p=4 curved stiffness: max rel Frobenius error {err:.3e}")
     assert err <= TOL[prec]
+    np.testing.assert_array_equal(out["dof"].cpu().numpy(), dof)
