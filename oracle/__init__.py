@@ -41,7 +41,8 @@ def build(force: bool = False) -> str:
 
 class _Patch(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
-                ("m", ctypes.c_int * 3), ("t", ctypes.c_void_p * 3)]
+                ("m", ctypes.c_int * 3), ("t", ctypes.c_void_p * 3),
+                ("pd", ctypes.c_int * 3), ("qd", ctypes.c_int * 3)]
 
 
 def lib():
@@ -164,27 +165,45 @@ def wq_weights(t, p: int, x, deriv: bool = False) -> np.ndarray:
     return W
 
 
-class Patch:
-    """One tensor-product patch: dimension, degree, Gauss points, knot vectors."""
+def _per_dir(x, dim):
+    if np.ndim(x) == 0:
+        return [int(x)] * dim
+    x = [int(v) for v in x]
+    if len(x) != dim:
+        raise ValueError(f"expected {dim} values per direction")
+    return x
 
-    def __init__(self, knots, p: int, q: int):
+
+class Patch:
+    """One tensor-product patch: dimension, knot vectors, and the degree and
+    Gauss points of each direction (an int for all directions, or one per
+    direction)."""
+
+    def __init__(self, knots, p, q):
         self.knots = [_f64(t) for t in knots]
         self.dim = len(self.knots)
         if self.dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")
-        self.p, self.q = int(p), int(q)
-        self.n = self.p + 1
-        self.N = self.n ** self.dim
-        self.Q = self.q ** self.dim
-        self.n_el = [len(spans(t, p)) for t in self.knots]
+        self.pd = _per_dir(p, self.dim)
+        self.qd = _per_dir(q, self.dim)
+        # p, q, n: the common value when every direction has the same one
+        self.p = self.pd[0] if len(set(self.pd)) == 1 else None
+        self.q = self.qd[0] if len(set(self.qd)) == 1 else None
+        self.n = self.p + 1 if self.p is not None else None
+        self.nd = [pk + 1 for pk in self.pd]
+        self.N = int(np.prod(self.nd))
+        self.Q = int(np.prod(self.qd))
+        self.n_el = [len(spans(t, pk)) for t, pk in zip(self.knots, self.pd)]
         self.E = int(np.prod(self.n_el))
-        self.n_fun = [len(t) - self.p - 1 for t in self.knots]
+        self.n_fun = [len(t) - pk - 1 for t, pk in zip(self.knots, self.pd)]
         self.n_dofs = int(np.prod(self.n_fun))
         s = _Patch()
-        s.dim, s.p, s.q = self.dim, self.p, self.q
+        s.dim, s.p, s.q = self.dim, self.pd[0], self.qd[0]
         for k, t in enumerate(self.knots):
             s.m[k] = len(t)
             s.t[k] = t.ctypes.data
+            s.pd[k] = self.pd[k]
+            s.qd[k] = self.qd[k]
         self._s = s
 
     def _elems(self, elems):

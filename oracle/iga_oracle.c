@@ -145,25 +145,38 @@ void ora_basis_1d(const double* t, int p, int s, int q, double* xi, double* w,
 /* ------------------------------------------------------------------------ */
 /* Shared bookkeeping for the element routines.                              */
 /* ------------------------------------------------------------------------ */
+/* Per direction k: degree p[k], n[k] = p[k]+1 functions per element, q[k]
+ * Gauss points (eq. 10 takes P_k points in direction k).  A direction beyond
+ * the patch's dimension has n = q = 1 so that the index products hold. */
 typedef struct {
-  int d, p, n, q, N, Q;
+  int d, p[3], n[3], q[3], N, Q;
   int K[3];           /* elements per direction */
   int* spans[3];
 } layout;
 
 static int make_layout(const ora_patch* pt, layout* L) {
-  if (!pt || (pt->dim != 2 && pt->dim != 3) || pt->p < 1 || pt->p > 16 || pt->q < 1 || pt->q > 64)
-    return -1;
-  L->d = pt->dim; L->p = pt->p; L->n = pt->p + 1; L->q = pt->q;
+  for (int k = 0; k < 3; ++k) { L->spans[k] = NULL; L->K[k] = 1; L->p[k] = 0; L->n[k] = 1; L->q[k] = 1; }
+  if (!pt || (pt->dim != 2 && pt->dim != 3)) return -1;
+  L->d = pt->dim;
   L->N = 1; L->Q = 1;
-  for (int k = 0; k < 3; ++k) { L->spans[k] = NULL; L->K[k] = 1; }
   for (int k = 0; k < L->d; ++k) {
-    if (!pt->t[k] || pt->m[k] < 2 * pt->p + 2) return -1;
+    const int p = pt->pd[k] ? pt->pd[k] : pt->p;
+    const int q = pt->qd[k] ? pt->qd[k] : pt->q;
+    if (p < 1 || p > 16 || q < 1 || q > 64) return -1;
+    L->p[k] = p; L->n[k] = p + 1; L->q[k] = q;
+    if (!pt->t[k] || pt->m[k] < 2 * p + 2) return -1;
     L->spans[k] = (int*)malloc(sizeof(int) * (size_t)pt->m[k]);
-    L->K[k] = ora_spans(pt->t[k], pt->m[k], pt->p, L->spans[k]);
-    L->N *= L->n; L->Q *= L->q;
+    L->K[k] = ora_spans(pt->t[k], pt->m[k], p, L->spans[k]);
+    L->N *= L->n[k]; L->Q *= L->q[k];
   }
   return 0;
+}
+
+/* 1 if every direction of the patch has the same degree. */
+static int same_degree(const layout* L) {
+  for (int k = 1; k < L->d; ++k)
+    if (L->p[k] != L->p[0]) return 0;
+  return 1;
 }
 
 static void free_layout(layout* L) {
@@ -215,23 +228,28 @@ typedef struct {
 
 static void element_1d(const ora_patch* pt, const layout* L, const int* ek, elem1d* B) {
   for (int k = 0; k < L->d; ++k)
-    ora_basis_1d(pt->t[k], L->p, L->spans[k][ek[k]], L->q, B->xi[k], B->w[k],
+    ora_basis_1d(pt->t[k], L->p[k], L->spans[k][ek[k]], L->q[k], B->xi[k], B->w[k],
                  B->val[k], B->der[k]);
 }
 
-/* Quadrature point k -> per-direction indices. */
+/* Quadrature point k -> per-direction indices (k = k1 + q_1 (k2 + q_2 k3)). */
 static void split_qp(const layout* L, int k, int* kk) {
-  kk[0] = k % L->q;
-  kk[1] = (k / L->q) % L->q;
-  kk[2] = (L->d == 3) ? k / (L->q * L->q) : 0;
+  kk[0] = k % L->q[0];
+  kk[1] = (k / L->q[0]) % L->q[1];
+  kk[2] = (L->d == 3) ? k / (L->q[0] * L->q[1]) : 0;
 }
 
-/* Local function a -> per-direction indices. */
+/* Local function a -> per-direction indices (a = a1 + n_1 (a2 + n_2 a3)). */
 static void split_local(const layout* L, int a, int* aa) {
-  aa[0] = a % L->n;
-  aa[1] = (a / L->n) % L->n;
-  aa[2] = (L->d == 3) ? a / (L->n * L->n) : 0;
+  aa[0] = a % L->n[0];
+  aa[1] = (a / L->n[0]) % L->n[1];
+  aa[2] = (L->d == 3) ? a / (L->n[0] * L->n[1]) : 0;
 }
+
+/* Value (s = 0) or derivative (s = 1) of local function r of direction j at
+ * its Gauss point k. */
+#define B1D(B, L, j, s, r, k) \
+  ((s) ? (B)->der[j][(k) * (L)->n[j] + (r)] : (B)->val[j][(k) * (L)->n[j] + (r)])
 
 /* Weights, |det G| and G^{-T}-mapped reference gradients at every quadrature
  * point of one element: the J(x^n) of eq. 10 is |det G| with G the derivative
@@ -264,7 +282,8 @@ int ora_classical(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
   layout L;
   if (make_layout(pt, &L)) { free_layout(&L); return -1; }
   if (K && !kappa) { free_layout(&L); return -1; }
-  int d = L.d, n = L.n, N = L.N, Q = L.Q;
+  int d = L.d, N = L.N, Q = L.Q;
+  const int n1 = L.n[0], n2 = L.n[1], n3 = L.n[2];
   int64_t E = n_elements(&L);
   elem1d* B = (elem1d*)malloc(sizeof(elem1d));
   double* W = (double*)malloc(sizeof(double) * Q);
@@ -287,11 +306,10 @@ int ora_classical(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
         int kk[3];
         split_qp(&L, k, kk);
         double v = 1.0, gr[3];
-        for (int j = 0; j < d; ++j) v *= B->val[j][kk[j] * n + aa[j]];
+        for (int j = 0; j < d; ++j) v *= B1D(B, &L, j, 0, aa[j], kk[j]);
         for (int i = 0; i < d; ++i) {
           double g = 1.0;
-          for (int j = 0; j < d; ++j)
-            g *= (i == j) ? B->der[j][kk[j] * n + aa[j]] : B->val[j][kk[j] * n + aa[j]];
+          for (int j = 0; j < d; ++j) g *= B1D(B, &L, j, i == j, aa[j], kk[j]);
           gr[i] = g;
         }
         phi[(size_t)a * Q + k] = v;
@@ -305,16 +323,16 @@ int ora_classical(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
     }
     double* Ke = K ? K + (size_t)s * N * N : NULL;
     double* Me = M ? M + (size_t)s * N * N : NULL;
-    /* the six nested test/trial loops of Algorithm 1, then the quadrature loop */
-    int n2 = (d == 3) ? n : 1;
-    for (int i1 = 0; i1 < n; ++i1)
-      for (int j1 = 0; j1 < n; ++j1)
-        for (int i2 = 0; i2 < n; ++i2)
-          for (int j2 = 0; j2 < n; ++j2)
-            for (int i3 = 0; i3 < n2; ++i3)
-              for (int j3 = 0; j3 < n2; ++j3) {
-                int a = i1 + n * (i2 + n * i3);
-                int b = j1 + n * (j2 + n * j3);
+    /* the six nested test/trial loops of Algorithm 1, then the quadrature
+     * loop (n3 = 1 in 2D) */
+    for (int i1 = 0; i1 < n1; ++i1)
+      for (int j1 = 0; j1 < n1; ++j1)
+        for (int i2 = 0; i2 < n2; ++i2)
+          for (int j2 = 0; j2 < n2; ++j2)
+            for (int i3 = 0; i3 < n3; ++i3)
+              for (int j3 = 0; j3 < n3; ++j3) {
+                int a = i1 + n1 * (i2 + n2 * i3);
+                int b = j1 + n1 * (j2 + n2 * j3);
                 double mab = 0.0, kab = 0.0;
                 for (int k = 0; k < Q; ++k) {
                   if (Me) {
@@ -350,69 +368,70 @@ int ora_classical(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
 /* ------------------------------------------------------------------------ */
 static void sf_term(const layout* L, const elem1d* B, const double* coef,
                     int sa[3], int sb[3], double* Dbuf, double* Cbuf, double* A) {
-  int n = L->n, q = L->q, N = L->N;
-  /* factor table of direction j for test (s=sa) or trial (s=sb) */
-#define FAC(j, s, r, k) ((s) ? B->der[j][(k) * n + (r)] : B->val[j][(k) * n + (r)])
+  const int n1 = L->n[0], n2 = L->n[1], n3 = L->n[2];
+  const int q1 = L->q[0], q2 = L->q[1], q3 = L->q[2], N = L->N;
+  /* factor of direction j for the test (s = sa[j]) or trial (s = sb[j]) function */
+#define FAC(j, s, r, k) B1D(B, L, j, s, r, k)
   if (L->d == 3) {
     /* D(i3,j3,k1,k2) = sum_k3 Bz_i3 Bz_j3 w_z J */
-    for (int i3 = 0; i3 < n; ++i3)
-      for (int j3 = 0; j3 < n; ++j3)
-        for (int k1 = 0; k1 < q; ++k1)
-          for (int k2 = 0; k2 < q; ++k2) {
+    for (int i3 = 0; i3 < n3; ++i3)
+      for (int j3 = 0; j3 < n3; ++j3)
+        for (int k1 = 0; k1 < q1; ++k1)
+          for (int k2 = 0; k2 < q2; ++k2) {
             double acc = 0.0;
-            for (int k3 = 0; k3 < q; ++k3)
+            for (int k3 = 0; k3 < q3; ++k3)
               acc += FAC(2, sa[2], i3, k3) * FAC(2, sb[2], j3, k3) * B->w[2][k3] *
-                     coef[k1 + q * (k2 + q * k3)];
-            Dbuf[((i3 * n + j3) * q + k1) * q + k2] = acc;
+                     coef[k1 + q1 * (k2 + q2 * k3)];
+            Dbuf[((i3 * n3 + j3) * q1 + k1) * q2 + k2] = acc;
           }
     /* C(i2,i3,j2,j3,k1) = sum_k2 By_i2 By_j2 D(i3,j3,k1,k2) w_y */
-    for (int i2 = 0; i2 < n; ++i2)
-      for (int j2 = 0; j2 < n; ++j2)
-        for (int i3 = 0; i3 < n; ++i3)
-          for (int j3 = 0; j3 < n; ++j3)
-            for (int k1 = 0; k1 < q; ++k1) {
+    for (int i2 = 0; i2 < n2; ++i2)
+      for (int j2 = 0; j2 < n2; ++j2)
+        for (int i3 = 0; i3 < n3; ++i3)
+          for (int j3 = 0; j3 < n3; ++j3)
+            for (int k1 = 0; k1 < q1; ++k1) {
               double acc = 0.0;
-              for (int k2 = 0; k2 < q; ++k2)
+              for (int k2 = 0; k2 < q2; ++k2)
                 acc += FAC(1, sa[1], i2, k2) * FAC(1, sb[1], j2, k2) *
-                       Dbuf[((i3 * n + j3) * q + k1) * q + k2] * B->w[1][k2];
-              Cbuf[(((i2 * n + i3) * n + j2) * n + j3) * q + k1] = acc;
+                       Dbuf[((i3 * n3 + j3) * q1 + k1) * q2 + k2] * B->w[1][k2];
+              Cbuf[(((i2 * n3 + i3) * n2 + j2) * n3 + j3) * q1 + k1] = acc;
             }
     /* A((i1,i2,i3),(j1,j2,j3)) += sum_k1 Bx_i1 Bx_j1 C(i2,i3,j2,j3,k1) w_x */
-    for (int i1 = 0; i1 < n; ++i1)
-      for (int j1 = 0; j1 < n; ++j1)
-        for (int i2 = 0; i2 < n; ++i2)
-          for (int j2 = 0; j2 < n; ++j2)
-            for (int i3 = 0; i3 < n; ++i3)
-              for (int j3 = 0; j3 < n; ++j3) {
+    for (int i1 = 0; i1 < n1; ++i1)
+      for (int j1 = 0; j1 < n1; ++j1)
+        for (int i2 = 0; i2 < n2; ++i2)
+          for (int j2 = 0; j2 < n2; ++j2)
+            for (int i3 = 0; i3 < n3; ++i3)
+              for (int j3 = 0; j3 < n3; ++j3) {
                 double acc = 0.0;
-                for (int k1 = 0; k1 < q; ++k1)
+                for (int k1 = 0; k1 < q1; ++k1)
                   acc += FAC(0, sa[0], i1, k1) * FAC(0, sb[0], j1, k1) *
-                         Cbuf[(((i2 * n + i3) * n + j2) * n + j3) * q + k1] * B->w[0][k1];
-                int a = i1 + n * (i2 + n * i3);
-                int b = j1 + n * (j2 + n * j3);
+                         Cbuf[(((i2 * n3 + i3) * n2 + j2) * n3 + j3) * q1 + k1] * B->w[0][k1];
+                int a = i1 + n1 * (i2 + n2 * i3);
+                int b = j1 + n1 * (j2 + n2 * j3);
                 A[(size_t)a * N + b] += acc;
               }
   } else {
     /* D(i2,j2,k1) = sum_k2 By_i2 By_j2 w_y J */
-    for (int i2 = 0; i2 < n; ++i2)
-      for (int j2 = 0; j2 < n; ++j2)
-        for (int k1 = 0; k1 < q; ++k1) {
+    for (int i2 = 0; i2 < n2; ++i2)
+      for (int j2 = 0; j2 < n2; ++j2)
+        for (int k1 = 0; k1 < q1; ++k1) {
           double acc = 0.0;
-          for (int k2 = 0; k2 < q; ++k2)
+          for (int k2 = 0; k2 < q2; ++k2)
             acc += FAC(1, sa[1], i2, k2) * FAC(1, sb[1], j2, k2) * B->w[1][k2] *
-                   coef[k1 + q * k2];
-          Dbuf[(i2 * n + j2) * q + k1] = acc;
+                   coef[k1 + q1 * k2];
+          Dbuf[(i2 * n2 + j2) * q1 + k1] = acc;
         }
     /* A((i1,i2),(j1,j2)) += sum_k1 Bx_i1 Bx_j1 D(i2,j2,k1) w_x */
-    for (int i1 = 0; i1 < n; ++i1)
-      for (int j1 = 0; j1 < n; ++j1)
-        for (int i2 = 0; i2 < n; ++i2)
-          for (int j2 = 0; j2 < n; ++j2) {
+    for (int i1 = 0; i1 < n1; ++i1)
+      for (int j1 = 0; j1 < n1; ++j1)
+        for (int i2 = 0; i2 < n2; ++i2)
+          for (int j2 = 0; j2 < n2; ++j2) {
             double acc = 0.0;
-            for (int k1 = 0; k1 < q; ++k1)
+            for (int k1 = 0; k1 < q1; ++k1)
               acc += FAC(0, sa[0], i1, k1) * FAC(0, sb[0], j1, k1) *
-                     Dbuf[(i2 * n + j2) * q + k1] * B->w[0][k1];
-            A[(size_t)(i1 + n * i2) * N + (j1 + n * j2)] += acc;
+                     Dbuf[(i2 * n2 + j2) * q1 + k1] * B->w[0][k1];
+            A[(size_t)(i1 + n1 * i2) * N + (j1 + n1 * j2)] += acc;
           }
   }
 #undef FAC
@@ -424,12 +443,15 @@ int ora_sumfact(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
   layout L;
   if (make_layout(pt, &L)) { free_layout(&L); return -1; }
   if (K && !kappa) { free_layout(&L); return -1; }
-  int d = L.d, n = L.n, q = L.q, N = L.N, Q = L.Q;
+  int d = L.d, N = L.N, Q = L.Q;
   int64_t E = n_elements(&L);
   elem1d* B = (elem1d*)malloc(sizeof(elem1d));
   double* coef = (double*)malloc(sizeof(double) * Q);
-  double* Dbuf = (double*)malloc(sizeof(double) * (size_t)n * n * q * q);
-  double* Cbuf = (double*)malloc(sizeof(double) * (size_t)n * n * n * n * q);
+  /* stage buffers: D [n_last^2][q1][q2], C [n2^2 n3^2][q1] (sizes of the 3D
+   * case, which cover the 2D one) */
+  const size_t nl = (size_t)L.n[d - 1];
+  double* Dbuf = (double*)malloc(sizeof(double) * nl * nl * L.q[0] * L.q[1]);
+  double* Cbuf = (double*)malloc(sizeof(double) * (size_t)L.n[1] * L.n[1] * L.n[2] * L.n[2] * L.q[0]);
   for (int64_t s = 0; s < n_sel; ++s) {
     int64_t e = elems[s];
     if (e < 0 || e >= E) { free(B); free(coef); free(Dbuf); free(Cbuf); free_layout(&L); return -1; }
@@ -482,7 +504,7 @@ int ora_dofmap(const ora_patch* pt, const int64_t* elems, int64_t n_sel, int32_t
   if (make_layout(pt, &L)) { free_layout(&L); return -1; }
   int64_t E = n_elements(&L);
   int64_t nf[3] = {1, 1, 1};
-  for (int k = 0; k < L.d; ++k) nf[k] = pt->m[k] - pt->p - 1;
+  for (int k = 0; k < L.d; ++k) nf[k] = pt->m[k] - L.p[k] - 1;
   for (int64_t s = 0; s < n_sel; ++s) {
     int64_t e = elems[s];
     if (e < 0 || e >= E) { free_layout(&L); return -1; }
@@ -493,7 +515,7 @@ int ora_dofmap(const ora_patch* pt, const int64_t* elems, int64_t n_sel, int32_t
       split_local(&L, a, aa);
       int64_t g = 0, stride = 1;
       for (int k = 0; k < L.d; ++k) {
-        g += (int64_t)(L.spans[k][ek[k]] - L.p + aa[k]) * stride;
+        g += (int64_t)(L.spans[k][ek[k]] - L.p[k] + aa[k]) * stride;
         stride *= nf[k];
       }
       dof[(size_t)s * L.N + a] = (int32_t)g;
@@ -512,7 +534,7 @@ int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
                 const double* v, double* g, double* J) {
   layout L;
   if (make_layout(pt, &L)) { free_layout(&L); return -1; }
-  int d = L.d, n = L.n, N = L.N, Q = L.Q;
+  int d = L.d, N = L.N, Q = L.Q;
   int64_t E = n_elements(&L);
   elem1d* B = (elem1d*)malloc(sizeof(elem1d));
   double* W = (double*)malloc(sizeof(double) * Q);
@@ -536,8 +558,7 @@ int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
         split_local(&L, a, aa);
         for (int i = 0; i < d; ++i) {
           double f = 1.0;
-          for (int j = 0; j < d; ++j)
-            f *= (i == j) ? B->der[j][kk[j] * n + aa[j]] : B->val[j][kk[j] * n + aa[j]];
+          for (int j = 0; j < d; ++j) f *= B1D(B, &L, j, i == j, aa[j], kk[j]);
           gu[i] += u[dof[a]] * f;
           gv[i] += v[dof[a]] * f;
         }
@@ -567,7 +588,7 @@ int ora_adjoint(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
 /* ------------------------------------------------------------------------ */
 static int64_t n_global_dofs(const ora_patch* pt, const layout* L) {
   int64_t nd = 1;
-  for (int k = 0; k < L->d; ++k) nd *= pt->m[k] - pt->p - 1;
+  for (int k = 0; k < L->d; ++k) nd *= pt->m[k] - L->p[k] - 1;
   return nd;
 }
 
@@ -849,8 +870,11 @@ int ora_wq_weights_deriv(const double* t, int m, int p, const double* x, int np,
 int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
                 const int32_t* col_idx, double* values) {
   layout L;
-  if (!row_ptr || !col_idx || !values || make_layout(pt, &L)) { free_layout(&L); return -1; }
-  const int d = L.d, p = L.p;
+  if (!row_ptr || !col_idx || !values || make_layout(pt, &L) || !same_degree(&L)) {
+    free_layout(&L);
+    return -1;
+  }
+  const int d = L.d, p = L.p[0];
   double* x[3] = {NULL, NULL, NULL};
   double* W[3] = {NULL, NULL, NULL};
   double* Bv[3] = {NULL, NULL, NULL};
@@ -903,8 +927,11 @@ int ora_wq_mass(const ora_patch* pt, const double* c, const int64_t* row_ptr,
 int ora_wq_stiffness(const ora_patch* pt, const double* c, const int64_t* row_ptr,
                      const int32_t* col_idx, double* values) {
   layout L;
-  if (!row_ptr || !col_idx || !values || make_layout(pt, &L)) { free_layout(&L); return -1; }
-  const int d = L.d, p = L.p;
+  if (!row_ptr || !col_idx || !values || make_layout(pt, &L) || !same_degree(&L)) {
+    free_layout(&L);
+    return -1;
+  }
+  const int d = L.d, p = L.p[0];
   /* per direction: R[0] mass rule, R[1] derivative rule; B[0] values, B[1] derivatives */
   double* x[3] = {NULL, NULL, NULL};
   double* R[3][2] = {{NULL, NULL}, {NULL, NULL}, {NULL, NULL}};
@@ -975,7 +1002,7 @@ int ora_integrate_grad(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
                        const double* GK, const double* GM, double* gk, double* gr) {
   layout L;
   if ((!GK && !GM) || (GK && !gk) || (GM && !gr) || make_layout(pt, &L)) { free_layout(&L); return -1; }
-  const int d = L.d, n = L.n, N = L.N, Q = L.Q;
+  const int d = L.d, N = L.N, Q = L.Q;
   const int64_t E = n_elements(&L);
   elem1d* B = (elem1d*)malloc(sizeof(elem1d));
   double* W = (double*)malloc(sizeof(double) * Q);
@@ -998,11 +1025,10 @@ int ora_integrate_grad(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
         int aa[3];
         split_local(&L, a, aa);
         double v = 1.0, gref[3];
-        for (int j = 0; j < d; ++j) v *= B->val[j][kk[j] * n + aa[j]];
+        for (int j = 0; j < d; ++j) v *= B1D(B, &L, j, 0, aa[j], kk[j]);
         for (int i = 0; i < d; ++i) {
           double g = 1.0;
-          for (int j = 0; j < d; ++j)
-            g *= (i == j) ? B->der[j][kk[j] * n + aa[j]] : B->val[j][kk[j] * n + aa[j]];
+          for (int j = 0; j < d; ++j) g *= B1D(B, &L, j, i == j, aa[j], kk[j]);
           gref[i] = g;
         }
         phi[a] = v;

@@ -8,13 +8,18 @@
  * fallback for it.
  *
  * Conventions (0-based everywhere, x fastest in every multi-index):
- *   knots t[0..m-1] per direction, degree p, number of functions m-p-1;
+ *   knots t[0..m-1] per direction, degree p_k, number of functions m-p_k-1;
  *   elements per direction = non-empty knot spans [t_s, t_{s+1});
  *   element e = e1 + K1*(e2 + K2*e3);
- *   local function a = a1 + n*(a2 + n*a3), n = p+1, global 1D index s-p+a_k;
- *   quadrature point k = k1 + q*(k2 + q*k3);
+ *   local function a = a1 + n_1*(a2 + n_2*a3), n_k = p_k+1, global 1D index
+ *   s_k-p_k+a_k;
+ *   quadrature point k = k1 + q_1*(k2 + q_2*k3);
  *   kappa[E][Q], rho[E][Q], G[E][Q][d][d] with G[i][j] = dx_i/dxi_j (row-major);
- *   element matrices [n_sel][N][N] row-major, N = n^d.
+ *   element matrices [n_sel][N][N] row-major, N = n_1 n_2 (n_3), Q = q_1 q_2 (q_3).
+ * The paper takes one degree for every direction and notes that the method
+ * extends to bases of different degrees (Sec. 2.3); its element sum (eq. 10)
+ * already has P_1, P_2, P_3 quadrature points per direction.  Each patch
+ * therefore has a degree and a number of Gauss points per direction.
  *
  * Every function cites the passage of the paper it follows.  Items with no
  * counterpart in the paper (derivatives, stiffness, the adjoint) are written
@@ -54,10 +59,12 @@ void ora_basis_1d(const double* t, int p, int s, int q, double* xi, double* w,
 /* Description of one patch for the element-matrix routines. */
 typedef struct {
   int dim;                 /* 2 or 3 */
-  int p;                   /* degree, all directions */
-  int q;                   /* Gauss points per direction */
+  int p;                   /* degree of every direction whose pd[k] is 0 */
+  int q;                   /* Gauss points of every direction whose qd[k] is 0 */
   int m[3];                /* knots per direction */
   const double* t[3];      /* knot vectors */
+  int pd[3];               /* degree of direction k, or 0 (= p) */
+  int qd[3];               /* Gauss points of direction k, or 0 (= q) */
 } ora_patch;
 
 /* Classical integration (Sec. 3.2, Algorithm 1; element integral eq. 10),
@@ -80,8 +87,8 @@ int ora_sumfact(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
                 double* K, double* M);
 
 /* Global dof of each local function of each selected element (Remark on the
- * support set K^Delta_alpha, Sec. 3.1): dof = sum_k (s_k - p + a_k) * stride_k,
- * stride = 1, n_1, n_1 n_2 with n_k = m_k - p - 1. */
+ * support set K^Delta_alpha, Sec. 3.1): dof = sum_k (s_k - p_k + a_k) * stride_k,
+ * stride = 1, f_1, f_1 f_2 with f_k = m_k - p_k - 1 functions in direction k. */
 int ora_dofmap(const ora_patch* pt, const int64_t* elems, int64_t n_sel,
                int32_t* dof);
 

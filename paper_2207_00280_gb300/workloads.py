@@ -41,36 +41,40 @@ def element_breaks(t: np.ndarray) -> np.ndarray:
     return np.unique(np.asarray(t, dtype=np.float64))
 
 
-def qp_coordinates(knots, q: int):
+def qp_coordinates(knots, q):
     """Parametric coordinates of every quadrature point: array [E][Q][d].
 
-    Elements are the spans between distinct knots, x fastest; points inside an
-    element are ordered x fastest as well.  Gauss--Legendre positions come from
-    numpy (see module docstring)."""
-    xr, _ = np.polynomial.legendre.leggauss(q)
+    q is the number of Gauss points of every direction, or one number per
+    direction.  Elements are the spans between distinct knots, x fastest;
+    points inside an element are ordered x fastest as well.  Gauss--Legendre
+    positions come from numpy (see module docstring)."""
+    d = len(knots)
+    qs = [int(q)] * d if np.ndim(q) == 0 else [int(v) for v in q]
     per_dir = []
-    for t in knots:
+    for t, qk in zip(knots, qs):
+        xr, _ = np.polynomial.legendre.leggauss(qk)
         b = element_breaks(t)
         lo, hi = b[:-1], b[1:]
         per_dir.append(0.5 * (lo + hi)[:, None] + 0.5 * (hi - lo)[:, None] * xr[None, :])
-    d = len(knots)
     if d == 2:
+        q1, q2 = qs
         X = per_dir[0][None, :, None, :]          # [e2][e1][k2][k1]
         Y = per_dir[1][:, None, :, None]
-        shape = (per_dir[1].shape[0], per_dir[0].shape[0], q, q)
+        shape = (per_dir[1].shape[0], per_dir[0].shape[0], q2, q1)
         X = np.broadcast_to(X, shape); Y = np.broadcast_to(Y, shape)
         E = shape[0] * shape[1]
-        return np.stack([X.reshape(E, q * q), Y.reshape(E, q * q)], axis=-1)
+        return np.stack([X.reshape(E, q1 * q2), Y.reshape(E, q1 * q2)], axis=-1)
+    q1, q2, q3 = qs
     K1, K2, K3 = (a.shape[0] for a in per_dir)
-    shape = (K3, K2, K1, q, q, q)                  # [e3][e2][e1][k3][k2][k1]
+    shape = (K3, K2, K1, q3, q2, q1)               # [e3][e2][e1][k3][k2][k1]
     X = np.broadcast_to(per_dir[0][None, None, :, None, None, :], shape)
     Y = np.broadcast_to(per_dir[1][None, :, None, None, :, None], shape)
     Z = np.broadcast_to(per_dir[2][:, None, None, :, None, None], shape)
-    E, Q = K1 * K2 * K3, q ** 3
+    E, Q = K1 * K2 * K3, q1 * q2 * q3
     return np.stack([X.reshape(E, Q), Y.reshape(E, Q), Z.reshape(E, Q)], axis=-1)
 
 
-def curved_map_jacobian(knots, q: int, amp: float = 0.05) -> np.ndarray:
+def curved_map_jacobian(knots, q, amp: float = 0.05) -> np.ndarray:
     """G[E][Q][3][3] = d x / d xi of the cyclic sine map
 
         x = xi  + amp sin(2 pi eta ) sin(2 pi zeta)

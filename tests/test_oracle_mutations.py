@@ -31,8 +31,8 @@ MUTANTS = {
     # adjoint product of u with itself
     "adjoint_product": ("dot += pu * pv;", "dot += pu * pu;"),
     # y-direction weight dropped in stage 2 of Algorithm 2
-    "sf_stage2_weight": ("Dbuf[((i3 * n + j3) * q + k1) * q + k2] * B->w[1][k2];",
-                         "Dbuf[((i3 * n + j3) * q + k1) * q + k2];"),
+    "sf_stage2_weight": ("Dbuf[((i3 * n3 + j3) * q1 + k1) * q2 + k2] * B->w[1][k2];",
+                         "Dbuf[((i3 * n3 + j3) * q1 + k1) * q2 + k2];"),
     # global assembly: element matrix inserted transposed
     "assemble_transposed": ("values[l] += Ae[((size_t)e * N + a) * N + b];",
                             "values[l] += Ae[((size_t)e * N + b) * N + a];", "test_oracle_assembly.py"),
@@ -65,7 +65,18 @@ MUTANTS = {
                           "if (GM) sm += GM[((size_t)s * N + a) * N + b] * phi[a] * phi[a];",
                           "test_oracle_assembly.py"),
     # Algorithm 1: the trial function's y index taken from the test function
-    "classical_trial_index": ("int b = j1 + n * (j2 + n * j3);", "int b = j1 + n * (i2 + n * j3);"),
+    "classical_trial_index": ("int b = j1 + n1 * (j2 + n2 * j3);", "int b = j1 + n1 * (i2 + n2 * j3);"),
+    # quadrature-point index: the y stride taken from the wrong direction
+    "qp_stride_direction": ("kk[1] = (k / L->q[0]) % L->q[1];", "kk[1] = (k / L->q[1]) % L->q[1];",
+                            "test_oracle_aniso.py"),
+    # local-function index: the z stride built from n_1 twice
+    "local_stride_direction": ("aa[2] = (L->d == 3) ? a / (L->n[0] * L->n[1]) : 0;",
+                               "aa[2] = (L->d == 3) ? a / (L->n[0] * L->n[0]) : 0;",
+                               "test_oracle_aniso.py"),
+    # Algorithm 2 stage 1: the z contraction weighted with the y direction's Gauss weights
+    "sf_stage1_weight_direction": ("acc += FAC(2, sa[2], i3, k3) * FAC(2, sb[2], j3, k3) * B->w[2][k3] *",
+                                   "acc += FAC(2, sa[2], i3, k3) * FAC(2, sb[2], j3, k3) * B->w[1][k3] *",
+                                   "test_oracle_aniso.py"),
     # element-matrix backward: every component of the trial gradient replaced by its x component
     "grad_stiff_component": ("for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + i];",
                              "for (int i = 0; i < d; ++i) dot += grad[(size_t)a * 3 + i] * grad[(size_t)b * 3 + 0];",
