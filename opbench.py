@@ -29,7 +29,7 @@ L2_FLUSH_BYTES = 2 * 129 * 1024 * 1024
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="integrate", choices=["integrate", "assemble", "apply", "adjoint", "grad", "wq_mass",
-                                                 "wq_stiffness"])
+                                                 "wq_stiffness", "probe"])
     ap.add_argument("--workload", default="3d_p3_16")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_df", "fp32", "bf16"])
     ap.add_argument("--method", default="sumfact", choices=["sumfact", "classical"])
@@ -39,6 +39,8 @@ def main(argv=None):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.op == "probe":
+        return probe(dev)
     W = wl.WORKLOADS[args.workload]
     sp = W.spec
     G = W.jacobian()
@@ -115,6 +117,28 @@ def main(argv=None):
                       "ms_median": round(statistics.median(ts), 4),
                       "ms_min": round(min(ts), 4)}), flush=True)
     plan.close()
+
+
+def probe(dev):
+    """Arithmetic rates of this GPU (include/iga_probe.h): DFMA, DMMA (mma.sync
+    m8n8k4 f64) and FFMA throughput for 1, 2, 4 and 8 CTAs of 256 threads per
+    SM, best of three CUDA-event timings each, in TFLOP/s."""
+    import ctypes
+    from paper_2207_00280_gb300 import capi
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    out = {}
+    for name, kind, iters in (("dfma", capi.IGA_PROBE_DFMA, 1 << 16),
+                              ("dmma", capi.IGA_PROBE_DMMA, 1 << 14),
+                              ("ffma", capi.IGA_PROBE_FFMA, 1 << 20)):
+        capi.iga_probe_rate(kind, 1024, 1, st)   # warm-up
+        for ctas in (1, 2, 4, 8):
+            best, ms_b = 0.0, 0.0
+            for _ in range(3):
+                ms, fl = capi.iga_probe_rate(kind, iters, ctas, st)
+                if fl / (ms * 1e-3) / 1e12 > best:
+                    best, ms_b = fl / (ms * 1e-3) / 1e12, ms
+            out[f"{name}_ctas{ctas}"] = {"tflops": round(best, 4), "ms": round(ms_b, 3)}
+    print(json.dumps({"op": "probe", "rates": out}), flush=True)
 
 
 if __name__ == "__main__":
