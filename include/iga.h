@@ -4,7 +4,7 @@
  * (arxiv 2207.00280, "A study of efficient concurrent integration methods of
  * B-Spline basis functions in IGA-FEM").
  *
- * What is computed (per element E of a patch, N = (p+1)^d local functions):
+ * What is computed (per element E of a patch, N local functions):
  *   mass       M_ab = sum_q w_q |det G_q| rho_q   phi_a(x_q) phi_b(x_q)
  *   stiffness  K_ab = sum_q w_q |det G_q| kappa_q (G_q^{-T} grad phi_a).(G_q^{-T} grad phi_b)
  * The mass is the element Gram matrix of Sec. 3.1 (eqs. 88 and 10); the
@@ -17,15 +17,21 @@
  * the classical loop (Sec. 3.2, Algorithm 1) and sum factorization
  * (Sec. 3.2, Algorithm 2, eqs. finalsum and bufferC).
  *
+ * Each direction k of a patch has its own degree p_k and number of Gauss
+ * points q_k: the paper uses one degree for every direction and notes that the
+ * method extends to bases of different degrees (Sec. 2.3), and its element sum
+ * (eq. 10) has P_1 P_2 P_3 points.  N = n_1 n_2 (n_3) with n_k = p_k + 1 and
+ * Q = q_1 q_2 (q_3).
+ *
  * Conventions (all indices 0-based, x fastest in every multi-index):
  *   element   e = e1 + K1*(e2 + K2*e3), elements = non-empty knot spans;
- *   local fn  a = a1 + n*(a2 + n*a3), n = p+1 (the support set of the Remark
- *             in Sec. 3.1, global 1D index s_k - p + a_k for span s_k);
- *   global dof = i1 + n1*(i2 + n2*i3), n_k = functions in direction k,
+ *   local fn  a = a1 + n_1*(a2 + n_2*a3) (the support set of the Remark in
+ *             Sec. 3.1, global 1D index s_k - p_k + a_k for span s_k);
+ *   global dof = i1 + f1*(i2 + f2*i3), f_k = functions in direction k,
  *             patches concatenated in batch order;
- *   quad pt   k = k1 + q*(k2 + q*k3);
+ *   quad pt   k = k1 + q_1*(k2 + q_2*k3);
  *   kappa, rho: [n_qp] doubles, element-major: index = qp_offset(patch) +
- *             e*Q + k, Q = q^d;
+ *             e*Q + k;
  *   jac:      [n_qp][d][d] doubles, jac[..][i][j] = d x_i / d xi_j with xi
  *             the knot (parametric) coordinate; |det| is the J(x^n) of eq. 10;
  *   K_out, M_out: per patch [E][N][N] row-major, patches concatenated
@@ -94,13 +100,26 @@ enum { IGA_SCHED_AUTO = 0, IGA_SCHED_PER_PATCH = 1, IGA_SCHED_PERSISTENT = 2,
        IGA_SCHED_PERSISTENT_GRAPH = 3 };
 
 /* One tensor-product patch.  Knot vectors are host arrays, copied by
- * iga_plan.  Each must be non-decreasing and open (first and last p+1 knots
- * equal) with interior multiplicity <= p (Sec. 2.3, eq. knot_vector).
- * 1 <= degree <= 5 in 3D and <= 8 in 2D; n_gauss in {degree+1, degree+2}. */
+ * iga_plan.  Knot vector k must be non-decreasing and open (first and last
+ * p_k+1 knots equal) with interior multiplicity <= p_k (Sec. 2.3,
+ * eq. knot_vector).  1 <= degree[k] <= 8 and 1 <= n_gauss[k] <= 16 for each of
+ * the dim directions (IGA_ERR_ARG otherwise); entries beyond dim are ignored.
+ *
+ * Which forms take which patches:
+ *   IGA_FP64 (classical and sum factorization), iga_integrate_backward on
+ *     IGA_FP64 plans, iga_basis_tables, iga_csr_pattern: every patch.  Patches
+ *     with one degree p <= 5 and one Gauss order q in {p+1, p+2} (2D: p <= 8)
+ *     run on kernels specialised for that (p, q); the others on runtime-sized
+ *     FP64 kernels.
+ *   IGA_FP32, IGA_BF16, IGA_FP64_DF (sum factorization only), and the other
+ *     entry points (iga_apply, iga_assemble, iga_integrate_grad, the weighted
+ *     quadrature): patches with one degree and one Gauss order in every
+ *     direction, within the limits each entry states; otherwise
+ *     IGA_ERR_UNSUPPORTED. */
 typedef struct {
   int dim;                  /* 2 or 3 */
-  int degree;               /* p, the same in every direction */
-  int n_gauss;              /* q, Gauss points per direction */
+  int degree[3];            /* p_k per direction */
+  int n_gauss[3];           /* q_k, Gauss points per direction */
   int n_knots[3];           /* knots per direction (dim entries used) */
   const double* knots[3];   /* host pointers */
 } iga_patch_desc;
@@ -173,9 +192,9 @@ int iga_integrate_backward(iga_plan_t plan, const double* kappa, const double* j
 /* Evaluate the 1D basis tables (Sec. 2.3, eqs. cox1/cox2; derivatives by the
  * de Boor identity) into `out` (device, n_table_entries doubles) on
  * `cuda_stream`.  Order: patches, then directions, then elements of that
- * direction; one record per element: val[q][p+1], der[q][p+1] of the p+1
- * functions non-zero on the element at its Gauss points, then w[q], the Gauss
- * weights times half the element length.  iga_integrate computes the same
+ * direction; one record per element of direction k: val[q_k][p_k+1],
+ * der[q_k][p_k+1] of the p_k+1 functions non-zero on the element at its Gauss
+ * points, then w[q_k], the Gauss weights times half the element length.  iga_integrate computes the same
  * tables internally; this entry exposes them for inspection. */
 int iga_basis_tables(iga_plan_t plan, double* out, void* cuda_stream);
 
@@ -295,17 +314,24 @@ int iga_profile_read(iga_plan_t plan, double* kernel_ms, int64_t* launches);
  * It computes dJ/dkappa and J = u^T K(kappa) v (FP64) for one 3D patch whose
  * knot vectors are host arrays, with kappa, jac, u, v, grad_kappa and J_out
  * in device memory as for a FP64 plan's iga_integrate_backward (jac may be
- * NULL; kappa may be NULL only if J_out is NULL).  Its working memory is one
- * file-scope device array of 3.7 MiB that every GPU which loads the library
- * holds until the process exits: at most 1024 knots per direction, 262144
- * elements and 196608 doubles of basis tables; larger patches return
- * IGA_ERR_TOO_LARGE before anything is launched.  The first call on a device
- * looks up the array's device address (with that device current), so make
- * that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU (different streams, or different host
- * threads on one device) race and must be serialized by the caller.  Nothing
- * in the array needs clearing: each call overwrites what it reads.  Launch
- * errors are returned; the call does not synchronize. */
+ * NULL; kappa may be NULL only if J_out is NULL).  The patch must have one
+ * degree (1..8) and one Gauss order (1..16) in all three directions
+ * (IGA_ERR_UNSUPPORTED otherwise).  Its working memory is one file-scope
+ * device array of 3.7 MiB that every GPU which loads the library holds until
+ * the process exits: at most 1024 knots per direction, 262144 elements and
+ * 196608 doubles of basis tables; larger patches return IGA_ERR_TOO_LARGE
+ * before anything is launched.  The first call in a CUDA context (the
+ * runtime's primary context of a device, or one the caller made current)
+ * looks up the array's device address in that context, so make that first
+ * call before any stream capture; the address is cached per context (by its
+ * unique id), so a context created later, e.g. after cudaDeviceReset, gets
+ * its own lookup.  All calls share the array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads on one device) race
+ * and must be serialized by the caller.  Nothing in the array needs clearing:
+ * each call overwrites what it reads.  The patch description (knots and the
+ * Gauss rule, about 25 KB) travels to the device as a kernel parameter, which
+ * needs the large kernel parameters of CUDA 12.1 or later.  Launch errors are
+ * returned; the call does not synchronize. */
 int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* kappa, const double* jac,
                         const double* u, const double* v, double* grad_kappa, double* J_out,
                         void* cuda_stream);

@@ -58,8 +58,18 @@ class IgaError(RuntimeError):
 
 
 class PatchDesc(ctypes.Structure):
-    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("n_gauss", ctypes.c_int),
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int * 3), ("n_gauss", ctypes.c_int * 3),
                 ("n_knots", ctypes.c_int * 3), ("knots", ctypes.c_void_p * 3)]
+
+    def set_order(self, degree, n_gauss):
+        """Degree and Gauss points of every direction: an int for all, or one per direction."""
+        ps = [int(degree)] * 3 if isinstance(degree, (int,)) or getattr(degree, "ndim", 1) == 0 \
+            else [int(v) for v in degree] + [0] * (3 - len(degree))
+        qs = [int(n_gauss)] * 3 if isinstance(n_gauss, (int,)) or getattr(n_gauss, "ndim", 1) == 0 \
+            else [int(v) for v in n_gauss] + [0] * (3 - len(n_gauss))
+        for k in range(3):
+            self.degree[k] = ps[k]
+            self.n_gauss[k] = qs[k]
 
 
 class PlanOpts(ctypes.Structure):

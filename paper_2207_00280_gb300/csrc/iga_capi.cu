@@ -365,15 +365,24 @@ int wq_build_direction(const double* t, int p, const std::vector<int>& spans,
   return IGA_OK;
 }
 
-bool method_supported(const iga_plan_opts& o, int dim, int p, int q) {
-  if (o.precision == IGA_FP64) {
-    if (o.method == IGA_SUMFACT) return sumfact_f64_supported(dim, p, q);
-    return classical_f64_supported(dim, p, q);
-  }
+// Whether the plan's method and precision can integrate patch pd: FP64 takes
+// every patch (specialised kernels where they exist, the runtime-sized ones
+// otherwise); the other precisions need a specialised kernel.
+bool method_supported(const iga_plan_opts& o, const PatchDev& pd) {
+  if (o.precision == IGA_FP64) return true;
+  if (!pd.iso) return false;
+  const int dim = pd.dim, p = pd.p, q = pd.q;
   if (o.precision == IGA_FP32 || o.precision == IGA_BF16)
     return o.method == IGA_SUMFACT && sumfact_f32_supported(dim, p, q);
   if (o.precision == IGA_FP64_DF) return o.method == IGA_SUMFACT && sumfact_df_supported(dim, p, q);
   return false;
+}
+
+// A specialised (compile-time sized) FP64 kernel exists for the patch.
+bool fp64_specialised(const iga_plan_opts& o, const PatchDev& pd) {
+  if (!pd.iso) return false;
+  if (o.method == IGA_SUMFACT) return sumfact_f64_supported(pd.dim, pd.p, pd.q);
+  return classical_f64_supported(pd.dim, pd.p, pd.q);
 }
 
 template <class T>
@@ -466,28 +475,32 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
   for (int ip = 0; ip < n_patches; ++ip) {
     const iga_patch_desc& d = patches[ip];
     if (d.dim != dim) { delete P; return IGA_ERR_UNSUPPORTED; }
-    const int p = d.degree, q = d.n_gauss;
-    if (p < 1 || q < 1 || q > kMaxGauss) { delete P; return IGA_ERR_ARG; }
-    if ((dim == 3 && p > kMaxDegree3D) || (dim == 2 && p > kMaxDegree2D)) {
-      delete P;
-      return IGA_ERR_UNSUPPORTED;
+    PatchDev pd{};
+    pd.dim = dim;
+    pd.iso = 1;
+    for (int k = 0; k < 3; ++k) {
+      if (k >= dim) { pd.pk[k] = 0; pd.qk[k] = 1; pd.nk[k] = 1; continue; }
+      const int p = d.degree[k], q = d.n_gauss[k];
+      if (p < 1 || p > kMaxDegree || q < 1 || q > kMaxGauss) { delete P; return IGA_ERR_ARG; }
+      pd.pk[k] = p; pd.qk[k] = q; pd.nk[k] = p + 1;
+      if (p != d.degree[0] || q != d.n_gauss[0]) pd.iso = 0;
     }
     for (int k = 0; k < dim; ++k) {
-      int rc = validate_knots(d.knots[k], d.n_knots[k], p);
+      int rc = validate_knots(d.knots[k], d.n_knots[k], pd.pk[k]);
       if (rc != IGA_OK) { delete P; return rc; }
     }
-    if (!method_supported(o, dim, p, q)) { delete P; return IGA_ERR_UNSUPPORTED; }
-    PatchDev pd{};
-    pd.dim = dim; pd.p = p; pd.q = q; pd.n = p + 1;
+    pd.p = pd.pk[0]; pd.q = pd.qk[0]; pd.n = pd.nk[0];
+    if (!method_supported(o, pd)) { delete P; return IGA_ERR_UNSUPPORTED; }
     pd.N = 1; pd.Q = 1;
     int64_t E = 1, nd = 1;
-    pd.gauss_offset = (int)gauss_all.size();
-    std::vector<double> xr(q), wr(q);
-    gauss_legendre_newton(q, xr.data(), wr.data());
-    gauss_all.insert(gauss_all.end(), xr.begin(), xr.end());
-    gauss_all.insert(gauss_all.end(), wr.begin(), wr.end());
     for (int k = 0; k < 3; ++k) {
       if (k >= dim) { pd.K[k] = 1; pd.nf[k] = 1; continue; }
+      const int p = pd.pk[k], q = pd.qk[k];
+      pd.gauss_offset[k] = (int)gauss_all.size();
+      std::vector<double> xr(q), wr(q);
+      gauss_legendre_newton(q, xr.data(), wr.data());
+      gauss_all.insert(gauss_all.end(), xr.begin(), xr.end());
+      gauss_all.insert(gauss_all.end(), wr.begin(), wr.end());
       const double* t = d.knots[k];
       const int m = d.n_knots[k];
       std::vector<int> s = knot_spans(t, m, p);
@@ -501,7 +514,7 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
         j.knot_off = pd.knot_offset[k];
         j.span = s[ek];
         j.p = p; j.q = q;
-        j.gauss_off = pd.gauss_offset;
+        j.gauss_off = pd.gauss_offset[k];
         j.out_off = tab_off;
         jobs.push_back(j);
         tab_off += record_size(p + 1, q);
@@ -511,7 +524,7 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
       P->spans_h.push_back(s);
       E *= pd.K[k];
       nd *= pd.nf[k];
-      pd.N *= pd.n;
+      pd.N *= pd.nk[k];
       pd.Q *= q;
     }
     pd.elem_offset = e_off; pd.qp_offset = qp_off; pd.dof_offset = dof_off;
@@ -523,7 +536,10 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
     dof_off += nd;
     mat_off += E * (int64_t)pd.N * pd.N;
     dm_off += E * (int64_t)pd.N;
-    if (dm_off > INT32_MAX || dof_off > INT32_MAX) { delete P; return IGA_ERR_UNSUPPORTED; }
+    if (dm_off > INT32_MAX || dof_off > INT32_MAX || E > INT32_MAX) {
+      delete P;
+      return IGA_ERR_UNSUPPORTED;
+    }
     P->ph.push_back(pd);
   }
   P->elem_off.push_back(e_off); P->qp_off.push_back(qp_off); P->dof_off.push_back(dof_off);
@@ -545,7 +561,7 @@ extern "C" int iga_plan(iga_plan_t* out, const iga_patch_desc* patches, int n_pa
       c.K[k] = pd.K[k]; c.nf[k] = pd.nf[k];
       c.span_offset[k] = pd.span_offset[k];
       if (k >= pd.dim) { c.fn_offset[k] = -1; c.W[k] = 1; continue; }
-      std::vector<FnCouple> f = couple_1d(P->spans_h[(size_t)ip * dim + k], pd.p, pd.nf[k]);
+      std::vector<FnCouple> f = couple_1d(P->spans_h[(size_t)ip * dim + k], pd.pk[k], pd.nf[k]);
       c.fn_offset[k] = (int)fc_all.size();
       c.W[k] = f.back().S + (f.back().fhi - f.back().flo + 1);
       int wmax = 0;
@@ -723,14 +739,15 @@ extern "C" int iga_integrate(iga_plan_t P, const double* kappa, const double* rh
     a.K_out = want_K ? (char*)K_out + esz * pd.mat_offset : nullptr;
     a.M_out = want_M ? (char*)M_out + esz * pd.mat_offset : nullptr;
     a.err = P->d_err;
+    const bool spec = fp64_specialised(P->opts, pd);
     if (P->opts.method == IGA_SUMFACT && P->opts.precision == IGA_FP64_DF)
       e = launch_sumfact_df(a, pd.dim, pd.p, pd.q, st);
     else if (P->opts.method == IGA_SUMFACT && P->opts.precision != IGA_FP64)
       e = launch_sumfact_f32(a, pd.dim, pd.p, pd.q, P->opts.precision == IGA_BF16, st);
     else if (P->opts.method == IGA_SUMFACT)
-      e = launch_sumfact_f64(a, pd.dim, pd.p, pd.q, st);
+      e = spec ? launch_sumfact_f64(a, pd.dim, pd.p, pd.q, st) : launch_sumfact_gen(a, pd, st);
     else
-      e = launch_classical_f64(a, pd.dim, pd.p, pd.q, st);
+      e = spec ? launch_classical_f64(a, pd.dim, pd.p, pd.q, st) : launch_classical_gen(a, pd, st);
     ++n_launch;
   }
   if (ev && e == cudaSuccess) {
@@ -747,8 +764,11 @@ extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const d
   if (!P) return IGA_ERR_ARG;
   if (P->sticky != IGA_OK) return P->sticky;
   if (!u || !v || (!grad_kappa && !J_out) || (J_out && !kappa)) return IGA_ERR_ARG;
+  // FP64 plans take every patch (the runtime-sized adjoint where no
+  // specialised one exists); the others need a specialised kernel
   for (const PatchDev& pd : P->ph)
-    if (!adjoint_supported(pd.dim, pd.p, pd.q)) return IGA_ERR_UNSUPPORTED;
+    if (P->opts.precision != IGA_FP64 && !(pd.iso && adjoint_supported(pd.dim, pd.p, pd.q)))
+      return IGA_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -773,7 +793,10 @@ extern "C" int iga_integrate_backward(iga_plan_t P, const double* kappa, const d
     a.grad = grad_kappa ? (char*)grad_kappa + gsz * pd.qp_offset : nullptr;
     a.partial = J_out ? P->d_partial : nullptr;
     a.partial_offset = pd.elem_offset;
-    e = launch_adjoint(a, pd.dim, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
+    if (pd.iso && adjoint_supported(pd.dim, pd.p, pd.q))
+      e = launch_adjoint(a, pd.dim, pd.p, pd.q, fp64, P->opts.precision == IGA_FP64_DF, st);
+    else
+      e = launch_adjoint_gen(a, pd, st);
   }
   if (e == cudaSuccess && J_out) e = launch_reduce_fixed(P->d_partial, P->info.n_elements, J_out, st);
   return finish(P, st, e);
@@ -788,7 +811,7 @@ extern "C" int iga_integrate_grad(iga_plan_t P, const double* jac, const void* G
   if ((!GK && !GM) || (GK && !grad_kappa) || (GM && !grad_rho)) return IGA_ERR_ARG;
   const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
   for (const PatchDev& pd : P->ph)
-    if (!grad_supported(pd.dim, pd.p, pd.q, fp64)) return IGA_ERR_UNSUPPORTED;
+    if (!pd.iso || !grad_supported(pd.dim, pd.p, pd.q, fp64)) return IGA_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -843,6 +866,9 @@ extern "C" int iga_assemble(iga_plan_t P, const void* A_elem, void* values, void
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const bool fp64 = P->opts.precision == IGA_FP64 || P->opts.precision == IGA_FP64_DF;
+  // the gather kernels are specialised per degree (3D: p <= 5, 2D: p <= 8)
+  for (const PatchDev& pd : P->ph)
+    if (!pd.iso || (pd.dim == 3 && pd.p > 5)) return IGA_ERR_UNSUPPORTED;
   cudaError_t e = cudaSuccess;
   for (int ip = 0; ip < P->n_patches && e == cudaSuccess; ++ip)
     e = launch_assemble(P->csr[ip], P->d_fc, P->d_spans, A_elem, values, fp64, st);
@@ -855,7 +881,7 @@ extern "C" int iga_apply(iga_plan_t P, const double* kappa, const double* rho, c
   if (!P || !x || !y) return IGA_ERR_ARG;
   if (P->sticky != IGA_OK) return P->sticky;
   for (const PatchDev& pd : P->ph)
-    if (!apply_supported(pd.dim, pd.p, pd.q)) return IGA_ERR_UNSUPPORTED;
+    if (!pd.iso || !apply_supported(pd.dim, pd.p, pd.q)) return IGA_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -905,7 +931,7 @@ int wq_ensure(iga_plan_s* P) {
   P->wq_coef_off.assign(1, 0);
   for (int ip = 0; ip < P->n_patches && rc == IGA_OK; ++ip) {
     const PatchDev& pd = P->ph[ip];
-    if (pd.p > 5) { rc = IGA_ERR_UNSUPPORTED; break; }
+    if (!pd.iso || pd.p > 5) { rc = IGA_ERR_UNSUPPORTED; break; }
     int64_t grid = 1;
     for (int k = 0; k < 3 && rc == IGA_OK; ++k) {
       iga_plan_s::WqDir& w = P->wq[(size_t)ip * 3 + k];
@@ -1011,7 +1037,7 @@ extern "C" int iga_wq_stiffness(iga_plan_t P, const double* c, double* values, v
   if (P->sticky != IGA_OK) return P->sticky;
   if (P->opts.precision != IGA_FP64 && P->opts.precision != IGA_FP64_DF) return IGA_ERR_UNSUPPORTED;
   for (const PatchDev& pd : P->ph)
-    if (!wq_stiffness_supported(pd.dim, pd.p)) return IGA_ERR_UNSUPPORTED;
+    if (!pd.iso || !wq_stiffness_supported(pd.dim, pd.p)) return IGA_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != P->device) return IGA_ERR_ARG;
   const int rc = wq_ensure(P);
@@ -1191,9 +1217,12 @@ extern "C" int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* ka
   if (!patch || !u || !v || (!grad_kappa && !J_out) || (J_out && !kappa)) return IGA_ERR_ARG;
   const iga_patch_desc& d = *patch;
   if (d.dim != 3) return IGA_ERR_UNSUPPORTED;
-  const int p = d.degree, q = d.n_gauss;
-  if (p < 1 || q < 1 || q > kMaxGauss) return IGA_ERR_ARG;
-  if (!adjoint_supported(3, p, q)) return IGA_ERR_UNSUPPORTED;
+  const int p = d.degree[0], q = d.n_gauss[0];
+  for (int k = 0; k < 3; ++k)
+    if (d.degree[k] < 1 || d.degree[k] > kMaxDegree || d.n_gauss[k] < 1 || d.n_gauss[k] > kMaxGauss)
+      return IGA_ERR_ARG;
+  for (int k = 1; k < 3; ++k)
+    if (d.degree[k] != p || d.n_gauss[k] != q) return IGA_ERR_UNSUPPORTED;
   int K[3], nf[3];
   int64_t E = 1, tab = 0;
   for (int k = 0; k < 3; ++k) {
@@ -1256,7 +1285,15 @@ extern "C" int iga_adjoint_noalloc(const iga_patch_desc* patch, const double* ka
     a.grad = grad_kappa;
     a.partial = J_out ? scratch + kNaPartials : nullptr;
     a.partial_offset = 0;
-    e = launch_adjoint(a, 3, p, q, true, false, st);
+    if (adjoint_supported(3, p, q)) {
+      e = launch_adjoint(a, 3, p, q, true, false, st);
+    } else {
+      PatchDev ph{};
+      ph.dim = 3;
+      ph.p = p; ph.q = q; ph.n = p + 1;
+      for (int k = 0; k < 3; ++k) { ph.pk[k] = p; ph.qk[k] = q; ph.nk[k] = p + 1; }
+      e = launch_adjoint_gen(a, ph, st);
+    }
   }
   if (e == cudaSuccess && J_out) e = launch_reduce_fixed(scratch + kNaPartials, E, J_out, st);
   if (e != cudaSuccess) return map_cuda(e);

@@ -9,14 +9,22 @@
 
 namespace iga {
 
-constexpr int kMaxDegree3D = 5;
-constexpr int kMaxDegree2D = 8;
+// Degrees and Gauss orders accepted by iga_plan (per direction).  Degrees
+// above the specialised kernels' range, a different degree or Gauss order per
+// direction, and Gauss orders other than p+1 / p+2 run on the runtime-sized
+// FP64 kernels of k_generic64.cu.
+constexpr int kMaxDegree = 8;
+constexpr int kMaxDegree2D = kMaxDegree;   // size of the per-point Cox--de Boor arrays
 constexpr int kMaxGauss = 16;
 
 // Per-patch description, uploaded to the device.  Offsets index the plan's
-// concatenated arrays.
+// concatenated arrays.  p, q, n are direction 0's values; pk, qk, nk hold
+// every direction's (1 beyond dim for nk and qk), iso = 1 when all directions
+// of the patch share p and q.
 struct PatchDev {
   int dim, p, q, n, N, Q;
+  int pk[3], qk[3], nk[3];
+  int iso;
   int K[3];              // elements per direction
   int nf[3];             // functions per direction (global 1D dofs)
   int64_t elem_offset;   // first global element
@@ -27,7 +35,7 @@ struct PatchDev {
   int64_t tab_offset[3]; // first double of direction k's basis records
   int span_offset[3];    // first entry of direction k's spans
   int knot_offset[3];    // first knot of direction k
-  int gauss_offset;      // first reference node / weight of this patch
+  int gauss_offset[3];   // first reference node / weight of direction k's rule
 };
 
 // Basis record of one element of one direction: val[q][n], der[q][n], w[q]
@@ -69,6 +77,13 @@ struct ElemArgs {
 cudaError_t launch_sumfact_f64(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
 // FP64 classical integration (Algorithm 1).
 cudaError_t launch_classical_f64(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
+
+// Runtime-sized FP64 forms for any patch (degree 1..8 and Gauss order 1..16
+// per direction, 2D and 3D): sum factorization tiled over the (a3, b3) blocks
+// of the element matrix, classical integration tiled over quadrature points,
+// and the matrix-free adjoint.  ph is the host copy of the patch.
+cudaError_t launch_sumfact_gen(const ElemArgs& a, const PatchDev& ph, cudaStream_t st);
+cudaError_t launch_classical_gen(const ElemArgs& a, const PatchDev& ph, cudaStream_t st);
 
 // Persistent batched form: one work item = `count` consecutive elements of one
 // patch; CTAs pop items from a device counter.
@@ -121,6 +136,8 @@ struct AdjArgs {
 };
 cudaError_t launch_adjoint(const AdjArgs& a, int dim, int p, int q, bool fp64, bool df,
                            cudaStream_t st);
+// FP64 adjoint for any patch (u, v double); ph gives the per-direction sizes.
+cudaError_t launch_adjoint_gen(const AdjArgs& a, const PatchDev& ph, cudaStream_t st);
 cudaError_t launch_reduce_fixed(const double* partial, int64_t n, double* out, cudaStream_t st);
 bool adjoint_supported(int dim, int p, int q);
 

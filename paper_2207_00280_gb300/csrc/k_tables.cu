@@ -78,7 +78,7 @@ cudaError_t launch_basis_tables(const TableJob* jobs, int n_jobs, const double* 
 }
 
 // Global dof of every local function of every element (support set of the
-// Remark in Sec. 3.1): dof = dof_offset + sum_k (s_k - p + a_k) stride_k.
+// Remark in Sec. 3.1): dof = dof_offset + sum_k (s_k - p_k + a_k) stride_k.
 // One block per element (grid-stride), one thread per local function:
 // consecutive threads write consecutive entries.  The planner keeps every
 // index below 2^31, so the arithmetic is 32-bit (64-bit division is slow).
@@ -87,18 +87,18 @@ __global__ void k_dofmap(const PatchDev* __restrict__ pdp, const int* __restrict
   const PatchDev pd = *pdp;
   const int a = threadIdx.x;
   if (a >= pd.N) return;
-  const int a1 = a % pd.n;
-  const int a2 = (a / pd.n) % pd.n;
-  const int a3 = a / (pd.n * pd.n);
+  const int a1 = a % pd.nk[0];
+  const int a2 = (a / pd.nk[0]) % pd.nk[1];
+  const int a3 = a / (pd.nk[0] * pd.nk[1]);
   const int base = (int)pd.dof_offset;
   for (int e = blockIdx.x; e < n_elem; e += gridDim.x) {
     const int e1 = e % pd.K[0];
     const int r = e / pd.K[0];
     const int e2 = r % pd.K[1];
     const int e3 = r / pd.K[1];
-    int g = spans[pd.span_offset[0] + e1] - pd.p + a1;
-    g += (spans[pd.span_offset[1] + e2] - pd.p + a2) * pd.nf[0];
-    if (pd.dim == 3) g += (spans[pd.span_offset[2] + e3] - pd.p + a3) * pd.nf[0] * pd.nf[1];
+    int g = spans[pd.span_offset[0] + e1] - pd.pk[0] + a1;
+    g += (spans[pd.span_offset[1] + e2] - pd.pk[1] + a2) * pd.nf[0];
+    if (pd.dim == 3) g += (spans[pd.span_offset[2] + e3] - pd.pk[2] + a3) * pd.nf[0] * pd.nf[1];
     dof[(int64_t)e * pd.N + a] = base + g;
   }
 }

@@ -20,12 +20,31 @@ _PRECISIONS = {"fp64": capi.IGA_FP64, "fp32": capi.IGA_FP32, "bf16": capi.IGA_BF
 @dataclass
 class Patch:
     knots: list          # one 1D array per direction
-    degree: int
-    n_gauss: int
+    degree: object       # int (every direction) or one int per direction
+    n_gauss: object      # int (every direction) or one int per direction
 
     @property
     def dim(self) -> int:
         return len(self.knots)
+
+    def per_dir(self, v):
+        return [int(v)] * self.dim if np.ndim(v) == 0 else [int(x) for x in v]
+
+    @property
+    def degrees(self):
+        return self.per_dir(self.degree)
+
+    @property
+    def gauss(self):
+        return self.per_dir(self.n_gauss)
+
+    @property
+    def N(self) -> int:
+        return int(np.prod([p + 1 for p in self.degrees]))
+
+    @property
+    def Q(self) -> int:
+        return int(np.prod(self.gauss))
 
 
 def _ptr(t):
@@ -58,7 +77,8 @@ class IgaPlan:
         descs = []
         for pt in self.patches:
             d = capi.PatchDesc()
-            d.dim, d.degree, d.n_gauss = pt.dim, int(pt.degree), int(pt.n_gauss)
+            d.dim = pt.dim
+            d.set_order(pt.degrees, pt.gauss)
             for k, t in enumerate(pt.knots):
                 arr = np.ascontiguousarray(t, dtype=np.float64)
                 self._knots.append(arr)
@@ -224,8 +244,7 @@ class IgaPlan:
 
     def patch_view(self, flat, i: int):
         """Reshape patch i's block of a flat K/M output to [E][N][N]."""
-        pt = self.patches[i]
-        N = (pt.degree + 1) ** pt.dim
+        N = self.patches[i].N
         a, b = self.mat_offset[i], self.mat_offset[i + 1]
         return flat[a:b].view(-1, N, N)
 

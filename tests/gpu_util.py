@@ -36,7 +36,7 @@ def run_gpu(knots, p, q, kappa=None, rho=None, G=None, method="sumfact", precisi
         M.fill_(float("nan"))
     plan.integrate(kappa=kap, rho=rh, jac=jac, K=K, M=M, dof=D)
     torch.cuda.synchronize()
-    N = (p + 1) ** len(knots)
+    N = plan.patches[0].N
     out = {
         "K": K.view(-1, N, N) if K is not None else None,
         "M": M.view(-1, N, N) if M is not None else None,

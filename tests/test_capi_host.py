@@ -51,10 +51,12 @@ def test_status_strings(capi):
 def _desc(capi, dim=3, p=3, q=4, knots=None):
     from paper_2207_00280_gb300 import workloads as wl
     d = capi.PatchDesc()
-    d.dim, d.degree, d.n_gauss = dim, p, q
+    p0 = p if np.ndim(p) == 0 else p[0]
+    d.dim = dim
+    d.set_order(p, q)
     keep = []
     for k in range(dim):
-        t = np.ascontiguousarray(knots[k] if knots is not None else wl.open_uniform_knots(4, p))
+        t = np.ascontiguousarray(knots[k] if knots is not None else wl.open_uniform_knots(4, p0))
         keep.append(t)
         d.n_knots[k] = len(t)
         d.knots[k] = t.ctypes.data
@@ -106,15 +108,40 @@ def test_argument_errors(capi):
 
 
 def test_degree_and_gauss_limits(capi):
+    """The boundary's domain: 1 <= p_k <= 8 and 1 <= q_k <= 16 per direction
+    (IGA_ERR_ARG outside); FP64 takes every patch inside it, anisotropic ones
+    included; FP32/BF16/FP64_DF plans only the (p, q) classes their specialised
+    kernels cover."""
     from paper_2207_00280_gb300 import workloads as wl
-    d, keep = _desc(capi, p=0, q=1, knots=[wl.open_uniform_knots(4, 1)] * 3)
+    ok = (capi.IGA_OK, capi.IGA_ERR_CUDA)   # a valid plan stops at its first CUDA call without a GPU
+    for p, q in ((0, 1), (9, 10), (3, 17), (3, 0)):
+        pk = max(p, 1)
+        d, keep = _desc(capi, p=p, q=q, knots=[wl.open_uniform_knots(4, pk)] * 3)
+        assert _plan_rc(capi, [d], _opts(capi)) == capi.IGA_ERR_ARG, (p, q)
+    # one direction out of range
+    d, keep = _desc(capi, p=(2, 9, 2), q=(3, 10, 3),
+                    knots=[wl.open_uniform_knots(3, 2), wl.open_uniform_knots(3, 9), wl.open_uniform_knots(3, 2)])
     assert _plan_rc(capi, [d], _opts(capi)) == capi.IGA_ERR_ARG
-    d, keep = _desc(capi, p=6, q=7, knots=[wl.open_uniform_knots(4, 6)] * 3)
-    assert _plan_rc(capi, [d], _opts(capi)) == capi.IGA_ERR_UNSUPPORTED
-    d, keep = _desc(capi, p=3, q=17)
-    assert _plan_rc(capi, [d], _opts(capi)) == capi.IGA_ERR_ARG
-    d, keep = _desc(capi, p=3, q=7)
-    assert _plan_rc(capi, [d], _opts(capi)) == capi.IGA_ERR_UNSUPPORTED
+    # FP64, classical and sum factorization: p up to 8, q from 1 to 16, a
+    # different degree and Gauss order per direction
+    for p, q in ((8, 9), (6, 7), (3, 1), (3, 16), (1, 16)):
+        d, keep = _desc(capi, p=p, q=q, knots=[wl.open_uniform_knots(2, p)] * 3)
+        for method in (0, 1):
+            assert _plan_rc(capi, [d], _opts(capi, method=method)) in ok, (p, q, method)
+    ps, qs = (1, 4, 8), (2, 7, 16)
+    d, keep = _desc(capi, p=ps, q=qs, knots=[wl.open_uniform_knots(2, pk) for pk in ps])
+    for method in (0, 1):
+        assert _plan_rc(capi, [d], _opts(capi, method=method)) in ok
+    d2, keep2 = _desc(capi, dim=2, p=(8, 3), q=(16, 2),
+                      knots=[wl.open_uniform_knots(3, 8), wl.open_uniform_knots(3, 3)])
+    assert _plan_rc(capi, [d2], _opts(capi)) in ok
+    # the low-precision and float-float forms need their specialised kernels
+    for prec in (1, 2, 3):
+        assert _plan_rc(capi, [d], _opts(capi, precision=prec)) == capi.IGA_ERR_UNSUPPORTED
+        d6, keep6 = _desc(capi, p=6, q=7, knots=[wl.open_uniform_knots(2, 6)] * 3)
+        assert _plan_rc(capi, [d6], _opts(capi, precision=prec)) == capi.IGA_ERR_UNSUPPORTED
+        d3, keep3 = _desc(capi, p=3, q=7)
+        assert _plan_rc(capi, [d3], _opts(capi, precision=prec)) == capi.IGA_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("bad", ["not_open", "decreasing", "multiplicity", "short", "nan", "end_mult"])
@@ -154,15 +181,18 @@ def test_valid_plan_without_gpu_reports_cuda_error(capi):
 
 def test_noalloc_size_limits_on_host(capi):
     """iga_adjoint_noalloc rejects a patch beyond its fixed scratch on the host,
-    before any CUDA call: more knots per direction than the scratch holds, and
-    more elements (p = 1, 70^3 = 343,000 > 262,144).  The pointers are never
-    dereferenced on these paths."""
+    before any CUDA call: more knots per direction than the scratch holds, more
+    elements (p = 1, 70^3 = 343,000 > 262,144), and more basis-table doubles.
+    The pointers are never dereferenced on these paths."""
     from paper_2207_00280_gb300 import workloads as wl
     L = capi.lib()
     dummy = ctypes.c_void_p(64)
     cases = [
         ([wl.open_uniform_knots(1100, 3), wl.open_uniform_knots(2, 3), wl.open_uniform_knots(2, 3)], 3, 4),
         ([wl.open_uniform_knots(70, 1)] * 3, 1, 2),
+        # 261,820 elements (under the limit) but (1007 + 260 + 1) x 304 = 385,472
+        # doubles of degree-8, 16-point basis tables (over the 196,608 limit)
+        ([wl.open_uniform_knots(1007, 8), wl.open_uniform_knots(260, 8), wl.open_uniform_knots(1, 8)], 8, 16),
     ]
     for knots, p, q in cases:
         d, keep = _desc(capi, p=p, q=q, knots=knots)

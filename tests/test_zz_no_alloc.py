@@ -24,7 +24,8 @@ TOL = 1e-12  # the FP64 tolerance of the other GPU tests
 
 def _desc(knots, p, q):
     d = capi.PatchDesc()
-    d.dim, d.degree, d.n_gauss = 3, p, q
+    d.dim = 3
+    d.set_order(p, q)
     keep = [np.ascontiguousarray(t, dtype=np.float64) for t in knots]
     for k, t in enumerate(keep):
         d.n_knots[k] = len(t)
@@ -48,7 +49,8 @@ def _noalloc(knots, p, q, kappa, jac, u, v):
 
 @pytest.mark.parametrize("curved", [False, True])
 def test_noalloc_matches_plan_twice(curved):
-    cases = [(3, 4, (7, 5, 6), 31), (2, 3, (9, 4, 5), 32)]  # two different calls in a row
+    # different calls in a row; the last one (degree 7) runs the runtime-sized adjoint
+    cases = [(3, 4, (7, 5, 6), 31), (2, 3, (9, 4, 5), 32), (7, 8, (2, 2, 1), 33)]
     for p, q, Ks, seed in cases:
         knots = [wl.open_uniform_knots(K, p) for K in Ks]
         E, Q = int(np.prod(Ks)), q ** 3
