@@ -277,9 +277,12 @@ __global__ void __launch_bounds__(kGenThreads)
         CB[t] = acc;
       }
       __syncthreads();
-      // stage 3 (x): block (a3, b3) of the element matrices
+      // stage 3 (x): block (a3, b3) of the element matrices; a diagonal block
+      // (a3 = b3) is symmetric, so only its upper triangle is formed and every
+      // entry is stored at (row, col) and (col, row)
       for (int t = tid; t < n12 * n12; t += kGenThreads) {
         const int r = t / n12, c = t % n12;
+        if (a3 == b3 && r > c) continue;
         const int a1 = r % n1, a2 = r / n1, b1 = c % n1, b2 = c / n1;
         const int64_t row = r + (int64_t)n12 * a3, col = c + (int64_t)n12 * b3;
         if (wantK) {
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(kGenThreads)
             for (int k1 = 0; k1 < q1; ++k1) acc = fma(x[k1], cb[k1], acc);
           }
           Ke[row * N + col] = acc;
-          if (a3 != b3) Ke[col * N + row] = acc;
+          if (row != col) Ke[col * N + row] = acc;
         }
         if (wantM) {
           double acc = 0.0;
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(kGenThreads)
           const double* cb = CB + ((4 * n2 + a2) * n2 + b2) * q1;
           for (int k1 = 0; k1 < q1; ++k1) acc = fma(x[k1], cb[k1], acc);
           Me[row * N + col] = acc;
-          if (a3 != b3) Me[col * N + row] = acc;
+          if (row != col) Me[col * N + row] = acc;
         }
       }
       __syncthreads();

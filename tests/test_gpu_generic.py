@@ -59,6 +59,7 @@ def _check(oracle_mod, knots, ps, qs, method, geometry, mass=True, stiffness=Tru
         Mg = out["M"].cpu().numpy()
         assert np.isfinite(Mg).all()
         errs["M"] = rel_frob(Mg, Mr)
+        assert np.array_equal(Mg, Mg.transpose(0, 2, 1))
     print(f"{method} p={ps} q={qs} {geometry}: {errs}")
     assert max(errs.values()) <= FP64_TOL, errs
     np.testing.assert_array_equal(out["dof"].cpu().numpy(), P.dofmap())
