@@ -660,6 +660,7 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
         torch.cuda.empty_cache()
     batch["speedup_graph_vs_per_patch"] = round(batch["per_patch"]["ms_per_step"] /
                                                 batch["persistent_graph_autotuned"]["ms_per_step"], 3)
+    batch["autotuned_schedules"] = autotune_table()
     forms["batch_64_patches_fp32"] = batch
     # adjoint: J = u^T K(kappa) v and dJ/dkappa, 40^3 p=3
     A = wl.WORKLOADS["3d_p3_40_adjoint"]
@@ -742,6 +743,30 @@ def measure_curved_p4(stream, flush, dev):
     for k, v in out.items():
         if isinstance(v, dict) and "ms_per_step" in v:
             v["speedup_vs_classical_fp64"] = round(base / v["ms_per_step"], 3)
+    return out
+
+
+SCHED_NAMES = {0: "cta", 4: "cta_mma_sync_stage3", 8: "cta_other_size", 16: "warp_per_element"}
+
+
+def autotune_table():
+    """The batch autotuner's choices, read back from its cache file: per (p, q)
+    class the schedule and the elements per work item."""
+    path = os.environ.get("IGA_AUTOTUNE_CACHE")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    out = {}
+    for k, v in tab.items():
+        parts = k.split("/")
+        try:
+            i = parts.index("sf3v2")
+        except ValueError:
+            continue
+        cls = "/".join(parts[i + 1:])
+        out[cls] = {"schedule": SCHED_NAMES.get(v // 100, str(v // 100)), "elements_per_item": v % 100}
     return out
 
 
@@ -1035,6 +1060,10 @@ def main():
             print(json.dumps(line), flush=True)
         return 0
 
+    # the batch autotuner's choices go to a file the line reports (a fresh one
+    # per run, so that every run tunes)
+    os.environ.setdefault("IGA_AUTOTUNE_CACHE",
+                          os.path.join("/tmp", f"iga_autotune_{os.getpid()}.json"))
     ws, rank, local = dist_setup()
     line = run_ours(args, ws, rank, local)
     if rank == 0:

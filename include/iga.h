@@ -95,7 +95,18 @@ enum { IGA_MASS = 1, IGA_STIFF = 2 };
  *   PERSISTENT_GRAPH: the same kernels plus the table and dof-map kernels
  *                     captured once into a CUDA graph (classes on parallel
  *                     branches) and replayed while the pointers are unchanged.
- * The persistent schedules exist for FP32/BF16 sum factorization only. */
+ * The persistent schedules exist for FP32/BF16 sum factorization only.
+ * Within them the autotuner chooses, per (degree, Gauss order) class, among
+ * the CTA-per-element kernel (one thread per element-matrix entry), its
+ * variants where the class has them (stage 3 on warp-level mma.sync instead of
+ * tcgen05 at p = 3 and BF16 p = 4; 512 instead of 256 threads per CTA at
+ * p = 4, and 256 instead of 512 at p = 5, identity geometry), and a
+ * warp-per-element kernel (p <= 2, all contractions in FP32), each with work
+ * items of 1, 2, 4 or 8 elements, by timing every candidate (median of three
+ * launches).  The environment variable IGA_BATCH_SCHED, read by iga_plan,
+ * forces one schedule (0 CTA, 4 mma.sync form, 8 other CTA size, 16 warp) for
+ * the classes that have it and disables the tuning; IGA_AUTOTUNE_CACHE names a
+ * JSON file that keeps the choices ({key: schedule * 100 + work-item size}). */
 enum { IGA_SCHED_AUTO = 0, IGA_SCHED_PER_PATCH = 1, IGA_SCHED_PERSISTENT = 2,
        IGA_SCHED_PERSISTENT_GRAPH = 3 };
 

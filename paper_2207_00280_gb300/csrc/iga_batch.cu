@@ -18,8 +18,10 @@ constexpr int kEpiCandidates[] = {1, 2, 4, 8};
 constexpr int kNumEpi = 4;
 
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;  // tuning key -> elements per work item
+std::map<std::string, int> g_tune;  // tuning key -> schedule * 100 + elements per work item
 bool g_tune_loaded = false;
+
+int tune_value(int sched, int epi) { return sched * 100 + epi; }
 
 const char* cache_path() {
   const char* p = getenv("IGA_AUTOTUNE_CACHE");
@@ -92,6 +94,8 @@ int batch_plan(BatchState* B, const std::vector<PatchDev>& ph, int precision, in
   B->schedule = schedule;
   const char* bud = getenv("IGA_QUEUE_BUDGET_NS");
   B->budget_ns = bud ? strtoull(bud, nullptr, 10) : 0ull;
+  const char* fs = getenv("IGA_BATCH_SCHED");
+  const int forced = (fs && fs[0]) ? atoi(fs) : -1;
   const char* corrupt = getenv("IGA_TEST_CORRUPT_QUEUE");
   const bool corrupt_items = corrupt && corrupt[0] == '1';
   // classes keyed by (p, q), patches of a class in decreasing size
@@ -124,8 +128,19 @@ int batch_plan(BatchState* B, const std::vector<PatchDev>& ph, int precision, in
       c.n_items[ci] = (int)((int64_t)all.size() - c.item_offset[ci]);
     }
     c.epi = c.p >= 3 ? 1 : (c.p == 2 ? 2 : 4);  // default until tuned
+    c.sched = kSchedCta;
     c.tuned = false;
     c.split = !queue_both_fit(c.p, c.q, B->bf16);
+    if (forced >= 0) {
+      // a schedule forced by the caller (tests): the classes that have it use
+      // it, the others keep the default; no tuning
+      const bool has = forced == kSchedCta ||
+                       (forced == kSchedWarp && warp_schedule_supported(c.p, c.q)) ||
+                       ((forced == kSchedCtaAltForm || forced == kSchedCtaAltSize) &&
+                        f32_variant_supported(c.p, c.q, B->bf16, forced));
+      if (has) c.sched = forced;
+      c.tuned = true;
+    }
     B->classes.push_back(c);
   }
   if (corrupt_items)  // host-made fault: the first item of every list names a missing patch
@@ -173,27 +188,53 @@ void batch_free(BatchState* B) {
   B->d_counters = nullptr;
 }
 
-// Launch one class (both matrix modes as needed) on stream s.
+// One queue launch of class c in schedule `sched` (grid <= 0: the resident
+// capacity, capped by the items).
+static cudaError_t launch_sched(const BatchState* B, const BatchClass& c, const QueueArgs& a,
+                                int mode, int sched, cudaStream_t s) {
+  int cap = 0;
+  cudaError_t e;
+  if (sched == kSchedWarp) {
+    e = launch_sumfact_warp_queue(a, c.p, c.q, mode, 0, s, &cap);
+    if (e != cudaSuccess) return e;
+    return launch_sumfact_warp_queue(a, c.p, c.q, mode, std::max(1, std::min(cap, a.n_items)), s,
+                                     nullptr);
+  }
+  if (sched == kSchedCta) {
+    e = launch_sumfact_f32_queue(a, c.p, c.q, B->bf16, mode, 0, s, &cap);
+    if (e != cudaSuccess) return e;
+    return launch_sumfact_f32_queue(a, c.p, c.q, B->bf16, mode, std::max(1, std::min(cap, a.n_items)),
+                                    s, nullptr);
+  }
+  e = launch_sumfact_f32_queue_alt(a, c.p, c.q, B->bf16, mode, sched, 0, s, &cap);
+  if (e != cudaSuccess) return e;
+  return launch_sumfact_f32_queue_alt(a, c.p, c.q, B->bf16, mode, sched,
+                                      std::max(1, std::min(cap, a.n_items)), s, nullptr);
+}
+
+// Launch one class (both matrix modes as needed) on stream s, in its chosen
+// schedule or the given one (sched_override >= 0, epi_override > 0).
 static cudaError_t launch_class(BatchState* B, size_t ci, const QueueArgs& base, int mode,
-                                cudaStream_t s, int epi_override) {
+                                cudaStream_t s, int epi_override, int sched_override = -1) {
   BatchClass& c = B->classes[ci];
   const int ei = epi_index(epi_override > 0 ? epi_override : c.epi);
+  int sched = sched_override >= 0 ? sched_override : c.sched;
+  // the 512-thread variant exists for the identity map only
+  if (sched == kSchedCtaAltSize && base.jac) sched = kSchedCta;
   QueueArgs a = base;
   a.items = B->d_items + c.item_offset[ei];
   a.n_items = c.n_items[ei];
   a.budget_ns = B->budget_ns;
-  const int modes[2] = {c.split && mode == 0 ? 1 : mode, 2};
-  const int n_launch = (c.split && mode == 0) ? 2 : 1;
+  // the warp form holds both matrices; the CTA forms split them when they do not fit
+  const bool split = c.split && mode == 0 && sched != kSchedWarp;
+  const int modes[2] = {split ? 1 : mode, 2};
+  const int n_launch = split ? 2 : 1;
   for (int m = 0; m < n_launch; ++m) {
     QueueArgs am = a;
     am.counter = B->d_counters + 2 * ci + m;
     if (modes[m] == 1) am.M_out = nullptr;
     if (modes[m] == 2) am.K_out = nullptr;
-    int cap = 0;
-    cudaError_t e = launch_sumfact_f32_queue(am, c.p, c.q, B->bf16, modes[m], 0, s, &cap);
-    if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(cap, a.n_items));
-    e = launch_sumfact_f32_queue(am, c.p, c.q, B->bf16, modes[m], grid, s, nullptr);
+    cudaError_t e = launch_sched(B, c, am, modes[m], sched, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -202,14 +243,20 @@ static cudaError_t launch_class(BatchState* B, size_t ci, const QueueArgs& base,
 static std::string tune_key(const BatchState* B, const BatchClass& c, int mode, bool gen) {
   int64_t bucket = 1;
   while (bucket < c.elements) bucket *= 4;
-  return B->gen_key + "/sf3/" + (B->bf16 ? "bf16" : "fp32") + "/p" + std::to_string(c.p) + "q" +
+  return B->gen_key + "/sf3v2/" + (B->bf16 ? "bf16" : "fp32") + "/p" + std::to_string(c.p) + "q" +
          std::to_string(c.q) + "/m" + std::to_string(mode) + (gen ? "/jac" : "/id") + "/E" +
          std::to_string(bucket);
 }
 
-// Autotuner: for every untuned class, time each work-item size with CUDA
-// events (one warm-up and one timed launch of the class alone on stream st)
-// and keep the fastest; results are cached per GPU, driver and class shape.
+// Autotuner: for every untuned class, time every candidate schedule (the
+// CTA-per-element kernel, its variants where the class has them, the
+// warp-per-element kernel for p <= 2) with every work-item size, each
+// candidate alone on stream st with CUDA events: one warm-up launch, then
+// three timed launches of which the median counts.  The fastest candidate is
+// kept, but a candidate replaces the current best only when it is at least 3%
+// faster, so that timing noise does not flip the choice between nearly equal
+// candidates.  Results are cached per GPU, driver and class shape (in memory,
+// and in the file named by IGA_AUTOTUNE_CACHE if set).
 static cudaError_t autotune(BatchState* B, const QueueArgs& base, int mode, cudaStream_t st) {
   const bool gen = base.jac != nullptr;
   cudaEvent_t t0, t1;
@@ -224,29 +271,63 @@ static cudaError_t autotune(BatchState* B, const QueueArgs& base, int mode, cuda
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       auto it = g_tune.find(key);
-      if (it != g_tune.end()) { c.epi = it->second; c.tuned = true; continue; }
-    }
-    float best = 1e30f;
-    int best_epi = c.epi;
-    for (int k = 0; k < kNumEpi && e == cudaSuccess; ++k) {
-      const int epi = kEpiCandidates[k];
-      if (k > 0 && c.n_items[k] < 152) break;  // keep every SM busy
-      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-        e = cudaMemsetAsync(B->d_counters + 2 * ci, 0, 2 * sizeof(int), st);
-        if (e == cudaSuccess) e = cudaEventRecord(t0, st);
-        if (e == cudaSuccess) e = launch_class(B, ci, base, mode, st, epi);
-        if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-        if (e == cudaSuccess && rep == 1 && ms < best) { best = ms; best_epi = epi; }
+      if (it != g_tune.end()) {
+        c.sched = it->second / 100;
+        c.epi = it->second % 100;
+        c.tuned = true;
+        continue;
       }
+    }
+    std::vector<int> scheds = {kSchedCta};
+    for (int v : {kSchedCtaAltForm, kSchedCtaAltSize})
+      if (f32_variant_supported(c.p, c.q, B->bf16, v) && !(v == kSchedCtaAltSize && gen))
+        scheds.push_back(v);
+    if (warp_schedule_supported(c.p, c.q)) scheds.push_back(kSchedWarp);
+    float best = 1e30f;
+    int best_epi = c.epi, best_sched = c.sched;
+    for (int sched : scheds) {
+      for (int k = 0; k < kNumEpi && e == cudaSuccess; ++k) {
+        const int epi = kEpiCandidates[k];
+        if (k > 0 && c.n_items[k] < 152) break;  // keep every SM busy
+        float ts[4];
+        bool ok = true;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+          e = cudaMemsetAsync(B->d_counters + 2 * ci, 0, 2 * sizeof(int), st);
+          if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+          if (e == cudaSuccess) {
+            const cudaError_t el = launch_class(B, ci, base, mode, st, epi, sched);
+            if (el == cudaErrorNotSupported || el == cudaErrorInvalidValue) {
+              ok = false;          // this variant does not fit the class: skip it
+              cudaGetLastError();
+              break;
+            }
+            e = el;
+          }
+          if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+          if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+          if (e != cudaSuccess) { ok = false; break; }
+          ts[rep] = ms;
+        }
+        if (e != cudaSuccess) break;
+        if (!ok) break;
+        std::sort(ts + 1, ts + 4);   // ts[0] is the warm-up
+        const float med = ts[2];
+        if (med < 0.97f * best || best >= 1e29f) {
+          best = med;
+          best_epi = epi;
+          best_sched = sched;
+        }
+      }
+      if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) break;
     c.epi = best_epi;
+    c.sched = best_sched;
     c.tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = best_epi;
+    g_tune[key] = tune_value(best_sched, best_epi);
     save_cache_locked();
   }
   cudaEventDestroy(t0);

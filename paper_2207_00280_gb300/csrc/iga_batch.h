@@ -14,6 +14,7 @@ struct BatchClass {
   int64_t item_offset[4];   // one item list per work-item size candidate
   int n_items[4];
   int epi;                  // chosen elements per work item
+  int sched;                // chosen schedule (kSched*)
   bool tuned;
   bool split;               // stiffness and mass in separate launches
 };

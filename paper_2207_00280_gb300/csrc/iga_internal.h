@@ -111,6 +111,21 @@ cudaError_t launch_sumfact_f32_queue(const QueueArgs& b, int p, int q, bool bf16
                                      int grid, cudaStream_t st, int* max_grid);
 bool queue_both_fit(int p, int q, bool bf16);
 
+// Schedules of one (p, q) class of the persistent batched launch, chosen by
+// the autotuner: the default CTA-per-element kernel, its variants (stage 3 on
+// mma.sync where the default is tcgen05; the other CTA size), and the
+// warp-per-element kernel (p <= 2).  The variant values are the MODE flags of
+// k_sumfact32.cuh.
+enum { kSchedCta = 0, kSchedCtaAltForm = 4, kSchedCtaAltSize = 8, kSchedWarp = 16 };
+bool f32_variant_supported(int p, int q, bool bf16, int variant);
+cudaError_t launch_sumfact_f32_queue_alt(const QueueArgs& b, int p, int q, bool bf16, int mode,
+                                         int variant, int grid, cudaStream_t st, int* max_grid);
+bool warp_schedule_supported(int p, int q);
+// max_grid reports the number of queue consumers (warps) that fit; grid is a
+// number of warps.
+cudaError_t launch_sumfact_warp_queue(const QueueArgs& b, int p, int q, int mode, int grid,
+                                      cudaStream_t st, int* max_grid);
+
 // FP32 sum factorization (3D): FP64 cofactors/determinant, FP32 contractions;
 // with bf16 = true the last contraction runs on the tensor cores in BF16.
 cudaError_t launch_sumfact_f32(const ElemArgs& a, int dim, int p, int q, bool bf16,

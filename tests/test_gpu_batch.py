@@ -46,8 +46,19 @@ def test_persistent_equals_per_patch_and_oracle(oracle_mod, prec):
     nqp = sum(s.E * s.Q for s in specs)
     kappa = torch.as_tensor(wl.lognormal(nqp, 2210), device=dev)
     ref = _batch(specs, kappa, "per_patch", prec)
+    tol = FP32_TOL if prec == "fp32" else BF16_TOL
     for sched in ("persistent", "graph", "auto"):
         plan, K, M, D = _batch(specs, kappa, sched, prec)
+        if sched == "auto":
+            # the autotuner may pick another schedule (warp-per-element, the
+            # other stage-3 form or CTA size): same sums, another rounding order
+            assert torch.equal(D, ref[3])
+            for i in range(len(specs)):
+                assert rel_frob(plan.patch_view(K, i).cpu().numpy(),
+                                ref[0].patch_view(ref[1], i).cpu().numpy()) <= tol
+                assert rel_frob(plan.patch_view(M, i).cpu().numpy(),
+                                ref[0].patch_view(ref[2], i).cpu().numpy()) <= tol
+            continue
         assert torch.equal(K, ref[1]) and torch.equal(M, ref[2]) and torch.equal(D, ref[3]), sched
         # the graph is replayed for the same pointers: same result again
         plan.integrate(kappa=kappa, K=K, M=M, dof=D)
@@ -191,4 +202,45 @@ def test_autotune_cache_file(tmp_path):
             os.environ["IGA_AUTOTUNE_CACHE"] = old
     if path.exists():  # the cache is process-wide: an earlier test may have tuned these classes
         tab = json.loads(path.read_text())
-        assert all(v in (1, 2, 4, 8) for v in tab.values())
+        assert all(v % 100 in (1, 2, 4, 8) and v // 100 in (0, 4, 8, 16) for v in tab.values())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("forced", [4, 8, 16])
+@pytest.mark.parametrize("curved", [False, True])
+def test_forced_schedules_match_oracle(oracle_mod, prec, forced, curved):
+    """Every schedule the autotuner can pick, forced through IGA_BATCH_SCHED on a
+    batch of every degree 1..5: the mma.sync stage-3 form (4; p = 3, BF16
+    p = 4), the other CTA size (8; p = 4, 5, identity map), the warp-per-element
+    kernel (16; p <= 2).  Each patch against the oracle within the plan's
+    tolerance, dof maps bit-exact."""
+    specs = _specs_small()
+    nqp = sum(s.E * s.Q for s in specs)
+    kappa = torch.as_tensor(wl.lognormal(nqp, 2211), device=dev)
+    G = None
+    if curved:
+        G = torch.as_tensor(np.concatenate([wl.curved_map_jacobian(s.knots, s.q).reshape(-1)
+                                            for s in specs]), device=dev)
+    old = os.environ.get("IGA_BATCH_SCHED")
+    os.environ["IGA_BATCH_SCHED"] = str(forced)
+    try:
+        plan, K, M, D = _batch(specs, kappa, "graph", prec, G=G)
+    finally:
+        if old is None:
+            os.environ.pop("IGA_BATCH_SCHED", None)
+        else:
+            os.environ["IGA_BATCH_SCHED"] = old
+    kh = kappa.cpu().numpy()
+    Gh = G.cpu().numpy() if curved else None
+    tol = FP32_TOL if prec == "fp32" else BF16_TOL
+    g0 = 0
+    for i, s in enumerate(specs):
+        P = oracle_mod.Patch(s.knots, s.p, s.q)
+        q0, q1 = plan.qp_offset[i], plan.qp_offset[i + 1]
+        Gi = Gh[g0 * 9:(g0 + P.E * P.Q) * 9].reshape(P.E, P.Q, 3, 3) if curved else None
+        g0 += P.E * P.Q
+        Kr, Mr = P.sumfact(kappa=kh[q0:q1], G=Gi)
+        assert rel_frob(plan.patch_view(K, i).cpu().numpy(), Kr) <= tol, (i, s)
+        assert rel_frob(plan.patch_view(M, i).cpu().numpy(), Mr) <= tol, (i, s)
+        d0, d1 = plan.dofmap_offset[i], plan.dofmap_offset[i + 1]
+        np.testing.assert_array_equal(D[d0:d1].view(-1, P.N).cpu().numpy(), P.dofmap() + plan.dof_offset[i])
