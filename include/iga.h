@@ -97,10 +97,11 @@ enum { IGA_MASS = 1, IGA_STIFF = 2 };
  *                     branches) and replayed while the pointers are unchanged.
  * The persistent schedules exist for FP32/BF16 sum factorization only.
  * Within them the autotuner chooses, per (degree, Gauss order) class, among
- * the CTA-per-element kernel (one thread per element-matrix entry), its
- * variants where the class has them (stage 3 on warp-level mma.sync instead of
- * tcgen05 at p = 3 and BF16 p = 4; 512 instead of 256 threads per CTA at
- * p = 4, and 256 instead of 512 at p = 5, identity geometry), and a
+ * the CTA-per-element kernel (one thread per element-matrix entry; at p = 4, 5
+ * the streamed tcgen05 form), its variants where the class has them (p = 3:
+ * stage 3 on warp-level mma.sync instead of tcgen05; p = 4, 5: the staged form
+ * with symmetric operand rows, and that form with 512 instead of 256 threads
+ * at FP32 p = 4 and 256 instead of 512 at p = 5, identity geometry), and a
  * warp-per-element kernel (p <= 2, all contractions in FP32), each with work
  * items of 1, 2, 4 or 8 elements, by timing every candidate (median of three
  * launches).  The environment variable IGA_BATCH_SCHED, read by iga_plan,

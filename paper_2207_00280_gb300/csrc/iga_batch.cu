@@ -207,6 +207,10 @@ static cudaError_t launch_sched(const BatchState* B, const BatchClass& c, const 
                                     s, nullptr);
   }
   e = launch_sumfact_f32_queue_alt(a, c.p, c.q, B->bf16, mode, sched, 0, s, &cap);
+  if (e == cudaErrorNotSupported && !B->tuning) {
+    // the variant does not fit this matrix mode: the default form
+    return launch_sched(B, c, a, mode, kSchedCta, s);
+  }
   if (e != cudaSuccess) return e;
   return launch_sumfact_f32_queue_alt(a, c.p, c.q, B->bf16, mode, sched,
                                       std::max(1, std::min(cap, a.n_items)), s, nullptr);
@@ -259,6 +263,8 @@ static std::string tune_key(const BatchState* B, const BatchClass& c, int mode, 
 // and in the file named by IGA_AUTOTUNE_CACHE if set).
 static cudaError_t autotune(BatchState* B, const QueueArgs& base, int mode, cudaStream_t st) {
   const bool gen = base.jac != nullptr;
+  B->tuning = true;
+  struct Reset { BatchState* b; ~Reset() { b->tuning = false; } } reset{B};
   cudaEvent_t t0, t1;
   cudaError_t e = cudaEventCreate(&t0);
   if (e != cudaSuccess) return e;

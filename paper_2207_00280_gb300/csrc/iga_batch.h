@@ -28,6 +28,7 @@ struct BatchPrologue {
 
 struct BatchState {
   bool bf16 = false;
+  bool tuning = false;      // inside the autotuner: a variant that does not fit is skipped
   int schedule = IGA_SCHED_AUTO;
   unsigned long long budget_ns = 0;
   std::vector<BatchClass> classes;

@@ -121,6 +121,13 @@ bool f32_variant_supported(int p, int q, bool bf16, int variant);
 cudaError_t launch_sumfact_f32_queue_alt(const QueueArgs& b, int p, int q, bool bf16, int mode,
                                          int variant, int grid, cudaStream_t st, int* max_grid);
 bool warp_schedule_supported(int p, int q);
+// The streamed tcgen05 form of p = 4, 5 (k_stream32.cu): the default FP32/BF16
+// form there, per patch and in the persistent queue.
+bool stream_form_supported(int p, int q);
+bool stream_both_fit(int p, int q, bool bf16);
+cudaError_t launch_sumfact_f32_stream(const ElemArgs& a, int p, int q, bool bf16, cudaStream_t st);
+cudaError_t launch_sumfact_f32_stream_queue(const QueueArgs& b, int p, int q, bool bf16, int mode,
+                                            int grid, cudaStream_t st, int* max_grid);
 // max_grid reports the number of queue consumers (warps) that fit; grid is a
 // number of warps.
 cudaError_t launch_sumfact_warp_queue(const QueueArgs& b, int p, int q, int mode, int grid,

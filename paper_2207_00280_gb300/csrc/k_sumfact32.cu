@@ -9,13 +9,14 @@ bool sumfact_f32_supported(int dim, int p, int q) {
 }
 
 bool queue_both_fit(int p, int q, bool bf16) {
+  if (stream_form_supported(p, q)) return stream_both_fit(p, q, bf16);
 #define F(PP, QQ)                                                           \
   if (p == PP && q == QQ)                                                   \
     return bf16 ? (SF3F<PP, QQ, true, 0, true>::smem <= 227 * 1024 &&       \
                    SF3F<PP, QQ, false, 0, true>::smem <= 227 * 1024)        \
                 : (SF3F<PP, QQ, true, 0, false>::smem <= 227 * 1024 &&      \
                    SF3F<PP, QQ, false, 0, false>::smem <= 227 * 1024);
-  F(1, 2) F(1, 3) F(2, 3) F(2, 4) F(3, 4) F(3, 5) F(4, 5) F(4, 6) F(5, 6)
+  F(1, 2) F(1, 3) F(2, 3) F(2, 4) F(3, 4) F(3, 5)
 #undef F
   return false;
 }
@@ -24,27 +25,28 @@ cudaError_t launch_sumfact_f32(const ElemArgs& a, int dim, int p, int q, bool bf
                                cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
   if (dim != 3) return cudaErrorInvalidValue;
+  // p = 4, 5: the streamed tcgen05 form
+  if (stream_form_supported(p, q)) return launch_sumfact_f32_stream(a, p, q, bf16, st);
   const int dq = q - p;
 #define C3(PP)                                                                                  \
   if (p == PP && dq == 1) return bf16 ? runm<PP, PP + 1, true>(a, st) : runm<PP, PP + 1, false>(a, st); \
   if (p == PP && dq == 2) return bf16 ? runm<PP, PP + 2, true>(a, st) : runm<PP, PP + 2, false>(a, st);
-  C3(1) C3(2) C3(3) C3(4)
-  if (p == 5 && dq == 1) return bf16 ? runm<5, 6, true>(a, st) : runm<5, 6, false>(a, st);
+  C3(1) C3(2) C3(3)
 #undef C3
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sumfact_f32_queue(const QueueArgs& b, int p, int q, bool bf16, int mode,
                                      int grid, cudaStream_t st, int* max_grid) {
+  if (stream_form_supported(p, q))
+    return launch_sumfact_f32_stream_queue(b, p, q, bf16, mode, grid, st, max_grid);
   const int dq = q - p;
 #define C3(PP)                                                                                \
   if (p == PP && dq == 1) return bf16 ? runq<PP, PP + 1, true>(b, mode, grid, st, max_grid)   \
                                       : runq<PP, PP + 1, false>(b, mode, grid, st, max_grid); \
   if (p == PP && dq == 2) return bf16 ? runq<PP, PP + 2, true>(b, mode, grid, st, max_grid)   \
                                       : runq<PP, PP + 2, false>(b, mode, grid, st, max_grid);
-  C3(1) C3(2) C3(3) C3(4)
-  if (p == 5 && dq == 1) return bf16 ? runq<5, 6, true>(b, mode, grid, st, max_grid)
-                                     : runq<5, 6, false>(b, mode, grid, st, max_grid);
+  C3(1) C3(2) C3(3)
 #undef C3
   return cudaErrorInvalidValue;
 }

@@ -1,10 +1,14 @@
 // k_sumfact32_alt.cu -- the persistent FP32 / BF16 sum-factorization kernels in
 // their non-default variants, timed by the batch autotuner against the default
-// ones (k_sumfact32.cu) and against the warp-per-element form (k_warp32.cu):
-//   MODE_ALT_FORM: stage 3 on warp-level mma.sync instead of tcgen05, for the
-//                  classes whose default is tcgen05 (p = 3; BF16 at p = 4);
-//   MODE_ALT_CTA:  the other CTA size (512 threads at p = 4, 256 at p = 5;
-//                  identity geometry, where 512 threads fit the registers).
+// ones (k_sumfact32.cu, k_stream32.cu) and against the warp-per-element form
+// (k_warp32.cu):
+//   MODE_ALT_FORM: p = 3: stage 3 on warp-level mma.sync instead of tcgen05;
+//                  p = 4, 5: the CTA-per-element form with symmetric operand
+//                  rows and a staged element matrix (mma.sync for FP32 and at
+//                  p = 5, tcgen05 for BF16 at p = 4) instead of the streamed form;
+//   MODE_ALT_CTA:  that staged form with the other CTA size (512 threads at
+//                  p = 4, 256 at p = 5; identity geometry, where 512 threads fit
+//                  the registers).
 // A separate translation unit, so that these instantiations compile in
 // parallel with the default ones.
 #include "k_sumfact32.cuh"
@@ -12,10 +16,13 @@
 namespace iga {
 namespace {
 
-template <int P, int QG, bool BF, int FLAG>
+// FLAG: the MODE flags of the instantiation (MODE_ALT_FORM at p >= 4 selects
+// the staged form, which is that class's flagless instantiation).
+template <int P, int QG, bool BF, int FLAG0>
 cudaError_t runq_alt(const QueueArgs& b, int mode, int grid, cudaStream_t st, int* max_grid) {
+  constexpr int FLAG = (P >= 4 && FLAG0 == MODE_ALT_FORM) ? 0 : FLAG0;
   if (b.jac) {
-    if constexpr (FLAG == MODE_ALT_CTA) {
+    if constexpr (FLAG0 == MODE_ALT_CTA) {
       return cudaErrorInvalidValue;   // general maps keep 256 threads (registers)
     } else {
       if (mode == 0) return run_queue<P, QG, true, 0 | FLAG, BF>(b, grid, st, max_grid);
@@ -31,8 +38,10 @@ cudaError_t runq_alt(const QueueArgs& b, int mode, int grid, cudaStream_t st, in
 }  // namespace
 
 bool f32_variant_supported(int p, int q, bool bf16, int variant) {
-  if (variant == MODE_ALT_FORM) return (p == 3 && (q == 4 || q == 5)) || (bf16 && p == 4 && (q == 5 || q == 6));
-  if (variant == MODE_ALT_CTA) return (p == 4 && (q == 5 || q == 6)) || (p == 5 && q == 6);
+  if (variant == MODE_ALT_FORM)
+    return (p == 3 && (q == 4 || q == 5)) || (p == 4 && (q == 5 || q == 6)) || (p == 5 && q == 6);
+  // BF16 at p = 4 has no 512-thread staged form (its staged form is tcgen05)
+  if (variant == MODE_ALT_CTA) return (!bf16 && p == 4 && (q == 5 || q == 6)) || (p == 5 && q == 6);
   return false;
 }
 
@@ -44,8 +53,12 @@ cudaError_t launch_sumfact_f32_queue_alt(const QueueArgs& b, int p, int q, bool 
                                       : runq_alt<3, 4, false, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
     if (p == 3 && q == 5) return bf16 ? runq_alt<3, 5, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid)
                                       : runq_alt<3, 5, false, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
-    if (p == 4 && q == 5) return runq_alt<4, 5, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
-    return runq_alt<4, 6, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
+    if (p == 4 && q == 5) return bf16 ? runq_alt<4, 5, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid)
+                                      : runq_alt<4, 5, false, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
+    if (p == 4 && q == 6) return bf16 ? runq_alt<4, 6, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid)
+                                      : runq_alt<4, 6, false, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
+    return bf16 ? runq_alt<5, 6, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid)
+                : runq_alt<5, 6, false, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
   }
   if (p == 4 && q == 5) return bf16 ? runq_alt<4, 5, true, MODE_ALT_CTA>(b, mode, grid, st, max_grid)
                                     : runq_alt<4, 5, false, MODE_ALT_CTA>(b, mode, grid, st, max_grid);
