@@ -8,18 +8,29 @@
 // beside the other stages, so the CTA-per-element kernel there kept only the
 // symmetric rows a' <= b' and scattered every result and its mirror into a
 // staged copy of the element matrix before writing it out.  This form instead
-// produces the rows in tiles of 128 (a' major, b' minor), all of them:
-//   tile t:  stage 2 writes the rows of tile t into operand buffer t mod 2;
-//            one thread issues the tile's MMAs into TMEM buffer t mod 2 and
-//            commits them to mbarrier t mod 2;
-//            meanwhile every warp reads tile t-1's accumulators (tcgen05.ld,
-//            one TMEM lane = one row (a', b') per thread) and stores the row's
-//            entries straight to HBM: thread (a', b') writes n contiguous floats
-//            per a1 at column n b', so the 32 consecutive b' of a warp cover a
-//            contiguous stretch of each output row.
+// produces all of the rows, in tiles of whole a' blocks: APT = floor(128 / n^2)
+// values of a' (5 at p = 4, 3 at p = 5) and all n^2 values of b' per 128-row
+// MMA tile.  The entries of such a tile, K[a1 + n a'][b1 + n b'], fill the
+// complete output rows n a'_0 .. n (a'_0 + APT) - 1: one contiguous block of
+// the element matrix.
+// The warps of a CTA split the tile loop (warp specialisation):
+//   producers (warps 4-7): stage 2 writes the rows of tile t into the operand
+//            buffer (once the MMAs of tile t-1 have read it); one thread
+//            issues the tile's MMAs into TMEM buffer t mod 2 (once the
+//            consumers have read that buffer's tile t-2) and commits them to
+//            the MMA mbarrier of the buffer;
+//   consumers (warps 0-3, one per TMEM lane quarter): wait for the MMAs of
+//            tile t, read the accumulators (tcgen05.ld, one TMEM lane = one
+//            row (a', b') per thread), release the TMEM buffer (its "free"
+//            mbarrier), place the entries in a shared-memory copy of the
+//            tile's output block (thread (a', b') writes n floats per a1 at
+//            stride n from its neighbours: no bank conflicts at odd n), and
+//            move the block to HBM with one bulk asynchronous copy; two staging
+//            buffers alternate, so a copy reads one while the next is filled.
+// Producers and consumers meet only at these mbarriers and at the start of
+// an element; every wait is bounded.
 // The symmetric half of stage 2 is computed twice (once per row order), which
-// costs FP32 FMAs but no scattered stores; the element matrix never passes
-// through shared memory.  FP32: 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi);
+// costs FP32 FMAs but no mirrored scatter.  FP32: 3xTF32 (A_hi B_hi + A_hi B_lo + A_lo B_hi);
 // BF16: A (B_hi + B_lo); FP32 accumulation in TMEM.  The Jacobian cofactors
 // and determinant are formed in FP64 (sf3_f32_coef).
 #include "k_sumfact32.cuh"
@@ -32,7 +43,13 @@ struct ST {
   static constexpr bool DK = (MODE & 3) != 2, DM = (MODE & 3) != 1;
   static constexpr int n = P + 1, q = QG, Q = q * q * q, n2 = n * n, N = n2 * n;
   static constexpr int NR = n2 * n2;                  // A rows (a', b'), all orders
-  static constexpr int MT = (NR + 127) / 128;         // 128-row tiles
+  static constexpr int APT = 128 / n2;                // values of a' per tile
+  static constexpr int RT = APT * n2;                 // rows used of a 128-row tile
+  static constexpr int MT = (n2 + APT - 1) / APT;     // tiles
+  // one output block, + alignment slack; a multiple of 4 floats, so that the
+  // second staging buffer starts on a 16-byte boundary like the first (the
+  // bulk copies read both from 16-byte-aligned addresses)
+  static constexpr size_t f_stage = ((size_t)n * APT * N + 8 + 3) / 4 * 4;
   static constexpr int NT = 256;
   static constexpr int REC = 2 * q * n + q;
   static constexpr int RW = 4 * q;                    // x, y pattern records: 4 patterns
@@ -56,7 +73,7 @@ struct ST {
   static constexpr size_t bBK = DK ? (size_t)NU * KA * EB : 0, bBM = DM ? (size_t)NU * KAM * EB : 0;
   static constexpr size_t b_bytes = 2 * (bBK + bBM);                     // B hi + lo
   static constexpr size_t al128(size_t x) { return (x + 127) / 128 * 128; }
-  static constexpr size_t o_A0 = 0, o_A1 = al128(tile_bytes), o_B = 2 * al128(tile_bytes);
+  static constexpr size_t o_A0 = 0, o_B = al128(tile_bytes);
   static constexpr size_t ops_bytes = o_B + al128(b_bytes);
   // floats after the operands
   static constexpr size_t f_px = (size_t)n2 * RW, f_py = (size_t)n2 * RW, f_pz = (size_t)n2 * RZ + 1;
@@ -66,8 +83,9 @@ struct ST {
   static constexpr size_t f_geo = 2 * d_geo + 3 * REC;   // the FP64 staging + FP32 records
   // the staging is dead once the coefficients exist, before stage 1 writes T1
   static constexpr size_t f_T1g = (f_T1 > f_geo ? f_T1 : f_geo) + 2;
-  static constexpr size_t floats = f_px + f_py + f_pz + f_T1g + f_coef + 8;
-  static constexpr size_t smem = ops_bytes + 4 * floats + 64 + 128;   // + mbarriers, slot, align
+  static constexpr size_t floats = f_px + f_py + f_pz + f_T1g + f_coef + 2 * f_stage + 8;
+  static constexpr size_t smem = ops_bytes + 4 * floats + 96 + 128;   // + mbarriers, slot, align
+  static_assert(f_stage % 4 == 0, "staging buffers must stay 16-byte aligned");
   static constexpr int CPB = (DK ? NU : 0) + (DM ? NU : 0);          // TMEM columns per buffer
   static constexpr int TCOLS = 2 * CPB <= 32 ? 32 : 2 * CPB <= 64 ? 64 : 2 * CPB <= 128 ? 128
                                : 2 * CPB <= 256 ? 256 : 512;
@@ -75,17 +93,16 @@ struct ST {
 
 template <class C>
 struct SPtrs {
-  unsigned char* A[2];     // tile buffers: K hi, K lo, M hi, M lo
+  unsigned char* A0;       // the operand tile: K hi, K lo, M hi, M lo
   unsigned char *BKh, *BKl, *BMh, *BMl;
-  float *px, *py, *pz, *T1, *coef, *recf;
+  float *px, *py, *pz, *T1, *coef, *recf, *stage[2];
   double *rec, *kap, *rho, *jac;
-  uint64_t* mbar;          // [2]
+  uint64_t* mbar;          // [4]: MMA done (buffer 0, 1), TMEM free (buffer 0, 1)
   uint32_t* tslot;
   __device__ __forceinline__ explicit SPtrs(unsigned char* sm) {
     uintptr_t o = ((uintptr_t)sm + 127) & ~(uintptr_t)127;
     unsigned char* ops = (unsigned char*)o;
-    A[0] = ops + C::o_A0;
-    A[1] = ops + C::o_A1;
+    A0 = ops + C::o_A0;
     BKh = ops + C::o_B;
     BKl = BKh + C::bBK;
     BMh = BKh + 2 * C::bBK;
@@ -103,16 +120,18 @@ struct SPtrs {
     jac = rho + C::Q;
     recf = (float*)(rec + C::d_geo);
     coef = T1 + C::f_T1g;
-    uintptr_t mb = ((uintptr_t)(coef + C::f_coef) + 15) & ~(uintptr_t)15;
+    stage[0] = (float*)(((uintptr_t)(coef + C::f_coef) + 15) & ~(uintptr_t)15);
+    stage[1] = stage[0] + C::f_stage;
+    uintptr_t mb = ((uintptr_t)(stage[1] + C::f_stage) + 15) & ~(uintptr_t)15;
     mbar = (uint64_t*)mb;
-    tslot = (uint32_t*)(mbar + 2);
+    tslot = (uint32_t*)(mbar + 4);
   }
-  // operand arrays of tile buffer b
-  __device__ __forceinline__ unsigned char* AKh(int b) const { return A[b]; }
-  __device__ __forceinline__ unsigned char* AKl(int b) const { return C::NAU == 2 ? A[b] + C::tAK : nullptr; }
-  __device__ __forceinline__ unsigned char* AMh(int b) const { return A[b] + C::NAU * C::tAK; }
-  __device__ __forceinline__ unsigned char* AMl(int b) const {
-    return C::NAU == 2 ? A[b] + C::NAU * C::tAK + C::tAM : nullptr;
+  // operand arrays of the tile
+  __device__ __forceinline__ unsigned char* AKh() const { return A0; }
+  __device__ __forceinline__ unsigned char* AKl() const { return C::NAU == 2 ? A0 + C::tAK : nullptr; }
+  __device__ __forceinline__ unsigned char* AMh() const { return A0 + C::NAU * C::tAK; }
+  __device__ __forceinline__ unsigned char* AMl() const {
+    return C::NAU == 2 ? A0 + C::NAU * C::tAK + C::tAM : nullptr;
   }
 };
 
@@ -122,15 +141,17 @@ struct SPtrs {
 template <class C>
 __device__ __forceinline__ void st_cta_setup(unsigned char* sm) {
   SPtrs<C> S(sm);
-  uint32_t* ops = (uint32_t*)S.A[0];
+  uint32_t* ops = (uint32_t*)S.A0;
   for (int i = threadIdx.x; i < (int)(C::ops_bytes / 4); i += C::NT) ops[i] = 0u;
   if (threadIdx.x < 32) {
     tmem_alloc(smem_u32(S.tslot), C::TCOLS);
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    mbar_init(smem_u32(S.mbar), 1);
+    mbar_init(smem_u32(S.mbar), 1);          // MMA done: one tcgen05.commit
     mbar_init(smem_u32(S.mbar + 1), 1);
+    mbar_init(smem_u32(S.mbar + 2), 128);    // TMEM free: the 128 consumer threads
+    mbar_init(smem_u32(S.mbar + 3), 128);
     fence_mbar_init();
   }
   fence_before_sync();
@@ -141,6 +162,8 @@ __device__ __forceinline__ void st_cta_setup(unsigned char* sm) {
 template <class C>
 __device__ __forceinline__ void st_cta_teardown(unsigned char* sm) {
   SPtrs<C> S(sm);
+  // the bulk copies of the last output blocks (issued by thread 0) complete
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -175,8 +198,9 @@ __device__ __forceinline__ void st_issue(uint32_t d, const unsigned char* Ah, co
   }
 }
 
-// Stage 2 of tile t: the operand rows m = 128 t + r, (a', b') = (m / n^2,
-// m mod n^2), a' = a2 + n a3, b' = b2 + n b3, written into buffer b.  Columns
+// Stage 2 of tile t (the 128 producer threads, ptid = 0..127): the operand
+// rows r < RT, (a', b') = (APT t + r / n^2, r mod n^2), a' = a2 + n a3,
+// b' = b2 + n b3.  Columns
 // of the stiffness operand X q + k1 in the x-pattern order 11, 00, 10, 01 of
 // the B operand; the mass operand has the 00 pattern only.
 //   C11 = sum_k2 Y00 T0;   C00 = sum_k2 Y11 T1' + Y00 T4 (+ Y10 T6(a3,b3) + Y01 T6(b3,a3));
@@ -185,15 +209,14 @@ __device__ __forceinline__ void st_issue(uint32_t d, const unsigned char* Ah, co
 // with T_t the stage-1 buffers of the terms (z00 D00, z00 D11, z00 D01, z00 DM,
 // z11 D22, z01 D02, z01 D12; T1' = T0 for the identity map, whose D is kappa W I).
 template <class C, bool GEN, bool BF>
-__device__ __forceinline__ void st_stage2(const SPtrs<C>& S, int t, int b) {
+__device__ __forceinline__ void st_stage2(const SPtrs<C>& S, int t, int ptid) {
   constexpr int n = C::n, q = C::q, n2 = C::n2, RW = C::RW, TS = C::TS;
   constexpr int SZ = n2 * TS;
   constexpr int T11 = GEN ? 1 : 0;
-  for (int it = threadIdx.x; it < 128 * q; it += C::NT) {
+  for (int it = ptid; it < C::RT * q; it += 128) {
     const int r = it / q, k1 = it - r * q;
-    const int m = 128 * t + r;
-    if (m >= C::NR) continue;
-    const int ap = m / n2, bp = m - ap * n2;
+    const int ap = C::APT * t + r / n2, bp = r % n2;
+    if (ap >= n2) continue;
     const int a2 = ap % n, a3 = ap / n, b2 = bp % n, b3 = bp / n;
     const float* y = S.py + (a2 * n + b2) * RW;   // 00, 11, 10, 01
     const int oab = (a3 * n + b3) * TS + k1, oba = (b3 * n + a3) * TS + k1;
@@ -220,63 +243,94 @@ __device__ __forceinline__ void st_stage2(const SPtrs<C>& S, int t, int b) {
       if (C::DM) cm = fmaf(y00, S.T1[C::ts(3) * SZ + o], cm);
     }
     if (C::DK) {
-      uput<BF, C::KA>(S.AKh(b), S.AKl(b), r, 0 * q + k1, c11);
-      uput<BF, C::KA>(S.AKh(b), S.AKl(b), r, 1 * q + k1, c00);
+      uput<BF, C::KA>(S.AKh(), S.AKl(), r, 0 * q + k1, c11);
+      uput<BF, C::KA>(S.AKh(), S.AKl(), r, 1 * q + k1, c00);
       if (GEN) {
-        uput<BF, C::KA>(S.AKh(b), S.AKl(b), r, 2 * q + k1, c10);
-        uput<BF, C::KA>(S.AKh(b), S.AKl(b), r, 3 * q + k1, c01);
+        uput<BF, C::KA>(S.AKh(), S.AKl(), r, 2 * q + k1, c10);
+        uput<BF, C::KA>(S.AKh(), S.AKl(), r, 3 * q + k1, c01);
       }
     }
-    if (C::DM) uput<BF, C::KAM>(S.AMh(b), S.AMl(b), r, k1, cm);
+    if (C::DM) uput<BF, C::KAM>(S.AMh(), S.AMl(), r, k1, cm);
   }
 }
 
-// Epilogue of tile t from TMEM buffer b: thread = TMEM lane = row (a', b');
-// its entries K[a1 + n a'][b1 + n b'] go straight to HBM.  With both
-// matrices, warps 0-3 store the stiffness and warps 4-7 the mass; with one,
-// they split the a1 range.
+__device__ __forceinline__ void bar_group(int id) {
+  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+
+// Epilogue of tile t from TMEM buffer b (the 128 consumer threads, ctid =
+// TMEM lane = operand row r; warp w reads lanes 32 w .. 32 w + 31).  All
+// accumulators of the tile are read first and the TMEM buffer released; then,
+// one matrix after the other, the entries K[a1 + n a'][b1 + n b'] go into a
+// staging buffer laid out as the output rows n APT t .. n APT (t + 1) - 1, and
+// consumer thread 0 moves it to HBM with one bulk asynchronous copy (the two
+// buffers alternate: before one is refilled, the copy issued from it two
+// steps earlier must have read it).  `sc` counts the staging steps.
 template <class C>
-__device__ __forceinline__ void st_epilogue(uint32_t tmem, int t, int b, float* gK, float* gM) {
+__device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, int t, int b,
+                                            float* gK, float* gM, int ctid, uint32_t& sc) {
   constexpr int n = C::n, n2 = C::n2, N = C::N, NU = C::NU;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = 128 * t + 32 * (warp & 3) + lane;
-  const bool both = C::DK && C::DM;
-  const int mat = both ? (warp >= 4) : (C::DK ? 0 : 1);
-  constexpr int H = (n + 1) / 2;
-  const int a1lo = both ? 0 : (warp < 4 ? 0 : H), a1hi = both ? n : (warp < 4 ? H : n);
-  const uint32_t col = (uint32_t)(b * C::CPB + ((mat == 1 && C::DK) ? NU : 0));
-  float v[NU];
-  const uint32_t ta = tmem + col + ((uint32_t)(32 * (warp & 3)) << 16);
+  const int warp = ctid >> 5;
+  const int r = ctid;
+  const int ap0 = C::APT * t;
+  const int na = (n2 - ap0) < C::APT ? (n2 - ap0) : C::APT;   // a' values in this tile
+  const int ap = ap0 + r / n2, bp = r % n2;
+  const bool valid = r < C::RT && ap < n2;
+  float vK[C::DK ? NU : 1], vM[C::DM ? NU : 1];
+  const uint32_t ta = tmem + (uint32_t)(b * C::CPB) + ((uint32_t)(32 * warp) << 16);
+  if (C::DK) {
 #pragma unroll
-  for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)c, v + c);
-  if (m >= C::NR) return;
-  const int ap = m / n2, bp = m - ap * n2;
-  float* g = mat == 0 ? gK : gM;
-  float* row = g + (int64_t)(n * ap) * N + n * bp;
-  const bool al8 = (((uintptr_t)row) & 7u) == 0 && (N % 2 == 0);
+    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)c, vK + c);
+  }
+  if (C::DM) {
 #pragma unroll
-  for (int a1 = 0; a1 < n; ++a1) {
-    if (a1 < a1lo || a1 >= a1hi) continue;
-    float* dst = row + (int64_t)a1 * N;
-    if constexpr (n % 2 == 0) {
-      if (al8) {
+    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)((C::DK ? NU : 0) + c), vM + c);
+  }
+  // the TMEM buffer may take the MMAs of tile t + 2
+  fence_before_sync();
+  mbar_arrive(smem_u32(S.mbar + 2 + b));
 #pragma unroll
-        for (int b1 = 0; b1 < n; b1 += 2)
-          *(float2*)(dst + b1) = make_float2(v[a1 * n + b1], v[a1 * n + b1 + 1]);
-        continue;
-      }
+  for (int mat = 0; mat < 2; ++mat) {
+    if ((mat == 0 && !C::DK) || (mat == 1 && !C::DM)) continue;
+    const float* v = mat == 0 ? vK : vM;
+    float* g = (mat == 0 ? gK : gM) + (int64_t)(n * ap0) * N;
+    const int sb = (int)(sc & 1u);
+    ++sc;
+    float* stg = S.stage[sb] + stage_offset(g);
+    if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+    bar_group(2);
+    if (valid) {
+      float* row = stg + (n * (ap - ap0)) * N + n * bp;
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+        for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
     }
-#pragma unroll
-    for (int b1 = 0; b1 < n; ++b1) dst[b1] = v[a1 * n + b1];
+    fence_proxy_async_smem();  // the staged block is read by the bulk copy
+    bar_group(2);
+    // the 16-byte-aligned middle by one bulk copy, the scalar head and tail by
+    // the consumer threads
+    const int nn = n * na * N;
+    const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
+    const int h = head < nn ? head : nn;
+    const int nv = (nn - h) / 4;
+    for (int i = ctid; i < h; i += 128) g[i] = stg[i];
+    for (int i = h + 4 * nv + ctid; i < nn; i += 128) g[i] = stg[i];
+    if (ctid == 0 && nv > 0) {
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+                   ::"l"(g + h), "r"(smem_u32(stg + h)), "r"(nv * 16) : "memory");
+      asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    }
   }
 }
 
-// One element, all stages.  Returns false only if a bounded MMA wait expired
-// (IGA_ERR_TIMEOUT recorded; the caller stops).  `ph` holds the parities of the
-// two MMA-completion mbarriers (bit b for buffer b).
+// One element, all stages.  Returns false only if a bounded wait expired
+// (IGA_ERR_TIMEOUT recorded; the caller stops).  `tc` counts the tiles this
+// CTA has processed (it fixes the buffers and mbarrier parities), `sc` the
+// staging steps of its consumer threads.
 template <int P, int QG, bool GEN, int MODE, bool BF>
 __device__ __forceinline__ bool st_element(const ElemArgs& A, int64_t e, unsigned char* sm,
-                                           uint32_t& ph) {
+                                           uint32_t& tc, uint32_t& sc) {
   using C = ST<P, QG, GEN, MODE, BF>;
   constexpr int n = C::n, q = C::q, Q = C::Q, n2 = C::n2, N = C::N, NT = C::NT, REC = C::REC,
                 RW = C::RW, TS = C::TS;
@@ -373,40 +427,60 @@ __device__ __forceinline__ bool st_element(const ElemArgs& A, int64_t e, unsigne
       }
     }
   }
+  fence_proxy_async_smem();  // every thread's B-operand writes are read by the tensor core
   __syncthreads();
 
-  // stages 2 and 3, tile by tile: operand rows of tile t, its MMAs, then the
-  // store of tile t-1 while they run
+  // stages 2 and 3, tile by tile, producers and consumers in parallel.  The
+  // global tile number g = tc + t picks the TMEM buffer b = g mod 2; use
+  // u = g / 2 of buffer b's mbarriers completes with parity u mod 2.
   const uint32_t tmem = *S.tslot;
   float* gK = C::DK ? (float*)A.K_out + e * (int64_t)N * N : nullptr;
   float* gM = C::DM ? (float*)A.M_out + e * (int64_t)N * N : nullptr;
+  constexpr unsigned long long kWait = 1000000000ull;   // 1 s of global time
+  bool ok = true;
+  const int warp = tid >> 5;
+  if (warp >= 4) {
+    const int ptid = tid - 128;
 #pragma unroll 1
-  for (int t = 0; t <= C::MT; ++t) {
-    const int b = t & 1;
-    if (t < C::MT) st_stage2<C, GEN, BF>(S, t, b);
-    fence_proxy_async_smem();  // the operand rows are read by the tensor core
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (t < C::MT && tid == 0) {
-      const uint32_t d = tmem + (uint32_t)(b * C::CPB);
-      if (C::DK) st_issue<C, C::KA>(d, S.AKh(b), S.AKl(b), S.BKh, S.BKl);
-      if (C::DM) st_issue<C, C::KAM>(d + (C::DK ? C::NU : 0), S.AMh(b), S.AMl(b), S.BMh, S.BMl);
-      umma_commit(smem_u32(S.mbar + b));
-    }
-    if (t >= 1) {
-      const int pb = (t - 1) & 1;
-      const bool done = mbar_wait_bounded(smem_u32(S.mbar + pb), (ph >> pb) & 1u, 1000000000ull);
-      ph ^= 1u << pb;
-      if (!__syncthreads_and(done)) {
-        if (tid == 0) atomicCAS(A.err, 0, (int)IGA_ERR_TIMEOUT);
-        return false;
+    for (int t = 0; t < C::MT; ++t) {
+      const uint32_t g = tc + (uint32_t)t, b = g & 1u;
+      // the operand tile is free once the MMAs of the previous tile have read it
+      if (g >= 1) ok &= mbar_wait_bounded(smem_u32(S.mbar + ((g - 1) & 1u)), ((g - 1) >> 1) & 1u, kWait);
+      st_stage2<C, GEN, BF>(S, t, ptid);
+      fence_proxy_async_smem();  // the operand rows are read by the tensor core
+      bar_group(1);
+      if (ptid == 0) {
+        // TMEM buffer b is free once the consumers have read tile g - 2
+        if (g >= 2) ok &= mbar_wait_bounded(smem_u32(S.mbar + 2 + b), ((g - 2) >> 1) & 1u, kWait);
+        fence_after_sync();
+        const uint32_t d = tmem + b * (uint32_t)C::CPB;
+        if (ok) {
+          if (C::DK) st_issue<C, C::KA>(d, S.AKh(), S.AKl(), S.BKh, S.BKl);
+          if (C::DM) st_issue<C, C::KAM>(d + (C::DK ? C::NU : 0), S.AMh(), S.AMl(), S.BMh, S.BMl);
+          umma_commit(smem_u32(S.mbar + b));
+        }
       }
+    }
+    // the last tile's MMAs have read the operand before the next element
+    // rewrites it (and the B operands)
+    const uint32_t gl = tc + (uint32_t)(C::MT - 1);
+    ok &= mbar_wait_bounded(smem_u32(S.mbar + (gl & 1u)), (gl >> 1) & 1u, kWait);
+  } else {
+#pragma unroll 1
+    for (int t = 0; t < C::MT; ++t) {
+      const uint32_t g = tc + (uint32_t)t, b = g & 1u;
+      ok &= mbar_wait_bounded(smem_u32(S.mbar + b), (g >> 1) & 1u, kWait);
       fence_after_sync();
-      st_epilogue<C>(tmem, t - 1, pb, gK, gM);
+      st_epilogue<C>(S, tmem, t, (int)b, gK, gM, tid, sc);
     }
   }
+  tc += (uint32_t)C::MT;
   fence_before_sync();
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) atomicCAS(A.err, 0, (int)IGA_ERR_TIMEOUT);
+    return false;
+  }
+  fence_after_sync();
   return true;
 }
 
@@ -415,9 +489,9 @@ __global__ void __launch_bounds__(256) k_sf3_stream(const ElemArgs A) {
   extern __shared__ __align__(16) unsigned char sms[];
   using C = ST<P, QG, GEN, MODE, BF>;
   st_cta_setup<C>(sms);
-  uint32_t ph = 0;
+  uint32_t tc = 0, sc = 0;
   for (int64_t e = blockIdx.x; e < A.n_elem; e += gridDim.x)
-    if (!st_element<P, QG, GEN, MODE, BF>(A, e, sms, ph)) break;
+    if (!st_element<P, QG, GEN, MODE, BF>(A, e, sms, tc, sc)) break;
   st_cta_teardown<C>(sms);
 }
 
@@ -430,7 +504,7 @@ __global__ void __launch_bounds__(256) k_sf3_stream_queue(const QueueArgs B) {
   __shared__ int s_item;
   const unsigned long long t0 = global_timer_ns();
   st_cta_setup<C>(sms);
-  uint32_t ph = 0;
+  uint32_t tc = 0, sc = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       int it = -1;
@@ -469,7 +543,7 @@ __global__ void __launch_bounds__(256) k_sf3_stream_queue(const QueueArgs B) {
     A.M_out = B.M_out ? (void*)((float*)B.M_out + pd.mat_offset) : nullptr;
     A.err = B.err;
     bool ok = true;
-    for (int64_t e = w.e0; e < w.e0 + w.count && ok; ++e) ok = st_element<P, QG, GEN, MODE, BF>(A, e, sms, ph);
+    for (int64_t e = w.e0; e < w.e0 + w.count && ok; ++e) ok = st_element<P, QG, GEN, MODE, BF>(A, e, sms, tc, sc);
     if (!ok) break;
   }
   st_cta_teardown<C>(sms);

@@ -25,20 +25,26 @@ cudaError_t launch_sumfact_f32(const ElemArgs& a, int dim, int p, int q, bool bf
                                cudaStream_t st) {
   if (a.n_elem <= 0) return cudaSuccess;
   if (dim != 3) return cudaErrorInvalidValue;
-  // p = 4, 5: the streamed tcgen05 form
-  if (stream_form_supported(p, q)) return launch_sumfact_f32_stream(a, p, q, bf16, st);
+  // p = 5, and p = 4 with the identity map: the streamed tcgen05 form.  With a
+  // general map at p = 4 its doubled stage 2 (all n^4 operand rows, with the
+  // off-diagonal terms) costs more than the staged form's scatter: measured on
+  // GB300, 48^3 curved FP32 8.3 ms streamed against 4.5 ms staged.
+  if (stream_form_supported(p, q) && !(p == 4 && a.jac))
+    return launch_sumfact_f32_stream(a, p, q, bf16, st);
   const int dq = q - p;
 #define C3(PP)                                                                                  \
   if (p == PP && dq == 1) return bf16 ? runm<PP, PP + 1, true>(a, st) : runm<PP, PP + 1, false>(a, st); \
   if (p == PP && dq == 2) return bf16 ? runm<PP, PP + 2, true>(a, st) : runm<PP, PP + 2, false>(a, st);
-  C3(1) C3(2) C3(3)
+  C3(1) C3(2) C3(3) C3(4)
 #undef C3
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sumfact_f32_queue(const QueueArgs& b, int p, int q, bool bf16, int mode,
                                      int grid, cudaStream_t st, int* max_grid) {
-  if (stream_form_supported(p, q))
+  // the same form choice as the per-patch launch (so that the default
+  // persistent schedules reproduce it bit for bit)
+  if (stream_form_supported(p, q) && !(p == 4 && b.jac))
     return launch_sumfact_f32_stream_queue(b, p, q, bf16, mode, grid, st, max_grid);
   const int dq = q - p;
 #define C3(PP)                                                                                \
@@ -46,7 +52,7 @@ cudaError_t launch_sumfact_f32_queue(const QueueArgs& b, int p, int q, bool bf16
                                       : runq<PP, PP + 1, false>(b, mode, grid, st, max_grid); \
   if (p == PP && dq == 2) return bf16 ? runq<PP, PP + 2, true>(b, mode, grid, st, max_grid)   \
                                       : runq<PP, PP + 2, false>(b, mode, grid, st, max_grid);
-  C3(1) C3(2) C3(3)
+  C3(1) C3(2) C3(3) C3(4)
 #undef C3
   return cudaErrorInvalidValue;
 }

@@ -3,9 +3,11 @@
 // ones (k_sumfact32.cu, k_stream32.cu) and against the warp-per-element form
 // (k_warp32.cu):
 //   MODE_ALT_FORM: p = 3: stage 3 on warp-level mma.sync instead of tcgen05;
-//                  p = 4, 5: the CTA-per-element form with symmetric operand
-//                  rows and a staged element matrix (mma.sync for FP32 and at
-//                  p = 5, tcgen05 for BF16 at p = 4) instead of the streamed form;
+//                  p = 4, 5: the other of the two forms there -- the
+//                  CTA-per-element form with symmetric operand rows and a
+//                  staged element matrix (mma.sync for FP32 and at p = 5,
+//                  tcgen05 for BF16 at p = 4), and the streamed form of
+//                  k_stream32.cu (the default except at p = 4 with a general map);
 //   MODE_ALT_CTA:  that staged form with the other CTA size (512 threads at
 //                  p = 4, 256 at p = 5; identity geometry, where 512 threads fit
 //                  the registers).
@@ -48,6 +50,10 @@ bool f32_variant_supported(int p, int q, bool bf16, int variant) {
 cudaError_t launch_sumfact_f32_queue_alt(const QueueArgs& b, int p, int q, bool bf16, int mode,
                                          int variant, int grid, cudaStream_t st, int* max_grid) {
   if (!f32_variant_supported(p, q, bf16, variant)) return cudaErrorInvalidValue;
+  // p = 4 with a general map defaults to the staged form: its other form is the
+  // streamed one
+  if (variant == MODE_ALT_FORM && p == 4 && b.jac)
+    return launch_sumfact_f32_stream_queue(b, p, q, bf16, mode, grid, st, max_grid);
   if (variant == MODE_ALT_FORM) {
     if (p == 3 && q == 4) return bf16 ? runq_alt<3, 4, true, MODE_ALT_FORM>(b, mode, grid, st, max_grid)
                                       : runq_alt<3, 4, false, MODE_ALT_FORM>(b, mode, grid, st, max_grid);
