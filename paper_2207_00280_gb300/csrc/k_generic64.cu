@@ -66,18 +66,28 @@ __device__ __forceinline__ double fw(const double* R, const Shape& S, int k, int
 
 // Basis records of element e into shared memory (a synthetic record for the
 // missing direction of a 2D patch).
+// (Per-direction values are selected, not indexed with a runtime direction,
+// so that the argument records stay out of local memory.)
 __device__ void load_records(double* R, const Shape& S, const double* const* tab, int e1, int e2,
                              int e3) {
+  const double* t0 = tab[0] + (int64_t)e1 * S.rs[0];
+  const double* t1 = tab[1] + (int64_t)e2 * S.rs[1];
+  const double* t2 = tab[2] + (int64_t)e3 * S.rs[2];
   for (int i = threadIdx.x; i < S.rsum; i += blockDim.x) {
     const int k = i < S.roff[1] ? 0 : (i < S.roff[2] ? 1 : 2);
-    const int j = i - S.roff[k];
+    const int j = i - (k == 0 ? 0 : (k == 1 ? S.roff[1] : S.roff[2]));
     if (k < S.dim) {
-      const int ek = k == 0 ? e1 : (k == 1 ? e2 : e3);
-      R[i] = tab[k][(int64_t)ek * S.rs[k] + j];
+      R[i] = (k == 0 ? t0 : (k == 1 ? t1 : t2))[j];
     } else {
       R[i] = j == 1 ? 0.0 : 1.0;   // val = 1, der = 0, w = 1
     }
   }
+}
+
+// c[i] for a runtime i < 7 by selects (c stays in registers).
+__device__ __forceinline__ double pick7(const double* c, int i) {
+  return i == 0 ? c[0] : i == 1 ? c[1] : i == 2 ? c[2] : i == 3 ? c[3] : i == 4 ? c[4]
+       : i == 5 ? c[5] : c[6];
 }
 
 // Coefficients at quadrature point k of element e.  GEN: {D00, D11, D01, DM,
@@ -253,7 +263,7 @@ __global__ void __launch_bounds__(kGenThreads)
           for (int i = 0; i < NI; ++i) {
             const int zp = GEN ? kItemGen[i][0] : kItemId[i][0];
             const int ci = GEN ? kItemGen[i][1] : kItemId[i][1];
-            acc[i] = fma(ZF[zp * q3 + k3], c[ci], acc[i]);
+            acc[i] = fma(ZF[zp * q3 + k3], pick7(c, ci), acc[i]);
           }
         }
 #pragma unroll

@@ -14,7 +14,7 @@
 // complete output rows n a'_0 .. n (a'_0 + APT) - 1: one contiguous block of
 // the element matrix.
 // The warps of a CTA split the tile loop (warp specialisation):
-//   producers (warps 4-7): stage 2 writes the rows of tile t into the operand
+//   producers (warps 4-11): stage 2 writes the rows of tile t into the operand
 //            buffer (once the MMAs of tile t-1 have read it); one thread
 //            issues the tile's MMAs into TMEM buffer t mod 2 (once the
 //            consumers have read that buffer's tile t-2) and commits them to
@@ -50,7 +50,8 @@ struct ST {
   // second staging buffer starts on a 16-byte boundary like the first (the
   // bulk copies read both from 16-byte-aligned addresses)
   static constexpr size_t f_stage = ((size_t)n * APT * N + 8 + 3) / 4 * 4;
-  static constexpr int NT = 256;
+  static constexpr int NT = 384;                      // 4 consumer + 8 producer warps
+  static constexpr int NP = NT - 128;                 // producer threads
   static constexpr int REC = 2 * q * n + q;
   static constexpr int RW = 4 * q;                    // x, y pattern records: 4 patterns
   static constexpr int RZ = (3 * q) % 2 == 0 ? 3 * q + 1 : 3 * q;
@@ -95,7 +96,7 @@ template <class C>
 struct SPtrs {
   unsigned char* A0;       // the operand tile: K hi, K lo, M hi, M lo
   unsigned char *BKh, *BKl, *BMh, *BMl;
-  float *px, *py, *pz, *T1, *coef, *recf, *stage[2];
+  float *px, *py, *pz, *T1, *coef, *recf, *stage0, *stage1;
   double *rec, *kap, *rho, *jac;
   uint64_t* mbar;          // [4]: MMA done (buffer 0, 1), TMEM free (buffer 0, 1)
   uint32_t* tslot;
@@ -120,9 +121,9 @@ struct SPtrs {
     jac = rho + C::Q;
     recf = (float*)(rec + C::d_geo);
     coef = T1 + C::f_T1g;
-    stage[0] = (float*)(((uintptr_t)(coef + C::f_coef) + 15) & ~(uintptr_t)15);
-    stage[1] = stage[0] + C::f_stage;
-    uintptr_t mb = ((uintptr_t)(stage[1] + C::f_stage) + 15) & ~(uintptr_t)15;
+    stage0 = (float*)(((uintptr_t)(coef + C::f_coef) + 15) & ~(uintptr_t)15);
+    stage1 = stage0 + C::f_stage;
+    uintptr_t mb = ((uintptr_t)(stage1 + C::f_stage) + 15) & ~(uintptr_t)15;
     mbar = (uint64_t*)mb;
     tslot = (uint32_t*)(mbar + 4);
   }
@@ -198,7 +199,7 @@ __device__ __forceinline__ void st_issue(uint32_t d, const unsigned char* Ah, co
   }
 }
 
-// Stage 2 of tile t (the 128 producer threads, ptid = 0..127): the operand
+// Stage 2 of tile t (the producer threads, ptid = 0..NP-1): the operand
 // rows r < RT, (a', b') = (APT t + r / n^2, r mod n^2), a' = a2 + n a3,
 // b' = b2 + n b3.  Columns
 // of the stiffness operand X q + k1 in the x-pattern order 11, 00, 10, 01 of
@@ -213,7 +214,7 @@ __device__ __forceinline__ void st_stage2(const SPtrs<C>& S, int t, int ptid) {
   constexpr int n = C::n, q = C::q, n2 = C::n2, RW = C::RW, TS = C::TS;
   constexpr int SZ = n2 * TS;
   constexpr int T11 = GEN ? 1 : 0;
-  for (int it = ptid; it < C::RT * q; it += 128) {
+  for (int it = ptid; it < C::RT * q; it += C::NP) {
     const int r = it / q, k1 = it - r * q;
     const int ap = C::APT * t + r / n2, bp = r % n2;
     if (ap >= n2) continue;
@@ -254,14 +255,15 @@ __device__ __forceinline__ void st_stage2(const SPtrs<C>& S, int t, int ptid) {
   }
 }
 
-__device__ __forceinline__ void bar_group(int id) {
-  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+// Named barrier of a warp group (id 1: the producers, 2: the consumers).
+__device__ __forceinline__ void bar_group(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Epilogue of tile t from TMEM buffer b (the 128 consumer threads, ctid =
-// TMEM lane = operand row r; warp w reads lanes 32 w .. 32 w + 31).  All
-// accumulators of the tile are read first and the TMEM buffer released; then,
-// one matrix after the other, the entries K[a1 + n a'][b1 + n b'] go into a
+// TMEM lane = operand row r; warp w reads lanes 32 w .. 32 w + 31), one matrix
+// after the other (the buffer is released after its last read): the
+// accumulators of the row are read, and the entries K[a1 + n a'][b1 + n b'] go into a
 // staging buffer laid out as the output rows n APT t .. n APT (t + 1) - 1, and
 // consumer thread 0 moves it to HBM with one bulk asynchronous copy (the two
 // buffers alternate: before one is refilled, the copy issued from it two
@@ -276,29 +278,27 @@ __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, in
   const int na = (n2 - ap0) < C::APT ? (n2 - ap0) : C::APT;   // a' values in this tile
   const int ap = ap0 + r / n2, bp = r % n2;
   const bool valid = r < C::RT && ap < n2;
-  float vK[C::DK ? NU : 1], vM[C::DM ? NU : 1];
   const uint32_t ta = tmem + (uint32_t)(b * C::CPB) + ((uint32_t)(32 * warp) << 16);
-  if (C::DK) {
-#pragma unroll
-    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)c, vK + c);
-  }
-  if (C::DM) {
-#pragma unroll
-    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)((C::DK ? NU : 0) + c), vM + c);
-  }
-  // the TMEM buffer may take the MMAs of tile t + 2
-  fence_before_sync();
-  mbar_arrive(smem_u32(S.mbar + 2 + b));
 #pragma unroll
   for (int mat = 0; mat < 2; ++mat) {
     if ((mat == 0 && !C::DK) || (mat == 1 && !C::DM)) continue;
-    const float* v = mat == 0 ? vK : vM;
+    float v[NU];
+    const uint32_t col = (mat == 1 && C::DK) ? (uint32_t)NU : 0u;
+#pragma unroll
+    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + col + (uint32_t)c, v + c);
+    if (mat == 1 || !C::DM) {
+      // the last read of this TMEM buffer: it may take the MMAs of tile t + 2
+      fence_before_sync();
+      mbar_arrive(smem_u32(S.mbar + 2 + b));
+    }
     float* g = (mat == 0 ? gK : gM) + (int64_t)(n * ap0) * N;
     const int sb = (int)(sc & 1u);
     ++sc;
-    float* stg = S.stage[sb] + stage_offset(g);
+    // (a select, not an indexed array: an index into a member array would put
+    // the pointer record in local memory)
+    float* stg = (sb ? S.stage1 : S.stage0) + stage_offset(g);
     if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-    bar_group(2);
+    bar_group(2, 128);
     if (valid) {
       float* row = stg + (n * (ap - ap0)) * N + n * bp;
 #pragma unroll
@@ -307,7 +307,7 @@ __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, in
         for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
     }
     fence_proxy_async_smem();  // the staged block is read by the bulk copy
-    bar_group(2);
+    bar_group(2, 128);
     // the 16-byte-aligned middle by one bulk copy, the scalar head and tail by
     // the consumer threads
     const int nn = n * na * N;
@@ -448,7 +448,7 @@ __device__ __forceinline__ bool st_element(const ElemArgs& A, int64_t e, unsigne
       if (g >= 1) ok &= mbar_wait_bounded(smem_u32(S.mbar + ((g - 1) & 1u)), ((g - 1) >> 1) & 1u, kWait);
       st_stage2<C, GEN, BF>(S, t, ptid);
       fence_proxy_async_smem();  // the operand rows are read by the tensor core
-      bar_group(1);
+      bar_group(1, C::NP);
       if (ptid == 0) {
         // TMEM buffer b is free once the consumers have read tile g - 2
         if (g >= 2) ok &= mbar_wait_bounded(smem_u32(S.mbar + 2 + b), ((g - 2) >> 1) & 1u, kWait);
@@ -485,7 +485,7 @@ __device__ __forceinline__ bool st_element(const ElemArgs& A, int64_t e, unsigne
 }
 
 template <int P, int QG, bool GEN, int MODE, bool BF>
-__global__ void __launch_bounds__(256) k_sf3_stream(const ElemArgs A) {
+__global__ void __launch_bounds__(384, GEN ? 1 : 2) k_sf3_stream(const ElemArgs A) {
   extern __shared__ __align__(16) unsigned char sms[];
   using C = ST<P, QG, GEN, MODE, BF>;
   st_cta_setup<C>(sms);
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256) k_sf3_stream(const ElemArgs A) {
 // Persistent form: CTAs pop work items (patch, first element, count) from the
 // class's device queue; checks and time budget as in k_sumfact32.cuh.
 template <int P, int QG, bool GEN, int MODE, bool BF>
-__global__ void __launch_bounds__(256) k_sf3_stream_queue(const QueueArgs B) {
+__global__ void __launch_bounds__(384, GEN ? 1 : 2) k_sf3_stream_queue(const QueueArgs B) {
   extern __shared__ __align__(16) unsigned char sms[];
   using C = ST<P, QG, GEN, MODE, BF>;
   __shared__ int s_item;

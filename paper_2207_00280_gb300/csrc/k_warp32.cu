@@ -89,11 +89,13 @@ __device__ __forceinline__ void w32_element(const PatchDev& pd, const QueueArgs&
   const int e1 = (int)(e % pd.K[0]);
   const int e2 = (int)((e / pd.K[0]) % pd.K[1]);
   const int e3 = (int)(e / ((int64_t)pd.K[0] * pd.K[1]));
-  // basis records of the three directions (FP64 tables -> FP32)
+  // basis records of the three directions (FP64 tables -> FP32); the offsets
+  // are selected, not indexed, so that the patch record stays in registers
+  const int64_t to0 = pd.tab_offset[0] + (int64_t)e1 * REC, to1 = pd.tab_offset[1] + (int64_t)e2 * REC,
+                to2 = pd.tab_offset[2] + (int64_t)e3 * REC;
   for (int i = lane; i < 3 * REC; i += 32) {
     const int d = i / REC, j = i - d * REC;
-    const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
-    rec[i] = (float)B.tables[pd.tab_offset[d] + (int64_t)ek * REC + j];
+    rec[i] = (float)B.tables[(d == 0 ? to0 : (d == 1 ? to1 : to2)) + j];
   }
   __syncwarp();
   // 1D factor patterns of every direction: pat[d][pt][a][b][k]
