@@ -623,6 +623,7 @@ def measure_forms(args, W, kappa, jac, mass, flush, stream, dev, main_ms):
     if not args.extra_forms:
         return forms
     forms["3d_p4_48_curved"] = measure_curved_p4(stream, flush, dev)
+    forms["3d_p8_8"] = measure_high_degree(stream, flush, dev)
     # 2D p=2 16x16 (256 elements, kappa = 1): launch-latency bound, reported in microseconds
     W2 = wl.WORKLOADS["2d_p2_16"]
     s2 = W2.spec
@@ -746,7 +747,49 @@ def measure_curved_p4(stream, flush, dev):
     return out
 
 
-SCHED_NAMES = {0: "cta", 4: "cta_mma_sync_stage3", 8: "cta_other_size", 16: "warp_per_element"}
+def measure_high_degree(stream, flush, dev):
+    """3D p=8, 8^3 elements, 9^3 Gauss points, lognormal kappa, identity map:
+    mass and stiffness (729 x 729 per element) by sum factorization and by
+    classical integration, FP64, on the runtime-sized kernels.  Each form with
+    its FP64 fraction (algorithmic flops over the element kernel's time) and
+    the speed-up of sum factorization over the classical loop."""
+    import torch
+    from paper_2207_00280_gb300 import workloads as wl
+    from paper_2207_00280_gb300.plan import IgaPlan, Patch
+    W8 = wl.WORKLOADS["3d_p8_8"]
+    sp = W8.spec
+    E = sp.E
+    kappa = torch.as_tensor(W8.kappa(), device=dev)
+    peaks = measured_peaks()[0]
+    fp64_peak = N_SM * DFMA_PER_SM_CLK * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    out = {"elements": E, "degree": sp.p, "gauss_per_dir": sp.q, "matrices": "stiffness+mass",
+           "geometry": "identity"}
+    for meth in ("sumfact", "classical"):
+        pl = IgaPlan(Patch(sp.knots, sp.p, sp.q), method=meth, precision="fp64", blocking=False,
+                     profile=True)
+        K, M, _ = pl.empty_outputs(device=dev, dof=False)
+        pl.integrate(kappa=kappa, K=K, M=M, stream=stream)
+        torch.cuda.synchronize(dev)
+        pl.profile_read()
+        ms = _time_steps(lambda: pl.integrate(kappa=kappa, K=K, M=M, stream=stream),
+                         1 if meth == "classical" else 3, stream, flush)
+        kern_ms, launches = pl.profile_read()
+        kms = kern_ms / max(1, launches)
+        f_el = (flops_per_element(3, sp.p, sp.q, True, True, False) if meth == "sumfact"
+                else classical_flops_per_element(3, sp.p, sp.q, True, True))
+        out[f"{meth}_fp64"] = {"ms_per_step": round(ms, 4), "kernel_ms": round(kms, 4),
+                               "value": round(E / (ms * 1e-3), 1), "flop_per_element": f_el,
+                               "fp64_frac": round(f_el * E / (kms * 1e-3) / fp64_peak, 4),
+                               **FORM_ERR.get(f"{meth}_fp64", {})}
+        del K, M
+        pl.close()
+        torch.cuda.empty_cache()
+    out["speedup_sumfact_vs_classical"] = round(out["classical_fp64"]["ms_per_step"] /
+                                                out["sumfact_fp64"]["ms_per_step"], 2)
+    return out
+
+
+SCHED_NAMES = {0: "cta", 4: "cta_other_stage3_form", 8: "cta_other_size", 16: "warp_per_element"}
 
 
 def autotune_table():

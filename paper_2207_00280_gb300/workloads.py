@@ -28,6 +28,7 @@ SEED_ADJ_KAPPA = 2211     # adjoint workload kappa
 SEED_ADJ_U = 2212
 SEED_ADJ_V = 2213
 SEED_ADJ_FD = 2214        # finite-difference sample points
+SEED_KAPPA_P8 = 2215      # 3D p=8 8^3 kappa (high-degree workload)
 
 
 def open_uniform_knots(K: int, p: int) -> np.ndarray:
@@ -183,4 +184,8 @@ WORKLOADS = {
     "3d_p5_10": Workload("3d_p5_10", PatchSpec(3, 5, 10, 6), SEED_BATCH_KAPPA),
     "3d_p4_16": Workload("3d_p4_16", PatchSpec(3, 4, 16, 5), SEED_BATCH_KAPPA),
     "3d_p4_24_curved": Workload("3d_p4_24_curved", PatchSpec(3, 4, 24, 5), SEED_KAPPA_P4, curved=True),
+    # high degree (the paper's experiments run p up to 9, Sec. 4): 3D p=8,
+    # 8^3 elements, 9^3 Gauss points, lognormal kappa, identity geometry; the
+    # element matrices (729 x 729) are formed by the runtime-sized FP64 kernels
+    "3d_p8_8": Workload("3d_p8_8", PatchSpec(3, 8, 8, 9), SEED_KAPPA_P8),
 }
