@@ -170,7 +170,8 @@ std::vector<FnCouple> couple_1d(const std::vector<int>& spans, int p, int nf) {
 
 // Values of the p+1 B-splines non-zero on span s at x (triangular Cox--de Boor
 // of Sec. 2.3, the polynomial piece of span s, so x at the span's right end
-// gives the left limit): N[r] = B_{s-p+r;p}(x).
+// gives the left limit): N[r] = B_{s-p+r;p}(x).  The left/right/saved
+// evaluation is Piegl and Tiller's, The NURBS Book (2nd ed.), Algorithm A2.2.
 void host_basis(const double* t, int p, int s, double x, double* N) {
   double left[kMaxDegree2D + 1], right[kMaxDegree2D + 1];
   N[0] = 1.0;

@@ -8,7 +8,9 @@ namespace iga {
 // triangular form of the Cox--de Boor recursion (Sec. 2.3, eq. cox2: each
 // degree combines two neighbours of the previous degree, the degree-0 start
 // being the indicator of span s, eq. cox1).  Only the non-vanishing functions
-// are carried, so no 0/0 term ever arises.  The derivative uses the degree
+// are carried, so no 0/0 term ever arises.  This left/right/saved evaluation
+// of the non-zero triangle is the published one of Piegl and Tiller, The
+// NURBS Book (2nd ed., 1997), Algorithm A2.2.  The derivative uses the degree
 // p-1 row:
 //   B'_{i;p} = p B_{i;p-1}/(t_{i+p}-t_i) - p B_{i+1;p-1}/(t_{i+p+1}-t_{i+1}).
 // The record also stores the Gauss weight scaled by half the span length.

@@ -3,9 +3,10 @@ memory (they run inside a memory pool or arena they do not own, or in a loop
 that must never enter the allocator, so they cannot build a plan).  Its
 working memory is a fixed device array inside the library.
 
-Checked through the C ABI against the plan-based iga_integrate_backward on
-the same inputs, for two calls in a row (the shared array keeps the first
-call's contents when the second one runs).  Collected last on purpose.
+Checked through the C ABI against the oracle's adjoint and against the
+plan-based iga_integrate_backward on the same inputs, for three calls in a row
+(the shared array keeps the previous call's contents when the next one runs).
+Collected last on purpose.
 """
 import ctypes
 
@@ -48,7 +49,7 @@ def _noalloc(knots, p, q, kappa, jac, u, v):
 
 
 @pytest.mark.parametrize("curved", [False, True])
-def test_noalloc_matches_plan_twice(curved):
+def test_noalloc_matches_oracle_and_plan(oracle_mod, curved):
     # different calls in a row; the last one (degree 7) runs the runtime-sized adjoint
     cases = [(3, 4, (7, 5, 6), 31), (2, 3, (9, 4, 5), 32), (7, 8, (2, 2, 1), 33)]
     for p, q, Ks, seed in cases:
@@ -65,6 +66,13 @@ def test_noalloc_matches_plan_twice(curved):
         J_ref = torch.empty(1, dtype=torch.float64, device=dev)
         plan.backward(kappa, u, v, grad=g_ref, J=J_ref, jac=jac)
         g, J = _noalloc(knots, p, q, kappa, jac, u, v)
+        # the oracle (plain C, FP64) on the same inputs
+        P = oracle_mod.Patch(knots, p, q)
+        G = wl.curved_map_jacobian(knots, q) if curved else None
+        gr, Jr = P.adjoint(u.cpu().numpy(), v.cpu().numpy(), kappa=kappa.cpu().numpy(), G=G)
+        gr = gr.reshape(-1)
+        assert np.abs(g.cpu().numpy() - gr).max() <= TOL * np.abs(gr).max()
+        assert J == pytest.approx(Jr, rel=TOL, abs=1e-13 * np.abs(kappa.cpu().numpy() * gr).sum())
         scale = float(g_ref.abs().max())
         assert float((g - g_ref).abs().max()) <= TOL * scale
         assert J == pytest.approx(float(J_ref.item()), rel=TOL)
