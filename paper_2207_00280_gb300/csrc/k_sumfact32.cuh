@@ -80,7 +80,12 @@ struct SF3F {
   // when their natural length is even, so that threads indexing consecutive
   // (a3, b3) hit different shared-memory banks
   static constexpr int RZ = (3 * q) % 2 == 0 ? 3 * q + 1 : 3 * q;       // z record stride
-  static constexpr int TS = (q * q) % 2 == 0 ? q * q + 1 : q * q;       // stage-1 row stride
+  // p = 3, q = 4 with identity geometry: stage 2 of the tcgen05 form writes
+  // whole 16-byte operand chunks (all k1 of a row at once, VEC2 below) and
+  // reads the stage-1 rows as float4, so their stride is a multiple of 4
+  // words (20: the stage-1 writes of consecutive b3 still spread over banks)
+  static constexpr bool VEC2 = !GEN && P == 3 && QG == 4;
+  static constexpr int TS = VEC2 ? 20 : ((q * q) % 2 == 0 ? q * q + 1 : q * q);  // stage-1 row stride
   static constexpr size_t f_px = (size_t)n2 * RW, f_py = (size_t)n2 * RW, f_pz = al4((size_t)n2 * RZ);
   // coefficients [7][Q]: 0 D00, 1 D11, 2 D01, 3 DM, 4 D22, 5 D02, 6 D12 (identity: 0 = W kappa, 3 = W rho)
   // stage-1 terms and coefficients held: all seven with a general Jacobian;
@@ -168,19 +173,39 @@ __device__ __forceinline__ int uoff(int r, int k) {
 }
 
 // Physical operand row of (a', b') in the tcgen05 form.  For n^2 = 16 the
-// low three bits of the row are rotated by a' within each 16-row block, so
-// that the threads of a warp writing rows (a', b') for consecutive a' -- and
-// the mirrored rows (b', a') -- land on different shared-memory banks.  A
-// permutation of A's rows only permutes the TMEM rows of the product; the
-// epilogue inverts it (urow_inv).
-template <int n2>
+// rows of one a' form one block of 16 (which keeps the epilogue's global
+// stores coalesced), permuted within the block so that stage 2's writes
+// spread over the shared-memory banks.  A permutation of A's rows only
+// permutes the TMEM rows of the product; the epilogue inverts it (urow_inv).
+//   V = false (stage 2 writes one value per thread and row): the low three
+//     bits of the row are rotated by a', so that the threads of a warp writing
+//     rows (a', b') for consecutive a' -- and the mirrored rows (b', a') --
+//     land on different banks;
+//   V = true (p = 3, q = 4, identity map: stage 2 writes whole 16-byte
+//     chunks, eight consecutive threads = four b2 by two a2 of one (a3, b3)
+//     pair): with b' = y2 + 4 y3 (y2 = b' mod 4) the row within the block is
+//       8 (y3 >> 1) + 4 ((y3 + a') mod 2) + ((y2 + a') mod 4),
+//     which puts the chunks of those eight threads in eight different 16-byte
+//     bank groups, for the rows (a', b') and for their mirrors (b', a').
+template <int n2, bool V>
 __device__ __forceinline__ int urow(int x, int y) {
-  if constexpr (n2 == 16) return 16 * x + ((y & 8) | ((x + y) & 7));
-  else return x * n2 + y;
+  if constexpr (n2 == 16 && V) {
+    const int y3 = y >> 2;
+    return 16 * x + 8 * (y3 >> 1) + 4 * ((y3 + x) & 1) + ((y + x) & 3);
+  } else if constexpr (n2 == 16) {
+    return 16 * x + ((y & 8) | ((x + y) & 7));
+  } else {
+    return x * n2 + y;
+  }
 }
-template <int n2>
+template <int n2, bool V>
 __device__ __forceinline__ void urow_inv(int r, int& x, int& y) {
-  if constexpr (n2 == 16) {
+  if constexpr (n2 == 16 && V) {
+    x = r >> 4;
+    const int lo = r & 15;
+    const int y3 = 2 * (lo >> 3) + (((lo >> 2) - x) & 1);
+    y = 4 * y3 + ((lo - x) & 3);
+  } else if constexpr (n2 == 16) {
     x = r >> 4;
     const int lo = r & 15;
     y = (lo & 8) | ((lo - x) & 7);
@@ -809,90 +834,165 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
   {
     constexpr int S = n2 * C::TS;
     constexpr int T11 = GEN ? 1 : 0;
-    // (a) C11, C00, CM: item = (a3 <= b3, k1, a2)
-    for (int it = tid; it < NS1 * q * n; it += NT) {
-      const int a2 = it % n, r = it / n, k1 = r % q, ps = r / q;
-      int a3 = 0, rr = ps;
-      while (rr >= n - a3) { rr -= n - a3; ++a3; }
-      const int b3 = a3 + rr;
-      // T layout [t][a3][b3][k1 + q k2]
-      const int ab3 = (a3 * n + b3) * C::TS + k1, ba3 = (b3 * n + a3) * C::TS + k1;
-      float t00[q], t11[q], t22[q], tab[q], tba[q], tm[q];
-#pragma unroll
-      for (int k2 = 0; k2 < q; ++k2) {
-        if (DK) {
-          t00[k2] = T1[C::ts(0) * S + ab3 + q * k2];
-          t11[k2] = T1[C::ts(T11) * S + ab3 + q * k2];
-          t22[k2] = T1[C::ts(4) * S + ab3 + q * k2];
-          if (GEN) { tab[k2] = T1[C::ts(6) * S + ab3 + q * k2]; tba[k2] = T1[C::ts(6) * S + ba3 + q * k2]; }
-        }
-        if (DM) tm[k2] = T1[C::ts(3) * S + ab3 + q * k2];
-      }
-      const int ap = a2 + n * a3;
-      const int b2s = (a3 == b3 ? a2 : 0);
-      const int pp0 = upper_index<Np>(ap, b2s + n * b3) - b2s;  // rows are consecutive in b2
-#pragma unroll
-      for (int b2 = 0; b2 < n; ++b2) {
-        if (b2 < b2s) continue;
-        const int pp = pp0 + b2;
+    if constexpr (UM && C::FULLR && C::VEC2) {
+      // p = 3, q = 4, identity geometry: item = (a3 <= b3, a2, b2), all four
+      // k1 at once, so that each operand row receives whole 16-byte chunks:
+      // FP32 A[m][X q + k1], k1 = 0..3, is one chunk per pattern X (hi and
+      // lo), BF16 holds both patterns of K in one chunk and the mass in half
+      // of one.  Threads: b2 fastest, then a2, then the (a3, b3) pair.
+      static_assert(n == 4 && q == 4 && !GEN, "VEC2 is the p = 3, q = 4 identity form");
+      const float4* T4 = (const float4*)T1;
+      constexpr int S4 = S / 4, TS4 = C::TS / 4;
+      for (int it = tid; it < NS1 * n2; it += NT) {
+        const int b2 = it & 3, a2 = (it >> 2) & 3, ps = it >> 4;
+        int a3 = 0, rr = ps;
+        while (rr >= n - a3) { rr -= n - a3; ++a3; }
+        const int b3 = a3 + rr;
         const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);  // 00, 11, 10, 01
-        float y[RW];
+        const float4 y00 = y4[0], y11 = y4[1];
+        const float ya[4] = {y00.x, y00.y, y00.z, y00.w}, yb[4] = {y11.x, y11.y, y11.z, y11.w};
+        const int ab3 = (a3 * n + b3) * TS4;
+        float4 c11 = make_float4(0.f, 0.f, 0.f, 0.f), c00 = c11, cm = c11;
 #pragma unroll
-        for (int v = 0; v < RW / 4; ++v) {
-          const float4 w4 = y4[v];
-          y[4 * v] = w4.x; y[4 * v + 1] = w4.y; y[4 * v + 2] = w4.z; y[4 * v + 3] = w4.w;
+        for (int k2 = 0; k2 < 4; ++k2) {
+          if (DK) {
+            const float4 t0 = T4[C::ts(0) * S4 + ab3 + k2], t4 = T4[C::ts(4) * S4 + ab3 + k2];
+            c11.x = fmaf(ya[k2], t0.x, c11.x); c11.y = fmaf(ya[k2], t0.y, c11.y);
+            c11.z = fmaf(ya[k2], t0.z, c11.z); c11.w = fmaf(ya[k2], t0.w, c11.w);
+            c00.x = fmaf(yb[k2], t0.x, fmaf(ya[k2], t4.x, c00.x));
+            c00.y = fmaf(yb[k2], t0.y, fmaf(ya[k2], t4.y, c00.y));
+            c00.z = fmaf(yb[k2], t0.z, fmaf(ya[k2], t4.z, c00.z));
+            c00.w = fmaf(yb[k2], t0.w, fmaf(ya[k2], t4.w, c00.w));
+          }
+          if (DM) {
+            const float4 t3 = T4[C::ts(3) * S4 + ab3 + k2];
+            cm.x = fmaf(ya[k2], t3.x, cm.x); cm.y = fmaf(ya[k2], t3.y, cm.y);
+            cm.z = fmaf(ya[k2], t3.z, cm.z); cm.w = fmaf(ya[k2], t3.w, cm.w);
+          }
         }
-        float c11 = 0.f, c00a = 0.f, c00b = 0.f, cm = 0.f;
+        const int ap = a2 + n * a3, bp = b2 + n * b3;
+        const int m1 = urow<n2, C::VEC2>(ap, bp), m2 = urow<n2, C::VEC2>(bp, ap);
 #pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          if (side == 1 && m2 == m1) break;
+          const int m = side == 0 ? m1 : m2;
+          // K-major core matrices: 8-row groups (8 rows x 16 bytes per K chunk)
+          const int base = (m >> 3) * (8 * 8 * C::EB * (C::KA / 8)) + (m & 7) * 16;
+          if constexpr (BF) {
+            if (DK) {
+              uint4 w;
+              w.x = pack_bf16x2(c11.x, c11.y); w.y = pack_bf16x2(c11.z, c11.w);
+              w.z = pack_bf16x2(c00.x, c00.y); w.w = pack_bf16x2(c00.z, c00.w);
+              *(uint4*)(U.AKh + base) = w;
+            }
+            if (DM) {
+              const int bm = (m >> 3) * (8 * 8 * C::EB * (C::KAM / 8)) + (m & 7) * 16;
+              *(uint2*)(U.AMh + bm) = make_uint2(pack_bf16x2(cm.x, cm.y), pack_bf16x2(cm.z, cm.w));
+            }
+          } else {
+            if (DK) {
+              *(float4*)(U.AKh + base) = c11;
+              *(float4*)(U.AKh + base + 128) = c00;
+              *(float4*)(U.AKl + base) = make_float4(c11.x - tf32_trunc(c11.x), c11.y - tf32_trunc(c11.y),
+                                                     c11.z - tf32_trunc(c11.z), c11.w - tf32_trunc(c11.w));
+              *(float4*)(U.AKl + base + 128) = make_float4(c00.x - tf32_trunc(c00.x), c00.y - tf32_trunc(c00.y),
+                                                           c00.z - tf32_trunc(c00.z), c00.w - tf32_trunc(c00.w));
+            }
+            if (DM) {
+              const int bm = (m >> 3) * (8 * 8 * C::EB * (C::KAM / 8)) + (m & 7) * 16;
+              *(float4*)(U.AMh + bm) = cm;
+              *(float4*)(U.AMl + bm) = make_float4(cm.x - tf32_trunc(cm.x), cm.y - tf32_trunc(cm.y),
+                                                   cm.z - tf32_trunc(cm.z), cm.w - tf32_trunc(cm.w));
+            }
+          }
+        }
+      }
+    } else {
+      // (a) C11, C00, CM: item = (a3 <= b3, k1, a2)
+      for (int it = tid; it < NS1 * q * n; it += NT) {
+        const int a2 = it % n, r = it / n, k1 = r % q, ps = r / q;
+        int a3 = 0, rr = ps;
+        while (rr >= n - a3) { rr -= n - a3; ++a3; }
+        const int b3 = a3 + rr;
+        // T layout [t][a3][b3][k1 + q k2]
+        const int ab3 = (a3 * n + b3) * C::TS + k1, ba3 = (b3 * n + a3) * C::TS + k1;
+        float t00[q], t11[q], t22[q], tab[q], tba[q], tm[q];
+  #pragma unroll
         for (int k2 = 0; k2 < q; ++k2) {
           if (DK) {
-            c11 = fmaf(y[k2], t00[k2], c11);
-            c00a = fmaf(y[q + k2], t11[k2], c00a);
-            c00b = fmaf(y[k2], t22[k2], c00b);
-            if (GEN) {
-              c00a = fmaf(y[2 * q + k2], tab[k2], c00a);
-              c00b = fmaf(y[3 * q + k2], tba[k2], c00b);
-            }
+            t00[k2] = T1[C::ts(0) * S + ab3 + q * k2];
+            t11[k2] = T1[C::ts(T11) * S + ab3 + q * k2];
+            t22[k2] = T1[C::ts(4) * S + ab3 + q * k2];
+            if (GEN) { tab[k2] = T1[C::ts(6) * S + ab3 + q * k2]; tba[k2] = T1[C::ts(6) * S + ba3 + q * k2]; }
           }
-          if (DM) cm = fmaf(y[k2], tm[k2], cm);
+          if (DM) tm[k2] = T1[C::ts(3) * S + ab3 + q * k2];
         }
-        if constexpr (UM && !C::FULLR) {
-          // rows a' <= b' only; the K columns past the data are rewritten with
-          // zeros (the staged matrix of the previous element covered them)
-          if (DK) {
-            uput<BF, C::KA>(U.AKh, U.AKl, pp, 0 * q + k1, c11);
-            uput<BF, C::KA>(U.AKh, U.AKl, pp, 1 * q + k1, c00a + c00b);
-            if (k1 == 0)
-              for (int kz = C::NXK * q; kz < C::KA; ++kz) uput<BF, C::KA>(U.AKh, U.AKl, pp, kz, 0.f);
+        const int ap = a2 + n * a3;
+        const int b2s = (a3 == b3 ? a2 : 0);
+        const int pp0 = upper_index<Np>(ap, b2s + n * b3) - b2s;  // rows are consecutive in b2
+  #pragma unroll
+        for (int b2 = 0; b2 < n; ++b2) {
+          if (b2 < b2s) continue;
+          const int pp = pp0 + b2;
+          const float4* y4 = (const float4*)(Py + (a2 * n + b2) * RW);  // 00, 11, 10, 01
+          float y[RW];
+  #pragma unroll
+          for (int v = 0; v < RW / 4; ++v) {
+            const float4 w4 = y4[v];
+            y[4 * v] = w4.x; y[4 * v + 1] = w4.y; y[4 * v + 2] = w4.z; y[4 * v + 3] = w4.w;
           }
-          if (DM) {
-            uput<BF, C::KAM>(U.AMh, U.AMl, pp, k1, cm);
-            if (k1 == 0)
-              for (int kz = q; kz < C::KAM; ++kz) uput<BF, C::KAM>(U.AMh, U.AMl, pp, kz, 0.f);
-          }
-        } else if constexpr (UM) {
-          // rows (a', b') and (b', a'): the patterns 11, 00 and the mass are
-          // symmetric under the exchange
-          const int bp = b2 + n * b3;
-          const int m1 = urow<n2>(ap, bp), m2 = urow<n2>(bp, ap);
-          if (DK) {
-            uput<BF, C::KA>(U.AKh, U.AKl, m1, 0 * q + k1, c11);
-            uput<BF, C::KA>(U.AKh, U.AKl, m1, 1 * q + k1, c00a + c00b);
-            if (m2 != m1) {
-              uput<BF, C::KA>(U.AKh, U.AKl, m2, 0 * q + k1, c11);
-              uput<BF, C::KA>(U.AKh, U.AKl, m2, 1 * q + k1, c00a + c00b);
+          float c11 = 0.f, c00a = 0.f, c00b = 0.f, cm = 0.f;
+  #pragma unroll
+          for (int k2 = 0; k2 < q; ++k2) {
+            if (DK) {
+              c11 = fmaf(y[k2], t00[k2], c11);
+              c00a = fmaf(y[q + k2], t11[k2], c00a);
+              c00b = fmaf(y[k2], t22[k2], c00b);
+              if (GEN) {
+                c00a = fmaf(y[2 * q + k2], tab[k2], c00a);
+                c00b = fmaf(y[3 * q + k2], tba[k2], c00b);
+              }
             }
+            if (DM) cm = fmaf(y[k2], tm[k2], cm);
           }
-          if (DM) {
-            uput<BF, C::KAM>(U.AMh, U.AMl, m1, k1, cm);
-            if (m2 != m1) uput<BF, C::KAM>(U.AMh, U.AMl, m2, k1, cm);
+          if constexpr (UM && !C::FULLR) {
+            // rows a' <= b' only; the K columns past the data are rewritten with
+            // zeros (the staged matrix of the previous element covered them)
+            if (DK) {
+              uput<BF, C::KA>(U.AKh, U.AKl, pp, 0 * q + k1, c11);
+              uput<BF, C::KA>(U.AKh, U.AKl, pp, 1 * q + k1, c00a + c00b);
+              if (k1 == 0)
+                for (int kz = C::NXK * q; kz < C::KA; ++kz) uput<BF, C::KA>(U.AKh, U.AKl, pp, kz, 0.f);
+            }
+            if (DM) {
+              uput<BF, C::KAM>(U.AMh, U.AMl, pp, k1, cm);
+              if (k1 == 0)
+                for (int kz = q; kz < C::KAM; ++kz) uput<BF, C::KAM>(U.AMh, U.AMl, pp, kz, 0.f);
+            }
+          } else if constexpr (UM) {
+            // rows (a', b') and (b', a'): the patterns 11, 00 and the mass are
+            // symmetric under the exchange
+            const int bp = b2 + n * b3;
+            const int m1 = urow<n2, C::VEC2>(ap, bp), m2 = urow<n2, C::VEC2>(bp, ap);
+            if (DK) {
+              uput<BF, C::KA>(U.AKh, U.AKl, m1, 0 * q + k1, c11);
+              uput<BF, C::KA>(U.AKh, U.AKl, m1, 1 * q + k1, c00a + c00b);
+              if (m2 != m1) {
+                uput<BF, C::KA>(U.AKh, U.AKl, m2, 0 * q + k1, c11);
+                uput<BF, C::KA>(U.AKh, U.AKl, m2, 1 * q + k1, c00a + c00b);
+              }
+            }
+            if (DM) {
+              uput<BF, C::KAM>(U.AMh, U.AMl, m1, k1, cm);
+              if (m2 != m1) uput<BF, C::KAM>(U.AMh, U.AMl, m2, k1, cm);
+            }
+          } else {
+            if (DK) {
+              AK[pp * C::LDA + 0 * q + k1] = c11;
+              AK[pp * C::LDA + 1 * q + k1] = c00a + c00b;
+            }
+            if (DM) AM[pp * C::LDAM + k1] = cm;
           }
-        } else {
-          if (DK) {
-            AK[pp * C::LDA + 0 * q + k1] = c11;
-            AK[pp * C::LDA + 1 * q + k1] = c00a + c00b;
-          }
-          if (DM) AM[pp * C::LDAM + k1] = cm;
         }
       }
     }
@@ -932,8 +1032,8 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
             if (bp <= ap) uput<BF, C::KA>(U.AKh, U.AKl, upper_index<Np>(bp, ap), 3 * q + k1, val);
           } else if constexpr (UM) {
             // C10 of row (a', b') is C01 of row (b', a')
-            uput<BF, C::KA>(U.AKh, U.AKl, urow<n2>(ap, bp), 2 * q + k1, val);
-            uput<BF, C::KA>(U.AKh, U.AKl, urow<n2>(bp, ap), 3 * q + k1, val);
+            uput<BF, C::KA>(U.AKh, U.AKl, urow<n2, C::VEC2>(ap, bp), 2 * q + k1, val);
+            uput<BF, C::KA>(U.AKh, U.AKl, urow<n2, C::VEC2>(bp, ap), 3 * q + k1, val);
           } else {
             if (ap <= bp) AK[upper_index<Np>(ap, bp) * C::LDA + 2 * q + k1] = val;
             if (bp <= ap) AK[upper_index<Np>(bp, ap) * C::LDA + 3 * q + k1] = val;
@@ -978,7 +1078,7 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
           const int m = t * 128 + 32 * (warp & 3) + lane;
           if (m < n2 * n2) {
             int ap, bp;
-            urow_inv<n2>(m, ap, bp);
+            urow_inv<n2, C::VEC2>(m, ap, bp);
             sf3_store_row_um<n, N>(g, ap, bp, v);
           }
         }
