@@ -128,6 +128,13 @@ bool stream_both_fit(int p, int q, bool bf16);
 cudaError_t launch_sumfact_f32_stream(const ElemArgs& a, int p, int q, bool bf16, cudaStream_t st);
 cudaError_t launch_sumfact_f32_stream_queue(const QueueArgs& b, int p, int q, bool bf16, int mode,
                                             int grid, cudaStream_t st, int* max_grid);
+// Stiffness of 3D patches with a general map at p = 4, q = 5 in FP32 / BF16
+// (k_curved32.cu): the default form of that class, per patch and in the
+// persistent queue (stiffness-only launches).
+bool curved_form_supported(int p, int q);
+cudaError_t launch_sumfact_f32_curved(const ElemArgs& a, bool bf16, cudaStream_t st);
+cudaError_t launch_sumfact_f32_curved_queue(const QueueArgs& b, bool bf16, int grid, cudaStream_t st,
+                                            int* max_grid);
 // max_grid reports the number of queue consumers (warps) that fit; grid is a
 // number of warps.
 cudaError_t launch_sumfact_warp_queue(const QueueArgs& b, int p, int q, int mode, int grid,

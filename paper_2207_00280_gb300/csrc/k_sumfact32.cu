@@ -31,6 +31,9 @@ cudaError_t launch_sumfact_f32(const ElemArgs& a, int dim, int p, int q, bool bf
   // GB300, 48^3 curved FP32 8.3 ms streamed against 4.5 ms staged.
   if (stream_form_supported(p, q) && !(p == 4 && a.jac))
     return launch_sumfact_f32_stream(a, p, q, bf16, st);
+  // the stiffness alone with a general map at p = 4, q = 5: k_curved32.cu
+  if (curved_form_supported(p, q) && a.jac && a.K_out && !a.M_out)
+    return launch_sumfact_f32_curved(a, bf16, st);
   const int dq = q - p;
 #define C3(PP)                                                                                  \
   if (p == PP && dq == 1) return bf16 ? runm<PP, PP + 1, true>(a, st) : runm<PP, PP + 1, false>(a, st); \
@@ -46,6 +49,8 @@ cudaError_t launch_sumfact_f32_queue(const QueueArgs& b, int p, int q, bool bf16
   // persistent schedules reproduce it bit for bit)
   if (stream_form_supported(p, q) && !(p == 4 && b.jac))
     return launch_sumfact_f32_stream_queue(b, p, q, bf16, mode, grid, st, max_grid);
+  if (curved_form_supported(p, q) && b.jac && mode == 1)
+    return launch_sumfact_f32_curved_queue(b, bf16, grid, st, max_grid);
   const int dq = q - p;
 #define C3(PP)                                                                                \
   if (p == PP && dq == 1) return bf16 ? runq<PP, PP + 1, true>(b, mode, grid, st, max_grid)   \

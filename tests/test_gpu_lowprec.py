@@ -60,6 +60,21 @@ def test_single_matrix_modes(oracle_mod, prec, which):
          stiffness=which == "stiffness")
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_curved_p4_stiffness_only_every_element(oracle_mod, prec):
+    """The stiffness alone with a general map at p = 4, q = 5 has a kernel of
+    its own (symmetric operand rows, staged mirror, bulk-copy output, the next
+    element's inputs prefetched): every element of a 7 x 7 x 8 mesh against
+    the oracle -- more elements than resident CTAs, so CTAs take several
+    elements and element matrices start at every 4-byte offset mod 16."""
+    p, q = 4, 5
+    knots = [wl.open_uniform_knots(K, p) for K in (7, 7, 8)]
+    P = oracle_mod.Patch(knots, p, q)
+    kappa = wl.lognormal(P.E * P.Q, 812)
+    G = wl.curved_map_jacobian(knots, q)
+    _cmp(oracle_mod, knots, p, q, kappa, None, G, prec, mass=False)
+
+
 _ORACLE_48 = {}
 
 
