@@ -73,6 +73,39 @@ struct ElemArgs {
   int* err;
 };
 
+#ifdef __CUDACC__
+// Coordinates (e1, e2, e3) of element e = e1 + K1 (e2 + K2 e3).  Element
+// indices below 2^31 (every patch in practice) take two 32-bit unsigned
+// divisions; a 64-bit division by a runtime divisor is a long instruction
+// sequence that each thread would otherwise run once per element.
+template <class Args>   // any launch-argument record with K1, K2
+__device__ __forceinline__ void elem_coords(const Args& A, int64_t e, int& e1, int& e2, int& e3) {
+  if (e < 0x7fffffffLL) {
+    const unsigned u = (unsigned)e, k1 = (unsigned)A.K1, k2 = (unsigned)A.K2;
+    const unsigned r1 = u / k1, r2 = r1 / k2;
+    e1 = (int)(u - r1 * k1);
+    e2 = (int)(r1 - r2 * k2);
+    e3 = (int)r2;
+  } else {
+    e1 = (int)(e % A.K1);
+    e2 = (int)((e / A.K1) % A.K2);
+    e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  }
+}
+// 2D: element e = e1 + K1 e2.
+template <class Args>
+__device__ __forceinline__ void elem_coords2(const Args& A, int64_t e, int& e1, int& e2) {
+  if (e < 0x7fffffffLL) {
+    const unsigned u = (unsigned)e, k1 = (unsigned)A.K1, r1 = u / k1;
+    e1 = (int)(u - r1 * k1);
+    e2 = (int)r1;
+  } else {
+    e1 = (int)(e % A.K1);
+    e2 = (int)(e / A.K1);
+  }
+}
+#endif
+
 // FP64 sum factorization (Algorithm 2 generalised to the stiffness terms).
 cudaError_t launch_sumfact_f64(const ElemArgs& a, int dim, int p, int q, cudaStream_t st);
 // FP64 classical integration (Algorithm 1).

@@ -42,9 +42,8 @@ __global__ void __launch_bounds__(128) k_apply3(const ApplyArgs A) {
   __shared__ T S[2][n2 * q];             // [a2 + n a3][q1]: pairs with d_x, with v_x
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   for (int i = tid; i < 3 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
@@ -209,7 +208,8 @@ __global__ void __launch_bounds__(64) k_apply2(const ApplyArgs A) {
   __shared__ T S[2][n * q];              // [a2][q1]: pairs with d_x, with v_x
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1), e2 = (int)(e / A.K1);
+  int e1, e2;
+  elem_coords2(A, e, e1, e2);
   for (int i = tid; i < 2 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     rec[i] = (d == 0 ? A.tab[0] + (int64_t)e1 * REC : A.tab[1] + (int64_t)e2 * REC)[j];

@@ -44,9 +44,8 @@ __global__ void __launch_bounds__(256) k_classical_f64(const ElemArgs A) {
   double* geo = wg + DIM * N * QT;        // [11][QT]: Wk, Wr, Ginv (row-major)
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   for (int i = tid; i < DIM * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);

@@ -140,11 +140,8 @@ __device__ __forceinline__ void cv_issue_inputs(const ElemArgs& A, int64_t e, do
                                                 double* jac, int t, int nt) {
   using C = CV<BF>;
   constexpr int REC = C::REC, Q = C::Q;
-  // element index -> (e1, e2, e3); one 64-bit division, the rest in 32 bits
-  const int64_t pl = (int64_t)A.K1 * A.K2;
-  const int e3 = (int)(e / pl);
-  const unsigned r = (unsigned)(e - (int64_t)e3 * pl);
-  const int e2 = (int)(r / (unsigned)A.K1), e1 = (int)(r - (unsigned)e2 * (unsigned)A.K1);
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   for (int i = t; i < 3 * REC; i += nt) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
@@ -778,13 +775,7 @@ struct CvSrc {
 // (e1, e2, e3) of element e, and the step to element e + s (s >= 0).
 struct CvCoord {
   int e1, e2, e3;
-  __device__ __forceinline__ CvCoord(const ElemArgs& A, int64_t e) {
-    const int64_t pl = (int64_t)A.K1 * A.K2;
-    e3 = (int)(e / pl);
-    const unsigned r = (unsigned)(e - (int64_t)e3 * pl);
-    e2 = (int)(r / (unsigned)A.K1);
-    e1 = (int)(r - (unsigned)e2 * (unsigned)A.K1);
-  }
+  __device__ __forceinline__ CvCoord(const ElemArgs& A, int64_t e) { elem_coords(A, e, e1, e2, e3); }
   __device__ __forceinline__ void step(const ElemArgs& A, int s1, int s2, int s3) {
     // s = s1 + K1 (s2 + K2 s3) with s1 < K1, s2 < K2: add with carries
     e1 += s1;

@@ -211,9 +211,8 @@ __global__ void __launch_bounds__(kGenThreads)
   const int n1 = S.n[0], n2 = S.n[1], n3 = S.n[2], q1 = S.q[0], q2 = S.q[1], q3 = S.q[2];
   const int N = S.N, Q = S.Q;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   const bool wantK = A.K_out != nullptr, wantM = A.M_out != nullptr;
   double* Ke = wantK ? (double*)A.K_out + e * (int64_t)N * N : nullptr;
   double* Me = wantM ? (double*)A.M_out + e * (int64_t)N * N : nullptr;
@@ -341,9 +340,8 @@ __global__ void __launch_bounds__(kGenThreads)
   double* wg = wphi + N * QT;             // [3][N][QT]  W |det| kappa g
   double* geo = wg + 3 * N * QT;          // [11][QT]    W|det|kappa, W|det|rho, G^{-1}
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   load_records(R, S, A.tab, e1, e2, e3);
   double* Ke = A.K_out ? (double*)A.K_out + e * (int64_t)N * N : nullptr;
   double* Me = A.M_out ? (double*)A.M_out + e * (int64_t)N * N : nullptr;
@@ -505,9 +503,8 @@ __global__ void __launch_bounds__(kGenThreads)
   const int n1 = S.n[0], n2 = S.n[1], n3 = S.n[2], q1 = S.q[0], q2 = S.q[1];
   const int N = S.N, Q = S.Q;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   load_records(R, S, A.tab, e1, e2, e3);
   // gather u_e, v_e through the dof map (support set of the element)
   const int s1 = A.span[0][e1] - p1, s2 = A.span[1][e2] - p2;

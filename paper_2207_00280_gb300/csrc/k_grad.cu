@@ -323,9 +323,8 @@ __global__ void __launch_bounds__(GRD<T, P, QG, GEN>::NT) k_grad3(const GradArgs
   S* G = reinterpret_cast<S*>(grad_dyn);
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   for (int i = tid; i < 3 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
@@ -380,7 +379,8 @@ __global__ void __launch_bounds__(64) k_grad2(const GradArgs A) {
   __shared__ T UX[NP + 1][N];                  // the stiffness pairs, then the mass pair
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1), e2 = (int)(e / A.K1);
+  int e1, e2;
+  elem_coords2(A, e, e1, e2);
   const int64_t NN = (int64_t)N * N;
   if (A.GK) issue_block<T, N, GS, NT>((const T*)A.GK + e * NN, Gs[0]);
   if (A.GM) issue_block<T, N, GS, NT>((const T*)A.GM + e * NN, Gs[1]);

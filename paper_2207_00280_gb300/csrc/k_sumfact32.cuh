@@ -590,9 +590,8 @@ __device__ __forceinline__ void sf3_f32_stage_inputs(const ElemArgs& A, int64_t 
                                                      double* kap, double* rho, double* jac) {
   constexpr int REC = C::REC, Q = C::Q, NT = C::NT;
   const int tid = threadIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   for (int i = tid; i < 3 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const int ek = d == 0 ? e1 : (d == 1 ? e2 : e3);
@@ -685,9 +684,8 @@ __device__ __forceinline__ bool sf3_f32_element(const ElemArgs& A, int64_t e, fl
   int* pairs = (int*)(region + C::f_region);         // [NSp] packed (a' << 16 | b')
 
   const int tid = threadIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
   __syncthreads();  // shared memory of the previous element is no longer read
 
   // ---- coalesced staging of this element's inputs -------------------------------

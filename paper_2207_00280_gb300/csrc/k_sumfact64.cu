@@ -83,9 +83,8 @@ __global__ void __launch_bounds__(SF3<P, QG, GEN>::NT)
 
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
 
   // ---- basis records of the three directions, pair tables ----------------
   for (int i = tid; i < 3 * REC; i += NT) {
@@ -357,7 +356,8 @@ __global__ void __launch_bounds__(SF2<P, QG, GEN>::NT) k_sf2_f64(const ElemArgs 
   int* pairs1 = (int*)(T + C::NTB * n2 * q);
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1), e2 = (int)(e / A.K1);
+  int e1, e2;
+  elem_coords2(A, e, e1, e2);
   for (int i = tid; i < 2 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
     const double* tb = d == 0 ? A.tab[0] : A.tab[1];

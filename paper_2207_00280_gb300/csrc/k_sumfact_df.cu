@@ -105,9 +105,8 @@ __global__ void __launch_bounds__(SFD<P, QG, GEN>::NT) k_sf3_df(const ElemArgs A
 
   const int tid = threadIdx.x;
   const int64_t e = blockIdx.x;
-  const int e1 = (int)(e % A.K1);
-  const int e2 = (int)((e / A.K1) % A.K2);
-  const int e3 = (int)(e / ((int64_t)A.K1 * A.K2));
+  int e1, e2, e3;
+  elem_coords(A, e, e1, e2, e3);
 
   for (int i = tid; i < 3 * REC; i += NT) {
     const int d = i / REC, j = i - d * REC;
