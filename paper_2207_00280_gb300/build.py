@@ -49,8 +49,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    # every header a translation unit may include (.h and .cuh)
     hdr_m = max(os.path.getmtime(p) for p in glob.glob(os.path.join(CSRC, "*.h")) +
-                glob.glob(os.path.join(INCLUDE, "*.h")))
+                glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
