@@ -25,8 +25,8 @@
 //            mbarrier), place the entries in a shared-memory copy of the
 //            tile's output block (thread (a', b') writes n floats per a1 at
 //            stride n from its neighbours: no bank conflicts at odd n), and
-//            move the block to HBM with one bulk asynchronous copy; two staging
-//            buffers alternate, so a copy reads one while the next is filled.
+//            move the block to HBM with one bulk asynchronous copy; three staging
+//            buffers rotate, so two copies can be in flight while the next is filled.
 // Producers and consumers meet only at these mbarriers and at the start of
 // an element; every wait is bounded.
 // The symmetric half of stage 2 is computed twice (once per row order), which
@@ -84,7 +84,8 @@ struct ST {
   static constexpr size_t f_geo = 2 * d_geo + 3 * REC;   // the FP64 staging + FP32 records
   // the staging is dead once the coefficients exist, before stage 1 writes T1
   static constexpr size_t f_T1g = (f_T1 > f_geo ? f_T1 : f_geo) + 2;
-  static constexpr size_t floats = f_px + f_py + f_pz + f_T1g + f_coef + 2 * f_stage + 8;
+  static constexpr int NSTG = 3;                     // staging buffers (two copies in flight)
+  static constexpr size_t floats = f_px + f_py + f_pz + f_T1g + f_coef + NSTG * f_stage + 8;
   static constexpr size_t smem = ops_bytes + 4 * floats + 96 + 128;   // + mbarriers, slot, align
   static_assert(f_stage % 4 == 0, "staging buffers must stay 16-byte aligned");
   static constexpr int CPB = (DK ? NU : 0) + (DM ? NU : 0);          // TMEM columns per buffer
@@ -96,7 +97,7 @@ template <class C>
 struct SPtrs {
   unsigned char* A0;       // the operand tile: K hi, K lo, M hi, M lo
   unsigned char *BKh, *BKl, *BMh, *BMl;
-  float *px, *py, *pz, *T1, *coef, *recf, *stage0, *stage1;
+  float *px, *py, *pz, *T1, *coef, *recf, *stage0, *stage1, *stage2;
   double *rec, *kap, *rho, *jac;
   uint64_t* mbar;          // [4]: MMA done (buffer 0, 1), TMEM free (buffer 0, 1)
   uint32_t* tslot;
@@ -123,7 +124,8 @@ struct SPtrs {
     coef = T1 + C::f_T1g;
     stage0 = (float*)(((uintptr_t)(coef + C::f_coef) + 15) & ~(uintptr_t)15);
     stage1 = stage0 + C::f_stage;
-    uintptr_t mb = ((uintptr_t)(stage1 + C::f_stage) + 15) & ~(uintptr_t)15;
+    stage2 = stage1 + C::f_stage;
+    uintptr_t mb = ((uintptr_t)(stage2 + C::f_stage) + 15) & ~(uintptr_t)15;
     mbar = (uint64_t*)mb;
     tslot = (uint32_t*)(mbar + 4);
   }
@@ -265,8 +267,8 @@ __device__ __forceinline__ void bar_group(int id, int count) {
 // after the other (the buffer is released after its last read): the
 // accumulators of the row are read, and the entries K[a1 + n a'][b1 + n b'] go into a
 // staging buffer laid out as the output rows n APT t .. n APT (t + 1) - 1, and
-// consumer thread 0 moves it to HBM with one bulk asynchronous copy (the two
-// buffers alternate: before one is refilled, the copy issued from it two
+// consumer thread 0 moves it to HBM with one bulk asynchronous copy (the three
+// buffers rotate: before one is refilled, the copy issued from it three
 // steps earlier must have read it).  `sc` counts the staging steps.
 template <class C>
 __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, int t, int b,
@@ -292,12 +294,14 @@ __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, in
       mbar_arrive(smem_u32(S.mbar + 2 + b));
     }
     float* g = (mat == 0 ? gK : gM) + (int64_t)(n * ap0) * N;
-    const int sb = (int)(sc & 1u);
+    const int sb = (int)(sc % 3u);
     ++sc;
     // (a select, not an indexed array: an index into a member array would put
     // the pointer record in local memory)
-    float* stg = (sb ? S.stage1 : S.stage0) + stage_offset(g);
-    if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+    float* stg = (sb == 0 ? S.stage0 : (sb == 1 ? S.stage1 : S.stage2)) + stage_offset(g);
+    // the copy issued from this buffer three steps ago has read it (the two
+    // later ones may still be in flight)
+    if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 2;\n" ::: "memory");
     bar_group(2, 128);
     if (valid) {
       float* row = stg + (n * (ap - ap0)) * N + n * bp;
