@@ -55,7 +55,10 @@ struct ST {
   static constexpr int REC = 2 * q * n + q;
   static constexpr int RW = 4 * q;                    // x, y pattern records: 4 patterns
   static constexpr int RZ = (3 * q) % 2 == 0 ? 3 * q + 1 : 3 * q;
-  static constexpr int TS = (q * q) % 2 == 0 ? q * q + 1 : q * q;
+  // stage-1 row stride: identity map, a multiple of 4 (stage 2 reads the q
+  // values k1 of one k2 as 16- and 8-byte vectors); general map, odd (its
+  // stage 2 reads one value per thread, consecutive threads along k1)
+  static constexpr int TS = !GEN ? (q * q + 3) / 4 * 4 : ((q * q) % 2 == 0 ? q * q + 1 : q * q);
   static constexpr int NTERM = GEN ? 7 : 3, NCOEF = GEN ? 7 : 2;
   // stage-1 term and coefficient slots (the identity map keeps terms 0, 3, 4
   // and coefficients W kappa, W rho)
@@ -83,7 +86,7 @@ struct ST {
   static constexpr size_t d_geo = 3 * REC + 2 * (size_t)Q + (GEN ? 9 * (size_t)Q : 0);  // doubles
   static constexpr size_t f_geo = 2 * d_geo + 3 * REC;   // the FP64 staging + FP32 records
   // the staging is dead once the coefficients exist, before stage 1 writes T1
-  static constexpr size_t f_T1g = (f_T1 > f_geo ? f_T1 : f_geo) + 2;
+  static constexpr size_t f_T1g = (f_T1 > f_geo ? f_T1 : f_geo) + 4;
   static constexpr int NSTG = 3;                     // staging buffers (two copies in flight)
   static constexpr size_t floats = f_px + f_py + f_pz + f_T1g + f_coef + NSTG * f_stage + 8;
   static constexpr size_t smem = ops_bytes + 4 * floats + 96 + 128;   // + mbarriers, slot, align
@@ -114,8 +117,9 @@ struct SPtrs {
     py = px + C::f_px;
     pz = py + C::f_py;
     T1 = pz + C::f_pz;
-    // 8-byte alignment for the FP64 staging that shares T1's space
-    T1 = (float*)(((uintptr_t)T1 + 7) & ~(uintptr_t)7);
+    // 16-byte alignment: the vector reads of stage 2 and the FP64 staging
+    // that shares T1's space
+    T1 = (float*)(((uintptr_t)T1 + 15) & ~(uintptr_t)15);
     rec = (double*)T1;
     kap = rec + 3 * C::REC;
     rho = kap + C::Q;
@@ -198,6 +202,145 @@ __device__ __forceinline__ void st_issue(uint32_t d, const unsigned char* Ah, co
       umma_tf32(d, dAh, dBl, IDESC, 1u);
       umma_tf32(d, dAl, dBh, IDESC, 1u);
     }
+  }
+}
+
+// The L consecutive floats base[OFF .. OFF + L) into v (base 16-byte
+// aligned; OFF and L fixed at compile time): 16-byte loads where the offset
+// allows, then 8-byte, then single words.
+template <int OFF, int L, int J = 0>
+__device__ __forceinline__ void ld_run(const float* __restrict__ base, float* v) {
+  if constexpr (J < L) {
+    constexpr int c = OFF + J;
+    if constexpr (c % 4 == 0 && J + 4 <= L) {
+      const float4 w = *(const float4*)(base + c);
+      v[J] = w.x; v[J + 1] = w.y; v[J + 2] = w.z; v[J + 3] = w.w;
+      ld_run<OFF, L, J + 4>(base, v);
+    } else if constexpr (c % 2 == 0 && J + 2 <= L) {
+      const float2 w = *(const float2*)(base + c);
+      v[J] = w.x; v[J + 1] = w.y;
+      ld_run<OFF, L, J + 2>(base, v);
+    } else {
+      v[J] = base[c];
+      ld_run<OFF, L, J + 1>(base, v);
+    }
+  }
+}
+
+// v[0 .. L) into the columns C0 .. C0 + L - 1 of one row of a K-major
+// operand (rb = the row's byte offset, (r >> 3) KDIM EB 8 + (r & 7) 16; one
+// 16-byte chunk per row and 16 / EB columns, the chunks 128 bytes apart), as
+// uput does it value by value: FP32 hi = the value, lo = value - its TF32
+// truncation; BF16 the rounded value (lo == nullptr: the A operand).  Runs
+// within a chunk go out as one 16-, 8- or 4-byte store.
+template <bool BF, int C0, int L, int J = 0>
+__device__ __forceinline__ void uput_run(unsigned char* hi, unsigned char* lo, int rb, const float* v) {
+  if constexpr (J < L) {
+    constexpr int c = C0 + J;
+    constexpr int EB = BF ? 2 : 4, PER = 16 / EB;
+    constexpr int o = (c / PER) * 128 + (c % PER) * EB;
+    if constexpr (!BF) {
+      if constexpr (c % 4 == 0 && J + 4 <= L) {
+        *(float4*)(hi + rb + o) = make_float4(v[J], v[J + 1], v[J + 2], v[J + 3]);
+        *(float4*)(lo + rb + o) = make_float4(v[J] - tf32_trunc(v[J]), v[J + 1] - tf32_trunc(v[J + 1]),
+                                              v[J + 2] - tf32_trunc(v[J + 2]), v[J + 3] - tf32_trunc(v[J + 3]));
+        uput_run<BF, C0, L, J + 4>(hi, lo, rb, v);
+      } else if constexpr (c % 2 == 0 && J + 2 <= L) {
+        *(float2*)(hi + rb + o) = make_float2(v[J], v[J + 1]);
+        *(float2*)(lo + rb + o) = make_float2(v[J] - tf32_trunc(v[J]), v[J + 1] - tf32_trunc(v[J + 1]));
+        uput_run<BF, C0, L, J + 2>(hi, lo, rb, v);
+      } else {
+        *(float*)(hi + rb + o) = v[J];
+        *(float*)(lo + rb + o) = v[J] - tf32_trunc(v[J]);
+        uput_run<BF, C0, L, J + 1>(hi, lo, rb, v);
+      }
+    } else {
+      if constexpr (c % 8 == 0 && J + 8 <= L) {
+        *(uint4*)(hi + rb + o) = make_uint4(pack_bf16x2(v[J], v[J + 1]), pack_bf16x2(v[J + 2], v[J + 3]),
+                                            pack_bf16x2(v[J + 4], v[J + 5]), pack_bf16x2(v[J + 6], v[J + 7]));
+        uput_run<BF, C0, L, J + 8>(hi, lo, rb, v);
+      } else if constexpr (c % 4 == 0 && J + 4 <= L) {
+        *(uint2*)(hi + rb + o) = make_uint2(pack_bf16x2(v[J], v[J + 1]), pack_bf16x2(v[J + 2], v[J + 3]));
+        uput_run<BF, C0, L, J + 4>(hi, lo, rb, v);
+      } else if constexpr (c % 2 == 0 && J + 2 <= L) {
+        *(uint32_t*)(hi + rb + o) = pack_bf16x2(v[J], v[J + 1]);
+        uput_run<BF, C0, L, J + 2>(hi, lo, rb, v);
+      } else {
+        *(__nv_bfloat16*)(hi + rb + o) = __float2bfloat16_rn(v[J]);
+        uput_run<BF, C0, L, J + 1>(hi, lo, rb, v);
+      }
+    }
+  }
+}
+
+// f(ic<0>{}), ..., f(ic<N - 1>{}): a loop whose index is a compile-time
+// constant in the body (the vector widths of ld_run depend on it).
+template <int V>
+struct ic {
+  static constexpr int value = V;
+};
+template <int I, int N, class F>
+__device__ __forceinline__ void unroll_ic(F&& f) {
+  if constexpr (I < N) {
+    f(ic<I>{});
+    unroll_ic<I + 1, N>(f);
+  }
+}
+
+// Stage 2 of tile t for the identity map: one thread per operand row and
+// value group, all q values k1 at once (role 0, producer threads 0-127: C11
+// and CM; role 1, threads 128-255: C00), so that each row receives whole
+// vector stores and the stage-1 rows T_t[a3][b3][k1 + q k2] (16-byte aligned,
+// TS a multiple of 4) are read as vectors.  Same sums, same order of the
+// terms as st_stage2.
+template <class C, bool BF>
+__device__ __forceinline__ void st_stage2_rows(const SPtrs<C>& S, int t, int ptid) {
+  constexpr int n = C::n, q = C::q, n2 = C::n2, RW = C::RW, TS = C::TS;
+  constexpr int SZ = n2 * TS;
+  static_assert(TS % 4 == 0 && RW % 4 == 0 && C::NP == 256 && C::RT <= 128, "row-vector stage 2");
+  const int role = ptid >> 7, r = ptid & 127;
+  if (r >= C::RT) return;
+  const int ap = C::APT * t + r / n2, bp = r - (r / n2) * n2;
+  if (ap >= n2) return;
+  const int a2 = ap % n, a3 = ap / n, b2 = bp % n, b3 = bp / n;
+  const float* y = S.py + (a2 * n + b2) * RW;   // 00, 11, 10, 01
+  const float* T = S.T1 + (a3 * n + b3) * TS;
+  float y00[q];
+  ld_run<0, q>(y, y00);
+  if (role == 0) {
+    float c11[q], cm[q];
+#pragma unroll
+    for (int k1 = 0; k1 < q; ++k1) { c11[k1] = 0.f; cm[k1] = 0.f; }
+    unroll_ic<0, q>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      float tv[q];
+      if constexpr (C::DK) {
+        ld_run<q * k2, q>(T + C::ts(0) * SZ, tv);
+#pragma unroll
+        for (int k1 = 0; k1 < q; ++k1) c11[k1] = fmaf(y00[k2], tv[k1], c11[k1]);
+      }
+      if constexpr (C::DM) {
+        ld_run<q * k2, q>(T + C::ts(3) * SZ, tv);
+#pragma unroll
+        for (int k1 = 0; k1 < q; ++k1) cm[k1] = fmaf(y00[k2], tv[k1], cm[k1]);
+      }
+    });
+    if constexpr (C::DK) uput_run<BF, 0, q>(S.AKh(), S.AKl(), (r >> 3) * (C::KA * C::EB * 8) + (r & 7) * 16, c11);
+    if constexpr (C::DM) uput_run<BF, 0, q>(S.AMh(), S.AMl(), (r >> 3) * (C::KAM * C::EB * 8) + (r & 7) * 16, cm);
+  } else if constexpr (C::DK) {
+    float y11[q], c00[q];
+    ld_run<q, q>(y, y11);
+#pragma unroll
+    for (int k1 = 0; k1 < q; ++k1) c00[k1] = 0.f;
+    unroll_ic<0, q>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      float t0[q], t4[q];
+      ld_run<q * k2, q>(T + C::ts(0) * SZ, t0);
+      ld_run<q * k2, q>(T + C::ts(4) * SZ, t4);
+#pragma unroll
+      for (int k1 = 0; k1 < q; ++k1) c00[k1] = fmaf(y00[k2], t4[k1], fmaf(y11[k2], t0[k1], c00[k1]));
+    });
+    uput_run<BF, q, q>(S.AKh(), S.AKl(), (r >> 3) * (C::KA * C::EB * 8) + (r & 7) * 16, c00);
   }
 }
 
@@ -305,10 +448,25 @@ __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, in
     bar_group(2, 128);
     if (valid) {
       float* row = stg + (n * (ap - ap0)) * N + n * bp;
+      bool written = false;
+      if constexpr (n % 2 == 0) {
+        // even n: every run of n entries starts on an 8-byte boundary when g
+        // is 8-byte aligned (the staging mirrors g's alignment)
+        if ((stage_offset(g) & 1) == 0) {
 #pragma unroll
-      for (int a1 = 0; a1 < n; ++a1)
+          for (int a1 = 0; a1 < n; ++a1)
 #pragma unroll
-        for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
+            for (int b1 = 0; b1 < n; b1 += 2)
+              *(float2*)(row + a1 * N + b1) = make_float2(v[a1 * n + b1], v[a1 * n + b1 + 1]);
+          written = true;
+        }
+      }
+      if (!written) {
+#pragma unroll
+        for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+          for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
+      }
     }
     fence_proxy_async_smem();  // the staged block is read by the bulk copy
     bar_group(2, 128);
@@ -386,7 +544,9 @@ __device__ __forceinline__ bool st_element(const ElemArgs& A, int64_t e, unsigne
   {
     constexpr int SZ = n2 * TS;
     for (int it = tid; it < q * q * n; it += NT) {
-      const int a3 = it % n, kk = it / n;   // kk = k1 + q k2
+      // consecutive threads take consecutive kk = k1 + q k2 (their T writes
+      // fall on consecutive words, their z reads are shared)
+      const int kk = it % (q * q), a3 = it / (q * q);
       float d0[q], d1[q], d2[q], d3[q], d4[q], d5[q], d6[q];
 #pragma unroll
       for (int k3 = 0; k3 < q; ++k3) {
@@ -450,7 +610,8 @@ __device__ __forceinline__ bool st_element(const ElemArgs& A, int64_t e, unsigne
       const uint32_t g = tc + (uint32_t)t, b = g & 1u;
       // the operand tile is free once the MMAs of the previous tile have read it
       if (g >= 1) ok &= mbar_wait_bounded(smem_u32(S.mbar + ((g - 1) & 1u)), ((g - 1) >> 1) & 1u, kWait);
-      st_stage2<C, GEN, BF>(S, t, ptid);
+      if constexpr (GEN) st_stage2<C, GEN, BF>(S, t, ptid);
+      else st_stage2_rows<C, BF>(S, t, ptid);
       fence_proxy_async_smem();  // the operand rows are read by the tensor core
       bar_group(1, C::NP);
       if (ptid == 0) {

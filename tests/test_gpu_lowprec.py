@@ -61,6 +61,21 @@ def test_single_matrix_modes(oracle_mod, prec, which):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("which", ["stiffness", "mass"])
+@pytest.mark.parametrize("p,q", [(4, 5), (4, 6), (5, 6)])
+def test_streamed_single_matrix_modes(oracle_mod, prec, which, p, q):
+    """The streamed form (identity map, p = 4 and 5) with one matrix only: its
+    row-vector stage 2 writes the C11/CM rows and the C00 rows from different
+    threads, and each single-matrix mode drops one of them."""
+    knots = [wl.open_uniform_knots(K, p) for K in (3, 2, 3)]
+    P = oracle_mod.Patch(knots, p, q)
+    kappa = wl.lognormal(P.E * P.Q, 820 + p)
+    rho = wl.lognormal(P.E * P.Q, 830 + p)
+    _cmp(oracle_mod, knots, p, q, kappa, rho, None, prec, mass=which == "mass",
+         stiffness=which == "stiffness")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_curved_p4_stiffness_only_every_element(oracle_mod, prec):
     """The stiffness alone with a general map at p = 4, q = 5 has a kernel of
     its own (symmetric operand rows, staged mirror, bulk-copy output, the next
