@@ -87,9 +87,16 @@ struct ST {
   static constexpr size_t f_geo = 2 * d_geo + 3 * REC;   // the FP64 staging + FP32 records
   // the staging is dead once the coefficients exist, before stage 1 writes T1
   static constexpr size_t f_T1g = (f_T1 > f_geo ? f_T1 : f_geo) + 4;
-  static constexpr int NSTG = 3;                     // staging buffers (two copies in flight)
-  static constexpr size_t floats = f_px + f_py + f_pz + f_T1g + f_coef + NSTG * f_stage + 8;
-  static constexpr size_t smem = ops_bytes + 4 * floats + 96 + 128;   // + mbarriers, slot, align
+  static constexpr size_t floats_for(int nb) { return f_px + f_py + f_pz + f_T1g + f_coef + nb * f_stage + 8; }
+  static constexpr size_t smem_for(int nb) { return ops_bytes + 4 * floats_for(nb) + 96 + 128; }
+  // output staging buffers: four where they fit beside the CTAs per SM of the
+  // form (two of at most 112 KB for the identity map, one for the general
+  // map) -- the K and M blocks of one tile then share one pair of group
+  // barriers, with the two copies of the previous tile still in flight --
+  // else three (one matrix per step, two copies in flight)
+  static constexpr int NSTG = smem_for(4) <= (GEN ? 227 * 1024 : 112 * 1024) ? 4 : 3;
+  static constexpr size_t floats = floats_for(NSTG);
+  static constexpr size_t smem = smem_for(NSTG);   // + mbarriers, slot, align
   static_assert(f_stage % 4 == 0, "staging buffers must stay 16-byte aligned");
   static constexpr int CPB = (DK ? NU : 0) + (DM ? NU : 0);          // TMEM columns per buffer
   static constexpr int TCOLS = 2 * CPB <= 32 ? 32 : 2 * CPB <= 64 ? 64 : 2 * CPB <= 128 ? 128
@@ -100,7 +107,7 @@ template <class C>
 struct SPtrs {
   unsigned char* A0;       // the operand tile: K hi, K lo, M hi, M lo
   unsigned char *BKh, *BKl, *BMh, *BMl;
-  float *px, *py, *pz, *T1, *coef, *recf, *stage0, *stage1, *stage2;
+  float *px, *py, *pz, *T1, *coef, *recf, *stage0, *stage1, *stage2, *stage3;
   double *rec, *kap, *rho, *jac;
   uint64_t* mbar;          // [4]: MMA done (buffer 0, 1), TMEM free (buffer 0, 1)
   uint32_t* tslot;
@@ -129,9 +136,15 @@ struct SPtrs {
     stage0 = (float*)(((uintptr_t)(coef + C::f_coef) + 15) & ~(uintptr_t)15);
     stage1 = stage0 + C::f_stage;
     stage2 = stage1 + C::f_stage;
-    uintptr_t mb = ((uintptr_t)(stage2 + C::f_stage) + 15) & ~(uintptr_t)15;
+    stage3 = stage2 + C::f_stage;   // (NSTG = 4 only)
+    uintptr_t mb = ((uintptr_t)(stage0 + C::NSTG * C::f_stage) + 15) & ~(uintptr_t)15;
     mbar = (uint64_t*)mb;
     tslot = (uint32_t*)(mbar + 4);
+  }
+  // staging buffer sb (a select, not an indexed array: an index into a
+  // member array would put the pointer record in local memory)
+  __device__ __forceinline__ float* stage(int sb) const {
+    return sb == 0 ? stage0 : (sb == 1 ? stage1 : (sb == 2 || C::NSTG == 3 ? stage2 : stage3));
   }
   // operand arrays of the tile
   __device__ __forceinline__ unsigned char* AKh() const { return A0; }
@@ -405,14 +418,61 @@ __device__ __forceinline__ void bar_group(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// The accumulators v of operand row (a', b') of a tile whose first a' is ap0:
+// entries K[a1 + n a'][b1 + n b'] into the tile's staged output block stg
+// (output rows n ap0 .., mirroring g's alignment).
+template <class C>
+__device__ __forceinline__ void st_stage_row(float* stg, const float* g, int ap, int ap0, int bp,
+                                             const float* v) {
+  constexpr int n = C::n, N = C::N;
+  float* row = stg + (n * (ap - ap0)) * N + n * bp;
+  if constexpr (n % 2 == 0) {
+    // even n: every run of n entries starts on an 8-byte boundary when g is
+    // 8-byte aligned
+    if ((stage_offset(g) & 1) == 0) {
+#pragma unroll
+      for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+        for (int b1 = 0; b1 < n; b1 += 2)
+          *(float2*)(row + a1 * N + b1) = make_float2(v[a1 * n + b1], v[a1 * n + b1 + 1]);
+      return;
+    }
+  }
+#pragma unroll
+  for (int a1 = 0; a1 < n; ++a1)
+#pragma unroll
+    for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
+}
+
+// A staged block of nn floats to g: the 16-byte-aligned middle by one bulk
+// copy (consumer thread 0; one bulk group per block, committed even when
+// empty, so that the group count per staging step is fixed), the scalar head
+// and tail by the consumer threads.
+__device__ __forceinline__ void st_copy_block(float* g, const float* stg, int nn, int ctid) {
+  const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
+  const int h = head < nn ? head : nn;
+  const int nv = (nn - h) / 4;
+  for (int i = ctid; i < h; i += 128) g[i] = stg[i];
+  for (int i = h + 4 * nv + ctid; i < nn; i += 128) g[i] = stg[i];
+  if (ctid == 0) {
+    if (nv > 0)
+      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
+                   ::"l"(g + h), "r"(smem_u32(stg + h)), "r"(nv * 16) : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  }
+}
+
 // Epilogue of tile t from TMEM buffer b (the 128 consumer threads, ctid =
-// TMEM lane = operand row r; warp w reads lanes 32 w .. 32 w + 31), one matrix
-// after the other (the buffer is released after its last read): the
-// accumulators of the row are read, and the entries K[a1 + n a'][b1 + n b'] go into a
-// staging buffer laid out as the output rows n APT t .. n APT (t + 1) - 1, and
-// consumer thread 0 moves it to HBM with one bulk asynchronous copy (the three
-// buffers rotate: before one is refilled, the copy issued from it three
-// steps earlier must have read it).  `sc` counts the staging steps.
+// TMEM lane = operand row r; warp w reads lanes 32 w .. 32 w + 31): the
+// accumulators of the row are read and the entries K[a1 + n a'][b1 + n b'] go
+// into a staging buffer laid out as the output rows n APT t .. n APT (t + 1) - 1,
+// which consumer thread 0 moves to HBM with one bulk asynchronous copy.  The
+// NSTG buffers rotate (`sc` counts the staging steps); before one is refilled,
+// the copy issued from it NSTG steps earlier must have read it.  Four buffers
+// (both matrices): one step per matrix, both in one pair of group barriers,
+// two copies of the previous tile in flight.  Three buffers (or one matrix):
+// one step and one barrier pair per matrix, two copies in flight.  The TMEM
+// buffer is released after its last read.
 template <class C>
 __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, int t, int b,
                                             float* gK, float* gM, int ctid, uint32_t& sc) {
@@ -424,64 +484,57 @@ __device__ __forceinline__ void st_epilogue(const SPtrs<C>& S, uint32_t tmem, in
   const int ap = ap0 + r / n2, bp = r % n2;
   const bool valid = r < C::RT && ap < n2;
   const uint32_t ta = tmem + (uint32_t)(b * C::CPB) + ((uint32_t)(32 * warp) << 16);
-#pragma unroll
-  for (int mat = 0; mat < 2; ++mat) {
-    if ((mat == 0 && !C::DK) || (mat == 1 && !C::DM)) continue;
-    float v[NU];
-    const uint32_t col = (mat == 1 && C::DK) ? (uint32_t)NU : 0u;
-#pragma unroll
-    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + col + (uint32_t)c, v + c);
-    if (mat == 1 || !C::DM) {
-      // the last read of this TMEM buffer: it may take the MMAs of tile t + 2
-      fence_before_sync();
-      mbar_arrive(smem_u32(S.mbar + 2 + b));
-    }
-    float* g = (mat == 0 ? gK : gM) + (int64_t)(n * ap0) * N;
-    const int sb = (int)(sc % 3u);
-    ++sc;
-    // (a select, not an indexed array: an index into a member array would put
-    // the pointer record in local memory)
-    float* stg = (sb == 0 ? S.stage0 : (sb == 1 ? S.stage1 : S.stage2)) + stage_offset(g);
-    // the copy issued from this buffer three steps ago has read it (the two
-    // later ones may still be in flight)
+  const int nn = n * na * N;
+  if constexpr (C::NSTG == 4 && C::DK && C::DM) {
+    float* g0 = gK + (int64_t)(n * ap0) * N;
+    float* g1 = gM + (int64_t)(n * ap0) * N;
+    float* st0 = S.stage((int)(sc & 3u)) + stage_offset(g0);
+    float* st1 = S.stage((int)((sc + 1u) & 3u)) + stage_offset(g1);
+    sc += 2u;
+    // the copies issued from these two buffers (the previous tile's but one)
+    // have read them; the previous tile's two may still be in flight
     if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 2;\n" ::: "memory");
     bar_group(2, 128);
-    if (valid) {
-      float* row = stg + (n * (ap - ap0)) * N + n * bp;
-      bool written = false;
-      if constexpr (n % 2 == 0) {
-        // even n: every run of n entries starts on an 8-byte boundary when g
-        // is 8-byte aligned (the staging mirrors g's alignment)
-        if ((stage_offset(g) & 1) == 0) {
+    float v[NU];
 #pragma unroll
-          for (int a1 = 0; a1 < n; ++a1)
+    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)c, v + c);
+    if (valid) st_stage_row<C>(st0, g0, ap, ap0, bp, v);
 #pragma unroll
-            for (int b1 = 0; b1 < n; b1 += 2)
-              *(float2*)(row + a1 * N + b1) = make_float2(v[a1 * n + b1], v[a1 * n + b1 + 1]);
-          written = true;
-        }
-      }
-      if (!written) {
-#pragma unroll
-        for (int a1 = 0; a1 < n; ++a1)
-#pragma unroll
-          for (int b1 = 0; b1 < n; ++b1) row[a1 * N + b1] = v[a1 * n + b1];
-      }
-    }
-    fence_proxy_async_smem();  // the staged block is read by the bulk copy
+    for (int c = 0; c < NU; c += 16) tmem_ld16(ta + (uint32_t)(NU + c), v + c);
+    // the last read of this TMEM buffer: it may take the MMAs of tile t + 2
+    fence_before_sync();
+    mbar_arrive(smem_u32(S.mbar + 2 + b));
+    if (valid) st_stage_row<C>(st1, g1, ap, ap0, bp, v);
+    fence_proxy_async_smem();  // the staged blocks are read by the bulk copies
     bar_group(2, 128);
-    // the 16-byte-aligned middle by one bulk copy, the scalar head and tail by
-    // the consumer threads
-    const int nn = n * na * N;
-    const int head = (int)((4 - (((uintptr_t)g >> 2) & 3)) & 3);
-    const int h = head < nn ? head : nn;
-    const int nv = (nn - h) / 4;
-    for (int i = ctid; i < h; i += 128) g[i] = stg[i];
-    for (int i = h + 4 * nv + ctid; i < nn; i += 128) g[i] = stg[i];
-    if (ctid == 0 && nv > 0) {
-      asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n"
-                   ::"l"(g + h), "r"(smem_u32(stg + h)), "r"(nv * 16) : "memory");
-      asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    st_copy_block(g0, st0, nn, ctid);
+    st_copy_block(g1, st1, nn, ctid);
+  } else {
+#pragma unroll
+    for (int mat = 0; mat < 2; ++mat) {
+      if ((mat == 0 && !C::DK) || (mat == 1 && !C::DM)) continue;
+      float v[NU];
+      const uint32_t col = (mat == 1 && C::DK) ? (uint32_t)NU : 0u;
+#pragma unroll
+      for (int c = 0; c < NU; c += 16) tmem_ld16(ta + col + (uint32_t)c, v + c);
+      if (mat == 1 || !C::DM) {
+        fence_before_sync();
+        mbar_arrive(smem_u32(S.mbar + 2 + b));
+      }
+      float* g = (mat == 0 ? gK : gM) + (int64_t)(n * ap0) * N;
+      float* stg = S.stage((int)(sc % (uint32_t)C::NSTG)) + stage_offset(g);
+      ++sc;
+      // the copy issued from this buffer NSTG steps ago has read it (the
+      // NSTG - 1 later ones may still be in flight)
+      if (ctid == 0) {
+        if constexpr (C::NSTG == 4) asm volatile("cp.async.bulk.wait_group.read 3;\n" ::: "memory");
+        else asm volatile("cp.async.bulk.wait_group.read 2;\n" ::: "memory");
+      }
+      bar_group(2, 128);
+      if (valid) st_stage_row<C>(stg, g, ap, ap0, bp, v);
+      fence_proxy_async_smem();  // the staged block is read by the bulk copy
+      bar_group(2, 128);
+      st_copy_block(g, stg, nn, ctid);
     }
   }
 }
