@@ -93,4 +93,25 @@ template <> __device__ __forceinline__ ff from_double<ff>(double x) { return spl
 template <typename T> __device__ __forceinline__ store_t<T> to_store(T x) { return x; }
 template <> __device__ __forceinline__ double to_store<ff>(ff x) { return (double)x.hi + (double)x.lo; }
 
+// The double equal to float f, by integer instructions for normal numbers
+// and zeros (sign, exponent rebiased from 127 to 1023, mantissa shifted to
+// the top of 52 bits); subnormal, infinite and NaN values take the
+// conversion instruction.  The same value as (double)f.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u <= 253u)
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu)),
+                            (int)(u << 29));
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)f;
+}
+
+// to_store with the two exact conversions of a float-float done by integer
+// instructions and one FP64 addition left (the same double).  For kernels
+// whose FP64 pipe also carries other work (the adjoint's FP64 partial sums);
+// where issue slots are the limit, to_store's conversion instructions cost less.
+template <typename T> __device__ __forceinline__ store_t<T> to_store_int(T x) { return to_store<T>(x); }
+template <> __device__ __forceinline__ double to_store_int<ff>(ff x) { return f2d_exact(x.hi) + f2d_exact(x.lo); }
+
 }  // namespace iga

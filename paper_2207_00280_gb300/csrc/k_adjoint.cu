@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(ADJ<T, P, QG, GEN>::NT) k_adjoint3(const AdjAr
     } else {
       gq = from_double<T>(Wd) * (gu[0] * gv[0] + gu[1] * gv[1] + gu[2] * gv[2]);
     }
-    const store_t<T> gs = to_store<T>(gq);
+    const store_t<T> gs = to_store_int<T>(gq);
     if (A.grad) ((store_t<T>*)A.grad)[e * Q + k] = gs;
     if (A.partial) part += (A.kappa ? A.kappa[e * Q + k] : 1.0) * (double)gs;
   }
