@@ -24,9 +24,15 @@
 //            row (a', b') per thread), release the TMEM buffer (its "free"
 //            mbarrier), place the entries in a shared-memory copy of the
 //            tile's output block (thread (a', b') writes n floats per a1 at
-//            stride n from its neighbours: no bank conflicts at odd n), and
-//            move the block to HBM with one bulk asynchronous copy; three staging
-//            buffers rotate, so two copies can be in flight while the next is filled.
+//            stride n from its neighbours: no bank conflicts at odd n; 8-byte
+//            stores at even n), and move the block to HBM with one bulk
+//            asynchronous copy; three or four staging buffers rotate, so two
+//            copies can be in flight while the next block is filled (with four,
+//            the K and M blocks of a tile are staged between one pair of group
+//            barriers).
+// Stage 2 for the identity map takes one thread per operand row and value
+// group, all q values k1 at once (st_stage2_rows); the general map one value
+// per thread (st_stage2).
 // Producers and consumers meet only at these mbarriers and at the start of
 // an element; every wait is bounded.
 // The symmetric half of stage 2 is computed twice (once per row order), which
